@@ -1,0 +1,111 @@
+"""The INLA objective f_obj(theta) of Eq. 8 and its gradient (oracle; test
+infrastructure only).
+
+f_obj(theta) = log p(theta) + log l(y | theta, x) + log p(x | theta)
+               - log p_G(x | theta, y)                                  (Eq. 8)
+with
+  log p(x | theta)     = -N/2 log 2 pi + 1/2 log|Q_p| - 1/2 x^T Q_p x        (Eq. 1)
+  log l(y | theta, x)  = sum_k [1/2 log d_k - 1/2 log 2 pi - 1/2 d_k (y_k - (A x)_k)^2]
+  log p_G(x | theta,y) = -N/2 log 2 pi + 1/2 log|Q_c| - 1/2 (x-mu)^T Q_c (x-mu)  (Eq. 3)
+  mu = Q_c^{-1} A^T D y   (zero prior mean, Gaussian likelihood).
+For a Gaussian likelihood p_G is exact (Section II-A.3), so f_obj does not
+depend on x; x = mu is used unless another point is given.
+
+Reading of log p(theta) (the paper leaves the hyperprior unspecified): an
+independent N(theta0_i, 1) density on every component of theta.
+
+Central finite differences (Eq. 10): d f / d theta_i ~ (f(theta + h e_i) -
+f(theta - h e_i)) / (2h), h = 1e-3 unless given.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import bta as bta_mod
+from . import dense
+from . import model
+
+LOG_2PI = math.log(2.0 * math.pi)
+
+
+def log_prior_theta(theta: np.ndarray, theta0: np.ndarray) -> float:
+    d = np.asarray(theta) - np.asarray(theta0)
+    return float(-0.5 * np.sum(d * d) - 0.5 * d.shape[0] * LOG_2PI)
+
+
+class Factorized:
+    """log|Q| and solves with Q through either tier (dense or BTA blocks)."""
+
+    def __init__(self, Q: sp.spmatrix, tier: str, n: int, b: int, a: int):
+        self.tier = tier
+        if tier == "dense":
+            self.L = dense.cholesky(Q)
+        elif tier == "bta":
+            self.L = bta_mod.factor(bta_mod.blocks_from_sparse(Q, n, b, a))
+        else:
+            raise ValueError(tier)
+
+    def logdet(self) -> float:
+        if self.tier == "dense":
+            return float(2.0 * np.sum(np.log(np.diag(self.L))))
+        return bta_mod.logdet(self.L)
+
+    def solve(self, r: np.ndarray) -> np.ndarray:
+        if self.tier == "dense":
+            import scipy.linalg as sla
+            z = sla.solve_triangular(self.L, r, lower=True)
+            return sla.solve_triangular(self.L, z, lower=True, trans="T")
+        return bta_mod.solve(self.L, r)
+
+
+def default_tier(problem) -> str:
+    return "dense" if problem.N <= 6000 else "bta"
+
+
+def f_obj_terms(problem, theta, *, x=None, tier=None, fd=None, params=None) -> dict:
+    """Every term of Eq. 8 at theta (x defaults to the conditional mean mu).
+
+    ``params`` overrides the theta map (model parameters given directly)."""
+    tier = tier or default_tier(problem)
+    fd = model.fem_data(problem) if fd is None else fd
+    p = params if params is not None else model.theta_to_params(theta, problem.nv)
+    built = model.build(problem, p, fd)
+    n, b, a = problem.nt, problem.b, problem.a
+    N = problem.N
+    fp = Factorized(built.Qp, tier, n, b, a)
+    fc = Factorized(built.Qc, tier, n, b, a)
+    logdet_p = fp.logdet()
+    logdet_c = fc.logdet()
+    mu = fc.solve(built.rhs)
+    xx = mu if x is None else np.asarray(x, dtype=np.float64)
+    resid = problem.y - built.A @ xx
+    d = built.d
+    log_lik = float(np.sum(0.5 * np.log(d) - 0.5 * LOG_2PI - 0.5 * d * resid * resid))
+    log_px = float(-0.5 * N * LOG_2PI + 0.5 * logdet_p - 0.5 * xx @ (built.Qp @ xx))
+    dx = xx - mu
+    log_pg = float(-0.5 * N * LOG_2PI + 0.5 * logdet_c - 0.5 * dx @ (built.Qc @ dx))
+    log_pt = log_prior_theta(theta, problem.theta0) if theta is not None else 0.0
+    f = log_pt + log_lik + log_px - log_pg
+    return dict(f=f, log_prior_theta=log_pt, log_lik=log_lik, log_px=log_px,
+                log_pg=log_pg, logdet_p=logdet_p, logdet_c=logdet_c, mu=mu,
+                built=built)
+
+
+def f_obj(problem, theta, **kw) -> float:
+    return f_obj_terms(problem, theta, **kw)["f"]
+
+
+def fd_gradient(problem, theta, h: float = 1e-3, **kw) -> np.ndarray:
+    """Central finite-difference gradient of f_obj (Eq. 10); uses the
+    2 dim(theta) points theta +- h e_i."""
+    theta = np.asarray(theta, dtype=np.float64)
+    g = np.empty_like(theta)
+    for i in range(theta.shape[0]):
+        e = np.zeros_like(theta)
+        e[i] = h
+        g[i] = (f_obj(problem, theta + e, **kw) - f_obj(problem, theta - e, **kw)) / (2 * h)
+    return g
