@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Throughput of the BTA hot path of one f_obj(theta) evaluation on GB300.
+
+One step = one f_obj(theta) evaluation of the univariate AR(1) x SPDE model
+at working size (32 x 32 grid mesh: ns = 1024, nt = 64, nb = 4 fixed
+effects, m = 65,536 observations, N = 65,540): assembly, factorisation and
+log-determinant of Q_p and Q_c, the conditional-mean solve, the objective,
+and the selected inversion of Q_c.  Each step uses a different theta.
+
+value  = steps / s with inputs resident in HBM (device-timed, CUDA events)
+e2e    = the same through the C ABI with theta copied host->device and f,
+         mu and the marginal variances copied device->host inside the timed
+         region (pinned host buffers)
+--impl reference times the CPU FP64 oracle (oracle/) on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "f_obj evals/s and BTA Cholesky+selinv TFLOP/s: mixed vs FP64 on one GB300"
+UNIT = "f_obj evals/s"
+WORKLOAD = ("univariate AR(1) x SPDE Matern, 32x32 grid mesh ns=1024, nt=64, nb=4 fixed effects, "
+            "m=65536 observations, N=65540; per step: assemble+factor+log-det of Q_p and Q_c, "
+            "conditional-mean solve, f_obj, selected inversion of Q_c")
+CONFIG_NAME = "c2"
+# FP64 peak of the GB300: the nominal FP64 rate (no FP64 figure is measured by
+# the driver); a DFMA throughput probe on this machine read 1.20 TFLOP/s at 1995 MHz.
+FP64_PEAK_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--config", default=CONFIG_NAME)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_record(kernel_key: str):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary,
+    null if the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel_key)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        h = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return rec["bytes_per_launch"] if h == rec["source_sha1"] else None
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads") for d in threadpool_info() if d.get("user_api") == "blas"]
+        if n and n[0]:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def oracle_step(problem, theta, fd):
+    """One step of the workload on the CPU oracle (tier B): f_obj and selinv(Q_c)."""
+    from oracle import bta as obta
+    from oracle import fobj as ofobj
+    terms = ofobj.f_obj_terms(problem, theta, tier="bta", fd=fd)
+    built = terms["built"]
+    L = obta.factor(obta.blocks_from_sparse(built.Qc, problem.nt, problem.b, problem.a))
+    obta.selinv(L)
+    return terms["f"]
+
+
+def thetas_for(problem, count, rank):
+    import numpy as np
+    rng = np.random.default_rng(1000 + rank)
+    return [problem.theta0 + 0.02 * rng.standard_normal(problem.theta0.shape) for _ in range(count)]
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    from oracle import model as omodel
+    p = synth.problem_from_config(args.config)
+    fd = omodel.fem_data(p)
+    thetas = thetas_for(p, args.warmup + args.steps, 0)
+    for j in range(args.warmup):
+        oracle_step(p, thetas[j], fd)
+    t0 = time.perf_counter()
+    for j in range(args.steps):
+        oracle_step(p, thetas[args.warmup + j], fd)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "name": args.config},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                         "sample": "whole workload per step (numpy/scipy FP64 block recurrences)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2507_06938_gb300 import _build
+    if rank == 0 or world == 1:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2507_06938_gb300 import bta
+    import synth
+
+    p = synth.problem_from_config(args.config)
+    precision = bta.BTA_FP64 if args.precision == "fp64" else bta.BTA_MIXED
+    stream = torch.cuda.Stream()
+    model = bta.BtaModel(p)
+    ctx = bta.BtaContext(p.nt, p.b, p.a, precision, stream)
+    nsteps = args.warmup + args.steps
+    thetas_h = np.stack(thetas_for(p, nsteps, rank))
+    thetas_d = torch.tensor(thetas_h, dtype=torch.float64, device="cuda")
+    f_d = torch.zeros(nsteps, dtype=torch.float64, device="cuda")
+    mu_d = torch.zeros(p.N, dtype=torch.float64, device="cuda")
+    var_d = torch.zeros(p.N, dtype=torch.float64, device="cuda")
+
+    def step(j, theta_dev):
+        ctx.fobj_eval(model, theta_dev, f_d[j:j + 1], mu_d)
+        ctx.selinv(bta.BTA_QC)
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        for j in range(args.warmup):
+            step(j, thetas_d[j:j + 1])
+        ctx.sync()
+        barrier_sync()
+        # ---- device-resident timed region
+        launches0 = bta.bta_launch_count()
+        ctx.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            for j in range(args.steps):
+                step(args.warmup + j, thetas_d[args.warmup + j:args.warmup + j + 1])
+            e1.record(stream)
+            e1.synchronize()
+        ctx.sync()
+        launches = bta.bta_launch_count() - launches0
+        prof_ms, prof_n, prof_flops = ctx.profile_read()
+        ctx.profile(False)
+        ms = e0.elapsed_time(e1)
+        barrier_sync()
+        # ---- end-to-end through the C ABI with host buffers
+        th_pin = torch.tensor(thetas_h, dtype=torch.float64).pin_memory()
+        f_pin = torch.zeros(args.steps, dtype=torch.float64).pin_memory()
+        mu_pin = torch.zeros(p.N, dtype=torch.float64).pin_memory()
+        var_pin = torch.zeros(p.N, dtype=torch.float64).pin_memory()
+        theta_stage = torch.zeros((1, p.theta0.shape[0]), dtype=torch.float64, device="cuda")
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for j in range(args.steps):
+            theta_stage.copy_(th_pin[args.warmup + j:args.warmup + j + 1], non_blocking=True)
+            ctx.fobj_eval(model, theta_stage, f_d[j:j + 1], mu_d)
+            ctx.selinv(bta.BTA_QC)
+            ctx.selinv_diag(bta.BTA_QC, var_d)
+            f_pin[j:j + 1].copy_(f_d[j:j + 1], non_blocking=True)
+            mu_pin.copy_(mu_d, non_blocking=True)
+            var_pin.copy_(var_d, non_blocking=True)
+        g1.record(stream)
+        g1.synchronize()
+        ctx.sync()
+        ms_e2e = g0.elapsed_time(g1)
+
+    t_local = torch.tensor([ms, ms_e2e], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms, ms_e2e = float(t_local[0]), float(t_local[1])
+    total_steps = args.steps * world
+    value = total_steps / (ms / 1e3)
+    e2e_value = total_steps / (ms_e2e / 1e3)
+    flops_step = 2 * bta.bta_flops_factor(p.nt, p.b, p.a) + bta.bta_flops_selinv(p.nt, p.b, p.a)
+    tflops = flops_step * total_steps / (ms / 1e3) / 1e12
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    achieved = (prof_flops / (prof_ms / 1e3) / 1e12) if prof_ms > 0 else None
+    roof = {
+        "bound": "alu", "kernel": "gemm64_kernel<4,4> (FP64 DFMA Schur-update GEMM, b x b x b)",
+        "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+        "traffic": traffic_record("gemm64_bxbxb"),
+        "launches_timed": prof_n, "flops_per_launch": (prof_flops / prof_n) if prof_n else None,
+        "peak_source": "nominal GB300 FP64 rate (no FP64 entry in the measured peaks)",
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "mixed",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "name": args.config, "precision": args.precision,
+                   "l2": "inputs larger than L2 (BTA blocks ~1.07 GB per matrix)",
+                   "parallelism": f"replicas x{world} (independent theta points per GPU)"},
+        "tflops": tflops, "tflops_unit": "nominal (2 F_fact + F_selinv) per step / step time",
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(p.theta0.shape[0] * 8),
+                "d2h_bytes_per_step": int(8 + 2 * p.N * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        from oracle import model as omodel
+        fd = omodel.fem_data(p)
+        th = thetas_h[args.warmup]
+        t0 = time.perf_counter()
+        oracle_step(p, th, fd)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                                "sample": "one step of the same workload (one theta) on the FP64 "
+                                          "numpy/scipy block recurrences"}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,255 @@
+/*
+ * bta.h -- C ABI of the GB300 (sm_103a) library for the block-tridiagonal-
+ * with-arrowhead (BTA) hot path of INLA on spatio-temporal (multivariate)
+ * Gaussian processes (arXiv 2507.06938, "DALIA").
+ *
+ * Each evaluation of the INLA objective f_obj(theta) (Eq. 8) needs the prior
+ * precision Q_p (Eq. 1, built from the SPDE / AR(1) / coregional model of
+ * Sections II-A, II-B and IV-B) and the conditional precision
+ * Q_c = Q_p + A^T D A (Eq. 4).  In the permuted order of Section IV-B.1 both
+ * are BTA matrices with n = nt diagonal blocks of size b = nv*ns and an arrow
+ * tip of size a = nv*nr, N = n*b + a (Section IV, structured-matrix table).
+ * This library assembles them, factors them by block Cholesky, and computes
+ * the log-determinant, the conditional-mean solve and the selected inverse
+ * (Section III-A), all in CUDA kernels on one GPU.
+ *
+ * Conventions
+ *  - Blocks are stored column-major in FP64, each block contiguous:
+ *      D_i = Q[i,i]      (b x b, i = 0..n-1)
+ *      B_i = Q[i+1,i]    (b x b, i = 0..n-2)
+ *      R_i = Q[tip,i]    (a x b, i = 0..n-1)
+ *      T   = Q[tip,tip]  (a x a)
+ *    The factor uses the same layout (only the lower triangle of D_i and T is
+ *    meaningful); the selected inverse Sigma = Q^{-1} restricted to the BTA
+ *    pattern also uses it (D_i and T stored full and symmetric).
+ *  - A vector of length N is ordered like the matrix: time block 0..n-1, each
+ *    holding variable-major spatial nodes (v*ns + s), then the nv*nr fixed
+ *    effects (v*nr + r).
+ *  - Every call is asynchronous on the context's stream unless stated.  Device
+ *    pointers passed in are borrowed: the caller owns them and keeps them
+ *    alive until the stream has passed the call.  Host pointers are read
+ *    before the call returns.
+ *  - Every function returns BTA_OK or an error code; no error is raised by a
+ *    device trap.  Errors found on the device (a non-positive pivot, a
+ *    non-finite result) are recorded in a status word of the context and
+ *    returned by bta_sync().
+ */
+#ifndef BTA_H
+#define BTA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define BTA_OK 0
+#define BTA_ERR_ARG 1        /* invalid argument (size, pointer, enum)          */
+#define BTA_ERR_OOM 2        /* device allocation failed                        */
+#define BTA_ERR_NOT_PD 3     /* non-positive pivot: matrix not positive definite
+                                (bta_last_info gives the global row index)      */
+#define BTA_ERR_TIMEOUT 4    /* a bounded device wait ran out                    */
+#define BTA_ERR_NONFINITE 5  /* NaN or Inf in an input or a result               */
+#define BTA_ERR_CUDA 6       /* a CUDA runtime call failed                       */
+#define BTA_ERR_STATE 7      /* call out of order (e.g. solve before factor)     */
+
+/* Which matrix of the pair. */
+#define BTA_QP 0             /* prior precision Q_p (Eq. 1)                      */
+#define BTA_QC 1             /* conditional precision Q_c = Q_p + A^T D A (Eq. 4) */
+
+/* Arithmetic of the factorisation / selected inversion. */
+#define BTA_FP64 0           /* every operation in FP64                          */
+#define BTA_MIXED 1          /* tensor-core split-precision Schur updates        */
+
+/* Block kinds for bta_block_ptr. */
+#define BTA_BLK_D 0
+#define BTA_BLK_B 1
+#define BTA_BLK_R 2
+#define BTA_BLK_T 3
+
+/* Storage selector for bta_block_ptr. */
+#define BTA_STORE_Q 0        /* the assembled matrix                             */
+#define BTA_STORE_L 1        /* its Cholesky factor                              */
+#define BTA_STORE_SIGMA 2    /* its selected inverse                             */
+#define BTA_STORE_LINV 3     /* inverses of the diagonal factor blocks (D, T)    */
+
+typedef struct bta_model_s* bta_model_t;
+typedef struct bta_ctx_s* bta_ctx_t;
+
+/*
+ * Model description (host arrays, read during bta_model_create only).
+ *  nv, ns, nt, nr  response variables, mesh nodes, time steps, fixed effects
+ *                  per variable (Section IV-B: N = nv (ns nt + nr)).
+ *  nodes           ns x 2 row-major node coordinates.
+ *  tri, n_tri      n_tri x 3 row-major node indices of the P1 triangles.
+ *  m               number of observations; for each k < m:
+ *  obs_var[k]      response variable (0..nv-1), obs_time[k] time step,
+ *  obs_xy[2k..]    location, obs_tri[k] triangle containing it,
+ *  X[k*nr + r]     covariate r (fixed effect r of variable obs_var[k]),
+ *  y[k]            observed value.
+ *  beta_prior_prec prior precision of every fixed effect before mixing.
+ *  theta0          prior mean of the hyperparameters (length
+ *                  4 nv + nv(nv-1)/2), used by the hyperprior of fobj_eval.
+ */
+typedef struct {
+    int nv, ns, nt, nr;
+    const double* nodes;
+    const int* tri;
+    int n_tri;
+    int m;
+    const int* obs_var;
+    const int* obs_time;
+    const double* obs_xy;
+    const int* obs_tri;
+    const double* X;
+    const double* y;
+    double beta_prior_prec;
+    const double* theta0;
+} bta_model_desc;
+
+/*
+ * bta_model_create -- theta-independent set-up (Sections II-A.1, II-A.2):
+ * P1 lumped mass C and stiffness G on the mesh, G C^{-1} G, barycentric
+ * interpolation of every observation, the per-(variable, time step) Gram
+ * matrices of the observation operator and A^T y, uploaded to the device.
+ * Synchronous.  Returns BTA_ERR_ARG for inconsistent sizes or indices.
+ * The model is owned by the library until bta_model_destroy.
+ */
+int bta_model_create(const bta_model_desc* desc, bta_model_t* out);
+int bta_model_destroy(bta_model_t model);
+/* Sizes of a model: n = nt, b = nv*ns, a = nv*nr, dim(theta). */
+int bta_model_dims(bta_model_t model, int* n, int* b, int* a, int* dim_theta);
+
+/*
+ * bta_create -- a context for BTA matrices with n diagonal blocks of size b
+ * and arrow tip a (n >= 1, b >= 1, a >= 0), the arithmetic `precision`
+ * (BTA_FP64 or BTA_MIXED) and the CUDA stream `stream` (a cudaStream_t; NULL
+ * = legacy default stream).  The context allocates and owns the device
+ * storage of Q_p and Q_c, their factors and inverse diagonal factor blocks;
+ * selected-inverse storage is allocated on the first bta_selinv of a matrix.
+ * Synchronous.  BTA_ERR_OOM if the device memory does not suffice.
+ */
+int bta_create(int n, int b, int a, int precision, void* stream, bta_ctx_t* out);
+int bta_destroy(bta_ctx_t ctx);
+
+/*
+ * bta_assemble -- write matrix `which` (BTA_QP or BTA_QC) of `model` into
+ * the context's Q storage for the model parameters `params_dev` (device
+ * array, layout [kappa, tau, rho, sigma, tau_eps] per variable followed by
+ * the nv(nv-1)/2 coregionalisation coefficients lambda):
+ *   Q_s^u = tau_u^2 (kappa_u^4 C + 2 kappa_u^2 G + G C^{-1} G)   (SPDE, II-A.1)
+ *   Q_t^u = stationary AR(1) precision with coefficient rho_u
+ *   Q^u   = blockdiag(Q_t^u (x) Q_s^u, beta_prior_prec I_nr)
+ *   Q_p   = Lambda^{-T} blockdiag(Q^u) Lambda^{-1}                 (Eq. 11)
+ *   Q_c   = Q_p + A^T D A                                         (Eq. 4)
+ * permuted to BTA order (Section IV-B.1).  Every entry of every block is
+ * written (zeros outside the sparsity pattern).
+ */
+int bta_assemble(bta_ctx_t ctx, bta_model_t model, const double* params_dev, int which);
+
+/* bta_theta_to_params -- device map theta -> params (layout above) of
+ * length 5 nv + nv(nv-1)/2: kappa = sqrt(8)/exp(theta_0), tau^2 =
+ * 1/(4 pi kappa^2), rho = exp(-1/exp(theta_1)), sigma = exp(theta_2),
+ * tau_eps = exp(theta_3) per variable; lambda copied. */
+int bta_theta_to_params(bta_ctx_t ctx, bta_model_t model, const double* theta_dev,
+                        double* params_dev);
+
+/*
+ * bta_factor -- block Cholesky Q = L L^T of matrix `which` (Section III-A):
+ * for i = 0..n-1: L_ii = chol(D_i), L_{i+1,i} = B_i L_ii^{-T},
+ * D_{i+1} -= L_{i+1,i} L_{i+1,i}^T, L_{t,i} = R_i L_ii^{-T},
+ * R_{i+1} -= L_{t,i} L_{i+1,i}^T, T -= L_{t,i} L_{t,i}^T; L_tt = chol(T).
+ * Also keeps L_ii^{-1} and L_tt^{-1}.  The assembled Q is left intact.
+ * A non-positive pivot records BTA_ERR_NOT_PD in the status word.
+ */
+int bta_factor(bta_ctx_t ctx, int which);
+
+/* bta_logdet -- log|Q| = 2 sum_k log L_kk of factored matrix `which`
+ * (Eq. 1), accumulated in FP64, written to the device scalar *out_dev. */
+int bta_logdet(bta_ctx_t ctx, int which, double* out_dev);
+
+/*
+ * bta_solve -- x = Q^{-1} rhs for factored matrix `which` by forward and
+ * backward block substitution (rhs_dev, x_dev: device vectors of length N;
+ * they may alias).  refine_iters >= 0 steps of iterative refinement
+ * x += Q^{-1}(rhs - Q x) with an FP64 residual on the assembled blocks.  If
+ * resid_dev is not NULL it receives ||rhs - Q x||_2 / ||rhs||_2.
+ */
+int bta_solve(bta_ctx_t ctx, int which, const double* rhs_dev, double* x_dev,
+              int refine_iters, double* resid_dev);
+
+/*
+ * bta_selinv -- selected inverse Sigma = Q^{-1} on the BTA pattern of
+ * factored matrix `which` (Section III-A, selected inversion):
+ * Sigma_tt = L_tt^{-T} L_tt^{-1}; for i = n-1..0 with G_i = L_{i+1,i} L_ii^{-1},
+ * F_i = L_{t,i} L_ii^{-1}:
+ *   Sigma_{i+1,i} = -Sigma_{i+1,i+1} G_i - Sigma_{t,i+1}^T F_i
+ *   Sigma_{t,i}   = -Sigma_{t,i+1} G_i - Sigma_tt F_i
+ *   Sigma_ii      = L_ii^{-T} L_ii^{-1} - Sigma_{i+1,i}^T G_i - Sigma_{t,i}^T F_i.
+ */
+int bta_selinv(bta_ctx_t ctx, int which);
+
+/* bta_selinv_diag -- gather the diagonal of the selected inverse of matrix
+ * `which` (the marginal variances of Section III, latent marginals) into
+ * the device vector out_dev of length N.  BTA_ERR_STATE before bta_selinv. */
+int bta_selinv_diag(bta_ctx_t ctx, int which, double* out_dev);
+
+/* bta_block_ptr -- device address of block (kind, i) of storage `store`
+ * of matrix `which`; *ld_out receives its leading dimension.  BTA_ERR_STATE
+ * if that storage does not exist yet. */
+int bta_block_ptr(bta_ctx_t ctx, int which, int store, int kind, int i,
+                  double** ptr_out, int* ld_out);
+
+/* bta_matvec -- y = Q x with the assembled blocks of matrix `which`
+ * (device vectors of length N, no aliasing). */
+int bta_matvec(bta_ctx_t ctx, int which, const double* x_dev, double* y_dev);
+
+/*
+ * fobj_eval -- f_obj(theta) of Eq. 8 for n_theta hyperparameter vectors
+ * (thetas_dev: device, n_theta x dim(theta) row-major), evaluated at the
+ * conditional mean x = mu with the hyperprior log p(theta) = sum_i
+ * log N(theta_i; theta0_i, 1):
+ *   f = log p(theta) + 1/2 log|Q_p| - 1/2 log|Q_c| - 1/2 (y^T D y - b^T mu)
+ *       + 1/2 sum_k log d_k - (m/2) log 2 pi,   b = A^T D y, mu = Q_c^{-1} b,
+ * which equals log p(theta) + log l(y|theta,mu) + log p(mu|theta)
+ * - log p_G(mu|theta,y) because y^T D y - b^T mu = (y - A mu)^T D (y - A mu)
+ * + mu^T Q_p mu.  f_out_dev receives n_theta values.  If mu_out_dev is not
+ * NULL it receives mu (length N) of the last theta.  The context's Q_p and
+ * Q_c hold the last theta's matrices and factors afterwards.
+ */
+int fobj_eval(bta_ctx_t ctx, bta_model_t model, const double* thetas_dev, int n_theta,
+              double* f_out_dev, double* mu_out_dev);
+
+/* bta_sync -- wait for the context's stream; return the first error the
+ * device recorded since the last bta_sync (and clear it), else BTA_OK. */
+int bta_sync(bta_ctx_t ctx);
+/* bta_last_info -- detail of the last device error: for BTA_ERR_NOT_PD the
+ * global row index (0..N-1) of the first non-positive pivot, else -1. */
+int bta_last_info(bta_ctx_t ctx, long long* info);
+/* bta_strerror -- static text of a return code. */
+const char* bta_strerror(int code);
+
+/* bta_launch_count -- number of CUDA kernels this library has launched in
+ * this process (host-side counter; all contexts). */
+long long bta_launch_count(void);
+
+/* bta_profile -- when enable != 0, record CUDA events around the two
+ * b x b x b Schur-update GEMM launches of every factorisation step of this
+ * context (counters reset).  bta_profile_read synchronises those events and
+ * returns their summed duration (ms), the number of timed launches and their
+ * nominal flops (b^3 each).  Measurement aid; no effect on results. */
+int bta_profile(bta_ctx_t ctx, int enable);
+int bta_profile_read(bta_ctx_t ctx, double* ms_total, long long* launches, double* flops_total);
+
+/* Nominal flop counts used for throughput figures: block Cholesky
+ * n b^3/3 + (n-1) 2 b^3 + n (a b^2 + a^2 b) + (n-1) 2 a b^2 + a^3/3 and
+ * selected inversion n 2 b^3/3 + (n-1) 5 b^3 + 6 n a b^2. */
+double bta_flops_factor(int n, int b, int a);
+double bta_flops_selinv(int n, int b, int a);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BTA_H */

@@ -1,0 +1,327 @@
+"""ctypes binding of libbta (include/bta.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library; this module turns torch CUDA
+tensors into device pointers, host arrays into C arrays, and return codes
+into exceptions.  There is no CPU fallback: if libbta.so is missing or a call
+fails, an exception is raised.
+
+Function names mirror the C ABI (bta_create, bta_assemble, bta_factor,
+bta_logdet, bta_solve, bta_selinv, fobj_eval, ...).  ``BtaModel`` and
+``BtaContext`` own the C handles and free them when collected.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libbta.so")
+_lib = None
+
+BTA_OK, BTA_ERR_ARG, BTA_ERR_OOM, BTA_ERR_NOT_PD = 0, 1, 2, 3
+BTA_ERR_TIMEOUT, BTA_ERR_NONFINITE, BTA_ERR_CUDA, BTA_ERR_STATE = 4, 5, 6, 7
+BTA_QP, BTA_QC = 0, 1
+BTA_FP64, BTA_MIXED = 0, 1
+BTA_BLK_D, BTA_BLK_B, BTA_BLK_R, BTA_BLK_T = 0, 1, 2, 3
+BTA_STORE_Q, BTA_STORE_L, BTA_STORE_SIGMA, BTA_STORE_LINV = 0, 1, 2, 3
+
+
+class BtaError(RuntimeError):
+    def __init__(self, code: int, where: str, info: int | None = None):
+        self.code = code
+        self.info = info
+        msg = f"{where}: {lib().bta_strerror(code).decode()} (code {code})"
+        if info is not None and info >= 0:
+            msg += f", info={info}"
+        super().__init__(msg)
+
+
+class _ModelDesc(C.Structure):
+    _fields_ = [
+        ("nv", C.c_int), ("ns", C.c_int), ("nt", C.c_int), ("nr", C.c_int),
+        ("nodes", C.POINTER(C.c_double)), ("tri", C.POINTER(C.c_int)), ("n_tri", C.c_int),
+        ("m", C.c_int), ("obs_var", C.POINTER(C.c_int)), ("obs_time", C.POINTER(C.c_int)),
+        ("obs_xy", C.POINTER(C.c_double)), ("obs_tri", C.POINTER(C.c_int)),
+        ("X", C.POINTER(C.c_double)), ("y", C.POINTER(C.c_double)),
+        ("beta_prior_prec", C.c_double), ("theta0", C.POINTER(C.c_double)),
+    ]
+
+
+def lib():
+    """Load libbta.so (built in-tree); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libbta.so not built ({_LIB_PATH}); run paper_2507_06938_gb300._build.build()")
+    L = C.CDLL(_LIB_PATH)
+    vp, ip, dp = C.c_void_p, C.c_int, C.c_double
+    sig = {
+        "bta_model_create": (ip, [C.POINTER(_ModelDesc), C.POINTER(vp)]),
+        "bta_model_destroy": (ip, [vp]),
+        "bta_model_dims": (ip, [vp, C.POINTER(ip), C.POINTER(ip), C.POINTER(ip), C.POINTER(ip)]),
+        "bta_create": (ip, [ip, ip, ip, ip, vp, C.POINTER(vp)]),
+        "bta_destroy": (ip, [vp]),
+        "bta_assemble": (ip, [vp, vp, vp, ip]),
+        "bta_theta_to_params": (ip, [vp, vp, vp, vp]),
+        "bta_factor": (ip, [vp, ip]),
+        "bta_logdet": (ip, [vp, ip, vp]),
+        "bta_solve": (ip, [vp, ip, vp, vp, ip, vp]),
+        "bta_selinv": (ip, [vp, ip]),
+        "bta_block_ptr": (ip, [vp, ip, ip, ip, ip, C.POINTER(vp), C.POINTER(ip)]),
+        "bta_matvec": (ip, [vp, ip, vp, vp]),
+        "fobj_eval": (ip, [vp, vp, vp, ip, vp, vp]),
+        "bta_sync": (ip, [vp]),
+        "bta_last_info": (ip, [vp, C.POINTER(C.c_longlong)]),
+        "bta_strerror": (C.c_char_p, [ip]),
+        "bta_selinv_diag": (ip, [vp, ip, vp]),
+        "bta_launch_count": (C.c_longlong, []),
+        "bta_profile": (ip, [vp, ip]),
+        "bta_profile_read": (ip, [vp, C.POINTER(dp), C.POINTER(C.c_longlong), C.POINTER(dp)]),
+        "bta_flops_factor": (dp, [ip, ip, ip]),
+        "bta_flops_selinv": (dp, [ip, ip, ip]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names the binding expects libbta.so to export."""
+    return ["bta_model_create", "bta_model_destroy", "bta_model_dims", "bta_create", "bta_destroy",
+            "bta_assemble", "bta_theta_to_params", "bta_factor", "bta_logdet", "bta_solve",
+            "bta_selinv", "bta_block_ptr", "bta_matvec", "fobj_eval", "bta_sync", "bta_last_info",
+            "bta_strerror", "bta_flops_factor", "bta_flops_selinv", "bta_selinv_diag",
+            "bta_launch_count", "bta_profile", "bta_profile_read"]
+
+
+def _check(code: int, where: str):
+    if code != BTA_OK:
+        raise BtaError(code, where)
+
+
+def _ptr(t) -> int:
+    """Device pointer of a contiguous CUDA float64 tensor (or None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 tensor")
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class _DevArray:
+    """__cuda_array_interface__ view of a raw device block (zero copy)."""
+
+    def __init__(self, ptr: int, rows: int, cols: int, ld: int):
+        self.__cuda_array_interface__ = {
+            "shape": (rows, cols), "typestr": "<f8", "data": (ptr, False),
+            "strides": (8, 8 * ld), "version": 3,
+        }
+
+
+# ----------------------------------------------------------------------------- model
+
+class BtaModel:
+    """bta_model_t built from a problem description (duck-typed: nv, ns, nt,
+    nr, nodes, tri, obs_var, obs_time, obs_xy, obs_tri, X, y, theta0,
+    beta_prior_prec)."""
+
+    def __init__(self, problem):
+        L = lib()
+        self._keep = []
+
+        def arr(a, dt, ct):
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._keep.append(a)
+            return a.ctypes.data_as(C.POINTER(ct))
+
+        d = _ModelDesc()
+        d.nv, d.ns, d.nt, d.nr = problem.nv, problem.ns, problem.nt, problem.nr
+        d.nodes = arr(problem.nodes, np.float64, C.c_double)
+        d.tri = arr(problem.tri, np.int32, C.c_int)
+        d.n_tri = int(problem.tri.shape[0])
+        d.m = int(problem.y.shape[0])
+        d.obs_var = arr(problem.obs_var, np.int32, C.c_int)
+        d.obs_time = arr(problem.obs_time, np.int32, C.c_int)
+        d.obs_xy = arr(problem.obs_xy, np.float64, C.c_double)
+        d.obs_tri = arr(problem.obs_tri, np.int32, C.c_int)
+        d.X = arr(problem.X, np.float64, C.c_double)
+        d.y = arr(problem.y, np.float64, C.c_double)
+        d.beta_prior_prec = float(problem.beta_prior_prec)
+        d.theta0 = arr(problem.theta0, np.float64, C.c_double)
+        h = C.c_void_p()
+        _check(L.bta_model_create(C.byref(d), C.byref(h)), "bta_model_create")
+        self._keep = []
+        self.handle = h
+        n, b, a, dt = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(L.bta_model_dims(h, C.byref(n), C.byref(b), C.byref(a), C.byref(dt)), "bta_model_dims")
+        self.n, self.b, self.a, self.dim_theta = n.value, b.value, a.value, dt.value
+        self.N = self.n * self.b + self.a
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bta_model_destroy(self.handle)
+            self.handle = None
+
+
+# ----------------------------------------------------------------------------- context
+
+class BtaContext:
+    """bta_ctx_t: device storage of Q_p and Q_c, their factors and selected
+    inverses, bound to a CUDA stream."""
+
+    def __init__(self, n: int, b: int, a: int, precision: int = BTA_FP64, stream=None):
+        L = lib()
+        self._stream_obj = stream
+        h = C.c_void_p()
+        _check(L.bta_create(n, b, a, precision, C.c_void_p(_stream_handle(stream)), C.byref(h)), "bta_create")
+        self.handle = h
+        self.n, self.b, self.a = n, b, a
+        self.N = n * b + a
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bta_destroy(self.handle)
+            self.handle = None
+
+    # -- the C ABI, one method per entry point
+    def assemble(self, model: BtaModel, params, which: int):
+        _check(lib().bta_assemble(self.handle, model.handle, _ptr(params), which), "bta_assemble")
+
+    def theta_to_params(self, model: BtaModel, theta, params):
+        _check(lib().bta_theta_to_params(self.handle, model.handle, _ptr(theta), _ptr(params)),
+               "bta_theta_to_params")
+
+    def factor(self, which: int):
+        _check(lib().bta_factor(self.handle, which), "bta_factor")
+
+    def logdet(self, which: int, out):
+        _check(lib().bta_logdet(self.handle, which, _ptr(out)), "bta_logdet")
+
+    def solve(self, which: int, rhs, x, refine_iters: int = 0, resid=None):
+        _check(lib().bta_solve(self.handle, which, _ptr(rhs), _ptr(x), refine_iters, _ptr(resid)), "bta_solve")
+
+    def selinv(self, which: int):
+        _check(lib().bta_selinv(self.handle, which), "bta_selinv")
+
+    def matvec(self, which: int, x, y):
+        _check(lib().bta_matvec(self.handle, which, _ptr(x), _ptr(y)), "bta_matvec")
+
+    def fobj_eval(self, model: BtaModel, thetas, f_out, mu_out=None):
+        n_theta = int(thetas.shape[0]) if thetas.dim() == 2 else 1
+        _check(lib().fobj_eval(self.handle, model.handle, _ptr(thetas), n_theta, _ptr(f_out), _ptr(mu_out)),
+               "fobj_eval")
+
+    def selinv_diag(self, which: int, out):
+        _check(lib().bta_selinv_diag(self.handle, which, _ptr(out)), "bta_selinv_diag")
+
+    def profile(self, enable: bool):
+        _check(lib().bta_profile(self.handle, 1 if enable else 0), "bta_profile")
+
+    def profile_read(self):
+        ms, n, fl = C.c_double(), C.c_longlong(), C.c_double()
+        _check(lib().bta_profile_read(self.handle, C.byref(ms), C.byref(n), C.byref(fl)), "bta_profile_read")
+        return ms.value, n.value, fl.value
+
+    def sync(self):
+        code = lib().bta_sync(self.handle)
+        if code != BTA_OK:
+            info = C.c_longlong()
+            lib().bta_last_info(self.handle, C.byref(info))
+            raise BtaError(code, "bta_sync", info.value)
+
+    def block(self, which: int, store: int, kind: int, i: int = 0):
+        """Zero-copy torch view of one stored block (rows x cols, column-major)."""
+        import torch
+        p = C.c_void_p()
+        ld = C.c_int()
+        _check(lib().bta_block_ptr(self.handle, which, store, kind, i, C.byref(p), C.byref(ld)),
+               "bta_block_ptr")
+        rows = self.a if kind in (BTA_BLK_R, BTA_BLK_T) else self.b
+        cols = self.a if kind == BTA_BLK_T else self.b
+        return torch.as_tensor(_DevArray(p.value, rows, cols, ld.value), device="cuda")
+
+
+# ----------------------------------------------------------------------------- flat C-ABI names
+
+def bta_model_create(problem) -> BtaModel:
+    return BtaModel(problem)
+
+
+def bta_create(n, b, a, precision=BTA_FP64, stream=None) -> BtaContext:
+    return BtaContext(n, b, a, precision, stream)
+
+
+def bta_assemble(ctx: BtaContext, model: BtaModel, params, which: int):
+    ctx.assemble(model, params, which)
+
+
+def bta_theta_to_params(ctx: BtaContext, model: BtaModel, theta, params):
+    ctx.theta_to_params(model, theta, params)
+
+
+def bta_factor(ctx: BtaContext, which: int):
+    ctx.factor(which)
+
+
+def bta_logdet(ctx: BtaContext, which: int, out):
+    ctx.logdet(which, out)
+
+
+def bta_solve(ctx: BtaContext, which: int, rhs, x, refine_iters: int = 0, resid=None):
+    ctx.solve(which, rhs, x, refine_iters, resid)
+
+
+def bta_selinv(ctx: BtaContext, which: int):
+    ctx.selinv(which)
+
+
+def bta_matvec(ctx: BtaContext, which: int, x, y):
+    ctx.matvec(which, x, y)
+
+
+def fobj_eval(ctx: BtaContext, model: BtaModel, thetas, f_out, mu_out=None):
+    ctx.fobj_eval(model, thetas, f_out, mu_out)
+
+
+def bta_sync(ctx: BtaContext):
+    ctx.sync()
+
+
+def bta_selinv_diag(ctx: BtaContext, which: int, out):
+    ctx.selinv_diag(which, out)
+
+
+def bta_launch_count() -> int:
+    return lib().bta_launch_count()
+
+
+def bta_profile(ctx: BtaContext, enable: bool):
+    ctx.profile(enable)
+
+
+def bta_profile_read(ctx: BtaContext):
+    return ctx.profile_read()
+
+
+def bta_flops_factor(n: int, b: int, a: int) -> float:
+    return lib().bta_flops_factor(n, b, a)
+
+
+def bta_flops_selinv(n: int, b: int, a: int) -> float:
+    return lib().bta_flops_selinv(n, b, a)

@@ -1,0 +1,491 @@
+// FP64 dense building blocks of the BTA factorisation, solve and selected
+// inversion: a tiled DFMA GEMM with triangular-operand and lower-output
+// variants, the recursive diagonal-block Cholesky + inverse, matrix copies,
+// GEMV and deterministic reductions.  On GB300 the FP64 pipe (measured about
+// 1.2 TFLOP/s for DFMA, below DMMA's 1.05) bounds all of these except the
+// GEMV and copies, which are bound by HBM.
+
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------- GEMM
+// Tile (16 MI) x (16 NJ) x 16 per CTA of 256 threads; thread (tx, ty),
+// tx = tid % 16 along m, ty = tid / 16 along n, owns rows m0 + tx + 16 i and
+// columns n0 + ty + 16 j.  Column-major output: lanes write consecutive rows.
+// blockIdx.z is the batch index, or the K split when ksplit > 1 (then every
+// split atomically adds alpha * partial into a C that already holds beta Cin).
+constexpr int BK = 16, GT = 256;
+
+__device__ __forceinline__ double load_opA(const Gemm64& p, const double* A, int m, int k, int kend) {
+    if (m >= p.M || k >= kend) return 0.0;
+    if (p.shA == 1 && k > m) return 0.0;
+    if (p.shA == 2 && k < m) return 0.0;
+    return p.ta ? A[k + (long long)m * p.lda] : A[m + (long long)k * p.lda];
+}
+
+__device__ __forceinline__ double load_opB(const Gemm64& p, const double* B, int k, int nn, int kend) {
+    if (nn >= p.N || k >= kend) return 0.0;
+    if (p.shB == 1 && nn > k) return 0.0;
+    if (p.shB == 2 && nn < k) return 0.0;
+    return p.tb ? B[nn + (long long)k * p.ldb] : B[k + (long long)nn * p.ldb];
+}
+
+template <int MI, int NJ>
+__global__ void __launch_bounds__(GT) gemm64_kernel(Gemm64 p, int ksplit) {
+    constexpr int TBM = 16 * MI, TBN = 16 * NJ;
+    __shared__ double As[BK][TBM + 1];
+    __shared__ double Bs[BK][TBN + 1];
+    const int m0 = blockIdx.x * TBM, n0 = blockIdx.y * TBN;
+    if (p.lowerC && m0 + TBM - 1 < n0) return;
+    const int z = ksplit > 1 ? 0 : blockIdx.z;
+    const double* A = p.A + z * p.sA;
+    const double* B = p.B + z * p.sB;
+    const double* Cin = p.Cin ? p.Cin + z * p.sCi : nullptr;
+    double* C = p.C + z * p.sC;
+    int kb = 0, ke = p.K;
+    if (p.shA == 1) ke = min(ke, m0 + TBM);
+    if (p.shA == 2) kb = max(kb, m0);
+    if (p.shB == 1) kb = max(kb, n0);
+    if (p.shB == 2) ke = min(ke, n0 + TBN);
+    kb = (kb / BK) * BK;
+    if (ksplit > 1) {
+        // split [kb, ke) into ksplit chunks of whole BK tiles
+        const int tiles = (ke - kb + BK - 1) / BK;
+        const int per = (tiles + ksplit - 1) / ksplit;
+        const int s0 = kb + blockIdx.z * per * BK;
+        const int s1 = min(ke, s0 + per * BK);
+        kb = s0;
+        ke = s1;
+        if (kb >= ke) return;
+    }
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    double acc[MI][NJ];
+#pragma unroll
+    for (int i = 0; i < MI; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) acc[i][j] = 0.0;
+
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        // op(A) tile TBM x BK: lanes along the contiguous stored dimension
+        for (int e = tid; e < TBM * BK; e += GT) {
+            int mm, kk;
+            if (!p.ta) { mm = e % TBM; kk = e / TBM; } else { kk = e % BK; mm = e / BK; }
+            As[kk][mm] = load_opA(p, A, m0 + mm, k0 + kk, ke);
+        }
+        for (int e = tid; e < TBN * BK; e += GT) {
+            int nn, kk;
+            if (!p.tb) { kk = e % BK; nn = e / BK; } else { nn = e % TBN; kk = e / TBN; }
+            Bs[kk][nn] = load_opB(p, B, k0 + kk, n0 + nn, ke);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[MI], b[NJ];
+#pragma unroll
+            for (int i = 0; i < MI; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < MI; ++i)
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int nn = n0 + ty + 16 * j;
+        if (nn >= p.N) continue;
+#pragma unroll
+        for (int i = 0; i < MI; ++i) {
+            const int mm = m0 + tx + 16 * i;
+            if (mm >= p.M) continue;
+            if (p.lowerC && mm < nn) continue;
+            double* c = C + mm + (long long)nn * p.ldc;
+            if (ksplit > 1) {
+                atomicAdd(c, p.alpha * acc[i][j]);
+            } else {
+                double v = p.alpha * acc[i][j];
+                if (p.beta != 0.0) v += p.beta * Cin[mm + (long long)nn * p.ldci];
+                *c = v;
+            }
+        }
+    }
+}
+
+// C = beta Cin (entries m >= n only when lower), the start of a split-K GEMM.
+__global__ void scale_into_kernel(int M, int N, const double* Cin, long long ldci, double beta, double* C,
+                                  long long ldc, int lower, int batch, long long sCi, long long sC) {
+    const long long total = (long long)M * N * batch;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long z = e / ((long long)M * N);
+        const long long r = e - z * M * N;
+        const int i = (int)(r % M), j = (int)(r / M);
+        if (lower && i < j) continue;
+        C[z * sC + i + j * ldc] = (beta != 0.0 && Cin) ? beta * Cin[z * sCi + i + j * ldci] : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------- leaf Cholesky + inverse
+// One CTA factors an n x n (n <= 64) lower block A = L L^T in shared memory and
+// forms X = L^{-1} by right-looking forward elimination of L X = I.  Iteration
+// k updates the trailing matrix with column k and eliminates with column k-1
+// of L, so each iteration needs a single barrier.  Output: L and X (lower; the
+// strict upper parts of both tiles are written as zeros).
+constexpr int LEAF_MAX = 64;
+constexpr int LDS = LEAF_MAX + 1;
+
+__global__ void __launch_bounds__(256) chol_inv_leaf_kernel(double* A, long long lda, double* X,
+                                                            long long ldx, int n, long long row0,
+                                                            long long* status) {
+    extern __shared__ double sm[];
+    double* S = sm;                 // working matrix, column-major, ld LDS
+    double* L = sm + LDS * LEAF_MAX;
+    double* W = sm + 2 * LDS * LEAF_MAX;
+    const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
+    for (int e = tid; e < n * n; e += nthr) {
+        int i = e % n, j = e / n;
+        S[j * LDS + i] = (i >= j) ? A[i + (long long)j * lda] : 0.0;
+        W[j * LDS + i] = (i == j) ? 1.0 : 0.0;
+        L[j * LDS + i] = 0.0;
+    }
+    const int rows_per = n <= 32 ? 32 : LEAF_MAX;
+    const int row = tid % rows_per;      // row handled by this thread
+    const int lane_q = tid / rows_per;   // column phase
+    const int nq = nthr / rows_per;
+    for (int k = 0; k <= n; ++k) {
+        __syncthreads();
+        if (k < n) {
+            const double dkk = S[k * LDS + k];
+            if (tid == 0 && !(dkk > 0.0) && status) {
+                if (atomicCAS((unsigned long long*)status, 0ull, (unsigned long long)BTA_ERR_NOT_PD) == 0ull)
+                    status[1] = row0 + k;
+            }
+            const double rk = dkk > 0.0 ? sqrt(dkk) : nan("");
+            const double rinv = 1.0 / rk;
+            const double dinv = rinv * rinv;
+            if (row >= k && row < n && lane_q == 0) L[k * LDS + row] = S[k * LDS + row] * rinv;
+            if (row > k && row < n) {
+                const double sik = S[k * LDS + row] * dinv;
+                for (int j = k + 1 + lane_q; j <= row; j += nq) S[j * LDS + row] -= sik * S[k * LDS + j];
+            }
+        }
+        if (k > 0) {
+            const int c = k - 1;   // eliminate with column c of L (complete since iteration c)
+            const double lcc = L[c * LDS + c];
+            if (row > c && row < n) {
+                const double f = L[c * LDS + row] / lcc;
+                for (int j = lane_q; j <= c; j += nq) W[j * LDS + row] -= f * W[j * LDS + c];
+            }
+            // row c of X is final: W[c][:] / L[c][c]
+            if (tid <= c) X[c + (long long)tid * ldx] = W[tid * LDS + c] / lcc;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += nthr) {
+        int i = e % n, j = e / n;
+        A[i + (long long)j * lda] = (i >= j) ? L[j * LDS + i] : 0.0;
+        if (i < j) X[i + (long long)j * ldx] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------- copies
+__global__ void copy_mat_kernel(const double* src, long long lds, double* dst, long long ldd, int rows,
+                                int cols, int lower_only) {
+    const long long total = (long long)rows * cols;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(e % rows), j = (int)(e / rows);
+        if (lower_only && i < j) continue;
+        dst[i + j * ldd] = src[i + j * lds];
+    }
+}
+
+__global__ void symmetrize_kernel(double* A, long long lda, int n) {
+    const long long total = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int i = (int)(e % n), j = (int)(e / n);
+        if (i < j) A[i + j * lda] = A[j + i * lda];
+    }
+}
+
+// ---------------------------------------------------------------- GEMV
+// y[m] = alpha sum_n op(A)[m][n] x[n] + beta yin[m]
+// Non-transposed: a CTA owns 32 rows; 8 warps split the columns; lanes read
+// consecutive rows (coalesced).  Transposed: a warp owns one output, lanes
+// stride down the stored column (coalesced), shuffle reduction.
+__global__ void __launch_bounds__(256) gemv_n_kernel(int M, int N, const double* A, long long lda, int sh,
+                                                     const double* x, double alpha, const double* yin,
+                                                     double beta, double* y, long long sA, long long sx,
+                                                     long long sy) {
+    __shared__ double part[8][33];
+    A += blockIdx.y * sA;
+    x += blockIdx.y * sx;
+    y += blockIdx.y * sy;
+    if (yin) yin += blockIdx.y * sy;
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    const int m = blockIdx.x * 32 + lane;
+    double acc = 0.0;
+    if (m < M) {
+        int nb = 0, ne = N;
+        if (sh == 1) ne = min(N, m + 1);
+        if (sh == 2) nb = m;
+        for (int n = nb + w; n < ne; n += 8) acc = fma(A[m + (long long)n * lda], x[n], acc);
+    }
+    part[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && m < M) {
+        double s = 0.0;
+        for (int q = 0; q < 8; ++q) s += part[q][lane];
+        double v = alpha * s;
+        if (beta != 0.0) v += beta * yin[m];
+        y[m] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) gemv_t_kernel(int M, int N, const double* A, long long lda, int sh,
+                                                     const double* x, double alpha, const double* yin,
+                                                     double beta, double* y, long long sA, long long sx,
+                                                     long long sy) {
+    A += blockIdx.y * sA;
+    x += blockIdx.y * sx;
+    y += blockIdx.y * sy;
+    if (yin) yin += blockIdx.y * sy;
+    // op(A) = A^T: op(A)[m][n] = A[n + m*lda], op(A) is M x N, A stored N x M.
+    const int lane = threadIdx.x % 32;
+    const int m = blockIdx.x * 8 + threadIdx.x / 32;
+    if (m >= M) return;
+    int nb = 0, ne = N;
+    if (sh == 1) ne = min(N, m + 1);
+    if (sh == 2) nb = m;
+    const double* col = A + (long long)m * lda;
+    double acc = 0.0;
+    for (int n = nb + lane; n < ne; n += 32) acc = fma(col[n], x[n], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        double v = alpha * acc;
+        if (beta != 0.0) v += beta * yin[m];
+        y[m] = v;
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (w == 0) {
+        s = (lane < (int)(blockDim.x / 32)) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;
+}
+
+__global__ void logdiag_partial_kernel(const double* A, long long lda, int dim, int count, long long stride,
+                                       double* partial) {
+    const long long total = (long long)dim * count;
+    double acc = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int blk = (int)(e / dim), k = (int)(e % dim);
+        acc += log(A[blk * stride + k * (lda + 1)]);
+    }
+    double s = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void dot_partial_kernel(const double* x, const double* y, long long len, double* partial) {
+    double acc = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+         e += (long long)gridDim.x * blockDim.x)
+        acc = fma(x[e], y[e], acc);
+    double s = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void finish_sum_kernel(const double* partial, int len, double* out, double scale, int accumulate) {
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < len; e += blockDim.x) acc += partial[e];
+    double s = block_sum(acc);
+    if (threadIdx.x == 0) *out = (accumulate ? *out : 0.0) + scale * s;
+}
+
+}  // namespace
+
+// ==================================================================== host launchers
+int gemm64(cudaStream_t s, const Gemm64& g) {
+    if (g.M <= 0 || g.N <= 0) return BTA_OK;
+    // micro-tile shape: thin outputs get thin tiles so that no DFMA is spent
+    // on padding rows/columns
+    int MI = g.M <= 16 ? 1 : (g.M <= 32 ? 2 : 4);
+    int NJ = g.N <= 16 ? 1 : (g.N <= 32 ? 2 : 4);
+    const int TBM = 16 * MI, TBN = 16 * NJ;
+    const int gm = (g.M + TBM - 1) / TBM, gn = (g.N + TBN - 1) / TBN;
+    long long tiles = (long long)gm * gn;
+    if (g.lowerC) tiles = (tiles + gm) / 2;
+    // the FP64 pipe of one SM is slow: split K until about two CTAs per SM
+    int ksplit = 1;
+    if (g.batch == 1 && g.K > 4 * BK) {
+        const long long want = 2LL * 152;
+        if (tiles < want) {
+            ksplit = (int)std::min<long long>((want + tiles - 1) / tiles, (g.K + 4 * BK - 1) / (4 * BK));
+            ksplit = std::max(1, std::min(ksplit, 64));
+        }
+    }
+    if (ksplit > 1) {
+        const bool inplace = (g.Cin == g.C && g.ldci == g.ldc && g.beta == 1.0);
+        if (!inplace) {
+            long long total = (long long)g.M * g.N;
+            int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
+            scale_into_kernel<<<blocks, 256, 0, s>>>(g.M, g.N, g.Cin, g.ldci, g.beta, g.C, g.ldc, g.lowerC,
+                                                     1, 0, 0);
+            BTA_LAUNCH_CHECK();
+        }
+    }
+    dim3 grid(gm, gn, ksplit > 1 ? ksplit : g.batch);
+#define BTA_GEMM_CASE(mi, nj) \
+    if (MI == mi && NJ == nj) gemm64_kernel<mi, nj><<<grid, GT, 0, s>>>(g, ksplit);
+    BTA_GEMM_CASE(1, 1) BTA_GEMM_CASE(1, 2) BTA_GEMM_CASE(1, 4)
+    BTA_GEMM_CASE(2, 1) BTA_GEMM_CASE(2, 2) BTA_GEMM_CASE(2, 4)
+    BTA_GEMM_CASE(4, 1) BTA_GEMM_CASE(4, 2) BTA_GEMM_CASE(4, 4)
+#undef BTA_GEMM_CASE
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}
+
+static int leaf_launch(cudaStream_t s, double* A, long long lda, double* X, long long ldx, int n,
+                       long long row0, long long* status) {
+    static bool attr_set = false;
+    const size_t smem = 3 * LDS * LEAF_MAX * sizeof(double);
+    if (!attr_set) {
+        BTA_CUDA_TRY(cudaFuncSetAttribute(chol_inv_leaf_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    const int threads = n <= 32 ? 128 : 256;
+    chol_inv_leaf_kernel<<<1, threads, smem, s>>>(A, lda, X, ldx, n, row0, status);
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}
+
+// Recursive Cholesky + inverse of the lower n x n matrix at A (in place) into
+// X (lower).  W: scratch of at least ceil(n/2)^2 doubles.
+//   [A11      ]   L11 = chol(A11), X11 = L11^{-1}
+//   [A21  A22 ]   L21 = A21 X11^T, A22 -= L21 L21^T, L22 = chol(A22), X22 = L22^{-1}
+//                 X21 = -X22 (L21 X11)
+int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ldx, int n, long long row0,
+               long long* status, double* W, int leaf) {
+    if (n <= 0) return BTA_OK;
+    leaf = std::max(8, std::min(leaf, LEAF_MAX));
+    if (n <= leaf) return leaf_launch(s, A, lda, X, ldx, n, row0, status);
+    const int half = (n + 1) / 2;
+    int n1 = ((half + leaf - 1) / leaf) * leaf;
+    if (n1 >= n) n1 = leaf;
+    const int n2 = n - n1;
+    double* A11 = A;
+    double* A21 = A + n1;
+    double* A22 = A + n1 + n1 * lda;
+    double* X11 = X;
+    double* X21 = X + n1;
+    double* X22 = X + n1 + n1 * ldx;
+    BTA_TRY(chol_inv64(s, A11, lda, X11, ldx, n1, row0, status, W, leaf));
+    Gemm64 g{};
+    // W (n2 x n1) = A21 * X11^T      (op(B) upper)
+    g = Gemm64{};
+    g.M = n2; g.N = n1; g.K = n1;
+    g.A = A21; g.lda = lda; g.ta = 0; g.shA = 0;
+    g.B = X11; g.ldb = ldx; g.tb = 1; g.shB = 2;
+    g.C = W; g.ldc = n2; g.alpha = 1.0; g.beta = 0.0;
+    BTA_TRY(gemm64(s, g));
+    BTA_TRY(copy_mat64(s, W, n2, A21, lda, n2, n1, 0));
+    // A22 -= L21 L21^T  (lower)
+    g = Gemm64{};
+    g.M = n2; g.N = n2; g.K = n1;
+    g.A = A21; g.lda = lda; g.ta = 0;
+    g.B = A21; g.ldb = lda; g.tb = 1;
+    g.Cin = A22; g.ldci = lda; g.beta = 1.0;
+    g.C = A22; g.ldc = lda; g.alpha = -1.0; g.lowerC = 1;
+    BTA_TRY(gemm64(s, g));
+    BTA_TRY(chol_inv64(s, A22, lda, X22, ldx, n2, row0 + n1, status, W, leaf));
+    // W = L21 * X11   (op(B) lower)
+    g = Gemm64{};
+    g.M = n2; g.N = n1; g.K = n1;
+    g.A = A21; g.lda = lda;
+    g.B = X11; g.ldb = ldx; g.tb = 0; g.shB = 1;
+    g.C = W; g.ldc = n2; g.alpha = 1.0; g.beta = 0.0;
+    BTA_TRY(gemm64(s, g));
+    // X21 = -X22 * W   (op(A) lower)
+    g = Gemm64{};
+    g.M = n2; g.N = n1; g.K = n2;
+    g.A = X22; g.lda = ldx; g.ta = 0; g.shA = 1;
+    g.B = W; g.ldb = n2; g.tb = 0;
+    g.C = X21; g.ldc = ldx; g.alpha = -1.0; g.beta = 0.0;
+    BTA_TRY(gemm64(s, g));
+    return BTA_OK;
+}
+
+int copy_mat64(cudaStream_t s, const double* src, long long lds, double* dst, long long ldd, int rows,
+               int cols, int lower_only) {
+    long long total = (long long)rows * cols;
+    if (total <= 0) return BTA_OK;
+    int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
+    copy_mat_kernel<<<blocks, 256, 0, s>>>(src, lds, dst, ldd, rows, cols, lower_only);
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}
+
+int symmetrize_lower64(cudaStream_t s, double* A, long long lda, int n) {
+    long long total = (long long)n * n;
+    if (total <= 0) return BTA_OK;
+    int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
+    symmetrize_kernel<<<blocks, 256, 0, s>>>(A, lda, n);
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}
+
+int gemv64(cudaStream_t s, int M, int N, const double* A, long long lda, int ta, int sh, const double* x,
+           double alpha, const double* yin, double beta, double* y, int batch, long long sA, long long sx,
+           long long sy) {
+    if (M <= 0 || batch <= 0) return BTA_OK;
+    if (!ta) {
+        dim3 grid((M + 31) / 32, batch);
+        gemv_n_kernel<<<grid, 256, 0, s>>>(M, N, A, lda, sh, x, alpha, yin, beta, y, sA, sx, sy);
+    } else {
+        dim3 grid((M + 7) / 8, batch);
+        gemv_t_kernel<<<grid, 256, 0, s>>>(M, N, A, lda, sh, x, alpha, yin, beta, y, sA, sx, sy);
+    }
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}
+
+int logdiag_sum64(cudaStream_t s, const double* A, long long lda, int dim, int count, long long stride,
+                  double* partial, int partial_len, double* out, double scale, int accumulate) {
+    long long total = (long long)dim * count;
+    int blocks = (int)std::min<long long>(std::max<long long>(1, (total + 255) / 256), partial_len);
+    logdiag_partial_kernel<<<blocks, 256, 0, s>>>(A, lda, dim, count, stride, partial);
+    BTA_LAUNCH_CHECK();
+    finish_sum_kernel<<<1, 256, 0, s>>>(partial, blocks, out, scale, accumulate);
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}
+
+int dot64(cudaStream_t s, const double* x, const double* y, long long len, double* partial, int partial_len,
+          double* out) {
+    int blocks = (int)std::min<long long>(std::max<long long>(1, (len + 255) / 256), partial_len);
+    dot_partial_kernel<<<blocks, 256, 0, s>>>(x, y, len, partial);
+    BTA_LAUNCH_CHECK();
+    finish_sum_kernel<<<1, 256, 0, s>>>(partial, blocks, out, 1.0, 0);
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}
