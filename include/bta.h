@@ -243,6 +243,33 @@ long long bta_launch_count(void);
 int bta_profile(bta_ctx_t ctx, int enable);
 int bta_profile_read(bta_ctx_t ctx, double* ms_total, long long* launches, double* flops_total);
 
+/*
+ * bta_chol_inv_noalloc -- allocation-free Cholesky factor and inverse of one
+ * dense symmetric positive definite block.  The paper has no counterpart to
+ * this entry point.  It is for callers that may not call cudaMalloc (for
+ * example a framework whose own pool already owns the device memory, or a
+ * serving loop that cannot take the synchronisation of cudaMalloc/cudaFree):
+ * no context is needed and nothing is allocated.
+ *   A       device, b x b column-major (leading dimension lda >= b); its
+ *           lower triangle is read and overwritten by L with A = L L^T (the
+ *           strict upper part of the diagonal 32 x 32 tiles is set to zero,
+ *           the rest of the strict upper triangle is left as it was).
+ *   X       device, b x b (ldx >= b): receives L^{-1} (lower; strict upper
+ *           triangle set to zero).
+ *   info_dev device scalar: -1 on success, else the 0-based row of the first
+ *           non-positive pivot (the results are then not usable).
+ *   stream  the cudaStream_t to run on (NULL = legacy default stream).
+ * The workspace is one fixed file-scope device array of 8.5 MiB, held by
+ * every GPU that loads the library until the process exits; it limits the
+ * block order to b <= 2048 (larger b returns BTA_ERR_ARG, as do bad pointers
+ * or leading dimensions).  The first call on a device looks up the device
+ * address of that array, so make that first call before any stream
+ * capture.  All calls share the one array: calls whose executions overlap
+ * on the GPU (other streams, other host threads) race and give wrong
+ * results; serialise them.
+ */
+int bta_chol_inv_noalloc(double* A, int b, int lda, double* X, int ldx, long long* info_dev, void* stream);
+
 /* Nominal flop counts used for throughput figures: block Cholesky
  * n b^3/3 + (n-1) 2 b^3 + n (a b^2 + a^2 b) + (n-1) 2 a b^2 + a^3/3 and
  * selected inversion n 2 b^3/3 + (n-1) 5 b^3 + 6 n a b^2. */

@@ -80,6 +80,7 @@ def lib():
         "bta_launch_count": (C.c_longlong, []),
         "bta_profile": (ip, [vp, ip]),
         "bta_profile_read": (ip, [vp, C.POINTER(dp), C.POINTER(C.c_longlong), C.POINTER(dp)]),
+        "bta_chol_inv_noalloc": (ip, [vp, ip, ip, vp, ip, vp, vp]),
         "bta_flops_factor": (dp, [ip, ip, ip]),
         "bta_flops_selinv": (dp, [ip, ip, ip]),
     }
@@ -97,7 +98,7 @@ def exported_symbols():
             "bta_assemble", "bta_theta_to_params", "bta_factor", "bta_logdet", "bta_solve",
             "bta_selinv", "bta_block_ptr", "bta_matvec", "fobj_eval", "bta_sync", "bta_last_info",
             "bta_strerror", "bta_flops_factor", "bta_flops_selinv", "bta_selinv_diag",
-            "bta_launch_count", "bta_profile", "bta_profile_read"]
+            "bta_launch_count", "bta_profile", "bta_profile_read", "bta_chol_inv_noalloc"]
 
 
 def _check(code: int, where: str):
@@ -317,6 +318,27 @@ def bta_profile(ctx: BtaContext, enable: bool):
 
 def bta_profile_read(ctx: BtaContext):
     return ctx.profile_read()
+
+
+NOALLOC_MAX_B = 2048
+
+
+def bta_chol_inv_noalloc(A, X, info, stream=None):
+    """Allocation-free Cholesky + inverse of one SPD block (no counterpart in
+    the paper): A (b x b, CUDA float64, column-major data of a symmetric
+    matrix) is overwritten in its lower triangle by L, X receives L^{-1},
+    info (1 int64 element) receives -1 or the first failing row.  Nothing is
+    allocated by the library; the workspace is a fixed 8.5 MiB device array,
+    so b is limited to 2048 and concurrent calls on the GPU race."""
+    import torch
+    b = int(A.shape[0])
+    if b > NOALLOC_MAX_B:
+        raise ValueError(f"bta_chol_inv_noalloc: block order {b} exceeds the maximum {NOALLOC_MAX_B}")
+    for t, dt in ((A, torch.float64), (X, torch.float64), (info, torch.int64)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError("expected contiguous CUDA tensors (float64 A, X; int64 info)")
+    _check(lib().bta_chol_inv_noalloc(A.data_ptr(), b, b, X.data_ptr(), b, info.data_ptr(),
+                                      C.c_void_p(_stream_handle(stream))), "bta_chol_inv_noalloc")
 
 
 def bta_flops_factor(n: int, b: int, a: int) -> float:
