@@ -117,6 +117,12 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
                long long row0, long long* status, double* W, int leaf);
 int copy_mat64(cudaStream_t s, const double* src, long long lds, double* dst, long long ldd,
                int rows, int cols, int lower_only);
+// C = beta Cin (C = 0 if beta == 0); only entries m >= n when lower
+int scale_into64(cudaStream_t s, int M, int N, const double* Cin, long long ldci, double beta, double* C,
+                 long long ldc, int lower);
+// Digit-split tensor-core GEMM (ozaki.cu): same contract as gemm64 (batch 1).
+size_t ozaki_workspace_bytes(int M, int N, int K);
+int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err);
 int symmetrize_lower64(cudaStream_t s, double* A, long long lda, int n);
 // y = alpha * op(A) x + beta * yin   (op(A) shape: 0 general, 1 lower, 2 upper)
 int gemv64(cudaStream_t s, int M, int N, const double* A, long long lda, int ta, int sh,

@@ -435,6 +435,16 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
     return BTA_OK;
 }
 
+int scale_into64(cudaStream_t s, int M, int N, const double* Cin, long long ldci, double beta, double* C,
+                 long long ldc, int lower) {
+    long long total = (long long)M * N;
+    if (total <= 0) return BTA_OK;
+    int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
+    scale_into_kernel<<<blocks, 256, 0, s>>>(M, N, Cin, ldci, beta, C, ldc, lower, 1, 0, 0);
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}
+
 int copy_mat64(cudaStream_t s, const double* src, long long lds, double* dst, long long ldd, int rows,
                int cols, int lower_only) {
     long long total = (long long)rows * cols;

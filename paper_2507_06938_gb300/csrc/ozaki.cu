@@ -1,0 +1,509 @@
+// Split-precision FP64 GEMM on the tcgen05 tensor cores (mixed path of the
+// BTA Schur updates).
+//
+// C += alpha * op(A) op(B) with FP64 A, B, C.  Every row i of op(A) is written
+// as 2^{e_i} sum_{p<S} d_p 2^{-7(p+1)} with integer digits |d_p| <= 128 (S = 5
+// slices, 36 bits below the row maximum), and every column j of op(B) the same
+// way with exponent f_j.  A digit is exact in bf16, a digit product is below
+// 2^14, so a sum of up to 1024 products is an integer below 2^24: the FP32
+// accumulator of tcgen05.mma kind::f16 holds it exactly.  The product is
+//   (op(A) op(B))_ij ~ 2^{e_i + f_j - 14} sum_{p+q<S} 2^{-7(p+q)} acc_pq(i,j)
+// (pairs with p + q >= S fall below the digits' own precision).  Each pair's
+// exact FP32 accumulator is drained from tensor memory and summed in
+// double-float (two FP32 words, error-free TwoSum) on the CUDA cores; FP64 is
+// used once per output element.  The FP64 pipe of GB300 delivers ~1.2
+// TFLOP/s, the bf16 tensor pipe ~1.9 PFLOP/s: 15 bf16 products per FP64
+// product still leave a large margin.
+//
+// Kernel structure (one 128 x 128 output tile per CTA, 320 threads):
+//   warp 0      TMA producer: digit tiles 128 x 64 (128-byte swizzle) of A and
+//               B into a 4-stage shared-memory ring
+//   warp 1      allocates 256 TMEM columns (two 128-column FP32 accumulators)
+//               and issues tcgen05.mma (M = 128, N = 128, K = 16) from one thread
+//   warps 2..9  drain each finished accumulator (tcgen05.ld) into double-float
+//               registers, then write alpha * result into C
+// grid.z splits the 15 pairs into groups (more CTAs for small outputs); the
+// groups add into C atomically.  Every wait on an mbarrier is bounded in
+// time; on expiry the kernel records an error, stops issuing, drains what it
+// issued and frees its tensor memory.
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace oz {
+
+constexpr int S = 5;
+constexpr int NPAIRS = S * (S + 1) / 2;
+constexpr int TM = 128, TN = 128, TK = 64;
+constexpr int STAGES = 4;
+constexpr int KB_PER_CHUNK = 1024 / TK;   // exactness bound of one FP32 accumulation
+constexpr int THREADS = 320;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t STAGE_BYTES = (TM + TN) * TK * 2;
+constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + STAGES * STAGE_BYTES + 256;
+constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;   // about 2 s
+
+__constant__ int c_pair_p[NPAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
+__constant__ int c_pair_q[NPAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
+
+struct Args {
+    int M, N;            // output extent
+    int Mp, Np;          // padded rows per digit slice (multiples of 128)
+    int kblocks;         // padded K / 64
+    const int* expA;     // Mp exponents of the rows of op(A)
+    const int* expB;     // Np exponents of the columns of op(B)
+    double* C;
+    long long ldc;
+    double alpha;
+    int pairs_per_group;
+    int atomic;          // several pair groups add into C
+    int lowerC;          // only entries m >= n (tiles strictly above skipped)
+    int* err;            // set to 1 on a wait time-out
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `parity` to complete.  Returns false (and
+// raises the CTA abort flag and the global error flag) after about 2 s, or
+// at once if another thread has already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* err) {
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+            *abort = 1;
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile whose 8-row groups of
+// 128-byte rows (64 bf16) are 1024 bytes apart, 128-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)(16 >> 4) << 16;      // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;              // descriptor version
+    d |= (uint64_t)2 << 61;              // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = 128.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// error-free sum: hi + lo <- hi + x exactly (Knuth's TwoSum), lo accumulates
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Args a) {
+    extern __shared__ uint8_t smem_raw[];
+    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+    if (a.lowerC && m0 + TM - 1 < n0) return;   // uniform for the CTA
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accfull = empty + STAGES;
+    uint64_t* accempty = accfull + 2;
+    uint64_t* drain = accempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int pb = blockIdx.z * a.pairs_per_group;
+    const int pe = min(NPAIRS, pb + a.pairs_per_group);
+    const int nchunks = (a.kblocks + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
+    const int units = (pe - pb) * nchunks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accfull[b], 1);
+            mbar_init(&accempty[b], 8);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------------------ TMA producer
+            int it = 0;
+            for (int u = 0; u < units && !*abort_flag; ++u) {
+                const int pair = pb + u / nchunks, chunk = u % nchunks;
+                const int p = c_pair_p[pair], q = c_pair_q[pair];
+                const int kb0 = chunk * KB_PER_CHUNK, kb1 = min(a.kblocks, kb0 + KB_PER_CHUNK);
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int st = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&empty[st], ph ^ 1, abort_flag, a.err)) break;
+                    uint8_t* sA = smem + st * STAGE_BYTES;
+                    uint8_t* sB = sA + TM * TK * 2;
+                    mbar_expect_tx(&full[st], STAGE_BYTES);
+                    tma_load_2d(smem_u32(sA), &tmA, &full[st], kb * TK, p * a.Mp + m0);
+                    tma_load_2d(smem_u32(sB), &tmB, &full[st], kb * TK, q * a.Np + n0);
+                }
+            }
+            if (*abort_flag) {
+                // let the copies already issued land before the CTA exits
+                const int first = max(0, it - STAGES);
+                for (int j = first; j < it; ++j) {
+                    const int st = j % STAGES;
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(&full[st], (j / STAGES) & 1) && clock64() - t0 < WAIT_LIMIT_CYCLES) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ------------------------------------------------------------ MMA issuer
+            int it = 0;
+            for (int u = 0; u < units && !*abort_flag; ++u) {
+                const int chunk = u % nchunks;
+                const int kb0 = chunk * KB_PER_CHUNK, kb1 = min(a.kblocks, kb0 + KB_PER_CHUNK);
+                const int buf = u & 1;
+                const uint32_t aph = (u >> 1) & 1;
+                if (!mbar_wait(&accempty[buf], aph ^ 1, abort_flag, a.err)) break;
+                fence_after_sync();
+                const uint32_t d_tmem = tmem_base + buf * TN;
+                bool ok = true;
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int st = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&full[st], ph, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after_sync();
+                    const uint32_t sA = smem_u32(smem + st * STAGE_BYTES);
+                    const uint32_t sB = sA + TM * TK * 2;
+#pragma unroll
+                    for (int k = 0; k < TK / 16; ++k) {
+                        umma_bf16(d_tmem, smem_desc_sw128(sA + k * 32), smem_desc_sw128(sB + k * 32),
+                                  (kb > kb0 || k > 0) ? 1u : 0u);
+                    }
+                    umma_commit(&empty[st]);
+                }
+                if (!ok) break;
+                umma_commit(&accfull[buf]);
+            }
+            // all MMAs issued by this thread have completed once `drain` fires
+            umma_commit(drain);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_LIMIT_CYCLES) {
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int ew = warp - 2;              // 0..7
+        const int quarter = warp % 4;         // TMEM lanes 32*quarter .. +31
+        const int colbase = (ew / 4) * 64;    // 64 of the 128 columns
+        const int row = quarter * 32 + lane;
+        float hi[64], lo[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+            hi[j] = 0.f;
+            lo[j] = 0.f;
+        }
+        bool ok = true;
+        for (int u = 0; u < units; ++u) {
+            const int pair = pb + u / nchunks;
+            const int buf = u & 1;
+            const uint32_t aph = (u >> 1) & 1;
+            if (!mbar_wait(&accfull[buf], aph, abort_flag, a.err)) {
+                ok = false;
+                break;
+            }
+            fence_after_sync();
+            const float scale = ldexpf(1.0f, -7 * (c_pair_p[pair] + c_pair_q[pair]));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t r[32];
+                tmem_ld_32cols(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * TN + colbase + h * 32, r);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) df_add(hi[h * 32 + j], lo[h * 32 + j], __uint_as_float(r[j]) * scale);
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[buf]);
+        }
+        const int i = m0 + row;
+        if (ok && i < a.M) {
+            const int ea = a.expA[i];
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const int nn = n0 + colbase + j;
+                if (nn >= a.N || (a.lowerC && i < nn)) continue;
+                const double v = ((double)hi[j] + (double)lo[j]) * ldexp(a.alpha, ea + a.expB[nn] - 14);
+                double* c = a.C + i + (long long)nn * a.ldc;
+                if (a.atomic) atomicAdd(c, v);
+                else *c += v;
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ digit split
+// Rows r < R of X (R x K, X[r][k] = P[r*sr + k*sk]) with an optional
+// triangular mask (shape 1: X[r][k] = 0 for k > r; shape 2: for k < r).
+// e_r = exponent of the row maximum (|X[r][k]| < 2^{e_r}); digits
+// d_s = rint(x * 128), x <- x * 128 - d_s, starting from x = X[r][k] 2^{-e_r}.
+// Output: dig[s][r][k] (bf16, rows padded to Rp, K padded to Kp with zeros)
+// and exp[r] (0 for padding rows).
+constexpr int SPLIT_ROWS = 32, SPLIT_K = 64;
+
+__global__ void __launch_bounds__(256) row_maxexp_kernel(const double* P, long long sr, long long sk, int R, int K,
+                                                         int shape, int Rp, int* expo) {
+    // one warp per row
+    const int r = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (r >= Rp) return;
+    double mx = 0.0;
+    if (r < R) {
+        int kb = 0, ke = K;
+        if (shape == 1) ke = min(K, r + 1);
+        if (shape == 2) kb = r;
+        for (int k = kb + lane; k < ke; k += 32) mx = fmax(mx, fabs(P[r * sr + k * sk]));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+        int e = 0;
+        if (mx > 0.0) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1): |x| < 2^e
+        expo[r] = e;
+    }
+}
+
+__global__ void __launch_bounds__(256) split_digits_kernel(const double* P, long long sr, long long sk, int R, int K,
+                                                           int shape, int Rp, int Kp, const int* expo,
+                                                           __nv_bfloat16* dig) {
+    // tile: SPLIT_ROWS rows x SPLIT_K columns; staged through shared memory so
+    // that both the FP64 read and the bf16 write are coalesced whatever the
+    // stride direction of P
+    __shared__ double tile[SPLIT_ROWS][SPLIT_K + 1];
+    const int r0 = blockIdx.y * SPLIT_ROWS, k0 = blockIdx.x * SPLIT_K;
+    for (int e = threadIdx.x; e < SPLIT_ROWS * SPLIT_K; e += 256) {
+        int rr, kk;
+        if (sr == 1) { rr = e % SPLIT_ROWS; kk = e / SPLIT_ROWS; } else { kk = e % SPLIT_K; rr = e / SPLIT_K; }
+        const int r = r0 + rr, k = k0 + kk;
+        double v = 0.0;
+        if (r < R && k < K && !(shape == 1 && k > r) && !(shape == 2 && k < r)) v = P[r * sr + k * sk];
+        tile[rr][kk] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < SPLIT_ROWS * SPLIT_K; e += 256) {
+        const int kk = e % SPLIT_K, rr = e / SPLIT_K;
+        const int r = r0 + rr, k = k0 + kk;
+        if (r >= Rp || k >= Kp) continue;
+        double x = (r < R) ? ldexp(tile[rr][kk], -expo[r]) : 0.0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            x *= 128.0;
+            const double d = rint(x);
+            x -= d;
+            dig[((size_t)s * Rp + r) * Kp + k] = __float2bfloat16_rn((float)d);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int kp) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return BTA_ERR_CUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    cuuint32_t box[2] = {TK, 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? BTA_OK : BTA_ERR_CUDA;
+}
+
+}  // namespace oz
+
+// Workspace needed by ozaki_gemm for an M x N x K product (bytes).
+size_t ozaki_workspace_bytes(int M, int N, int K) {
+    const size_t Mp = ((size_t)M + 127) / 128 * 128, Np = ((size_t)N + 127) / 128 * 128;
+    const size_t Kp = ((size_t)K + oz::TK - 1) / oz::TK * oz::TK;
+    return oz::S * (Mp + Np) * Kp * 2 + (Mp + Np) * sizeof(int) + 4 * 256;
+}
+
+// C = beta Cin + alpha op(A) op(B) through the digit-split tensor-core path.
+// ws: device workspace of ozaki_workspace_bytes(M, N, K); err: device int.
+int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
+    using namespace oz;
+    if (g.M <= 0 || g.N <= 0) return BTA_OK;
+    if (g.batch != 1) return BTA_ERR_ARG;
+    const int Mp = (g.M + 127) / 128 * 128, Np = (g.N + 127) / 128 * 128;
+    const int Kp = std::max(TK, (g.K + TK - 1) / TK * TK);
+    uint8_t* w = static_cast<uint8_t*>(ws);
+    __nv_bfloat16* digA = reinterpret_cast<__nv_bfloat16*>(w);
+    __nv_bfloat16* digB = digA + (size_t)S * Mp * Kp;
+    int* expA = reinterpret_cast<int*>(digB + (size_t)S * Np * Kp);
+    int* expB = expA + Mp;
+    // rows of op(A): op(A)[i][k] = ta ? A[k + i lda] : A[i + k lda]
+    const long long srA = g.ta ? g.lda : 1, skA = g.ta ? 1 : g.lda;
+    // rows of op(B)^T: op(B)[k][j] = tb ? B[j + k ldb] : B[k + j ldb]
+    const long long srB = g.tb ? 1 : g.ldb, skB = g.tb ? g.ldb : 1;
+    // shape of op(B)^T: lower op(B) (zero for j > k) is upper in op(B)^T
+    const int shBt = g.shB == 1 ? 2 : (g.shB == 2 ? 1 : 0);
+    row_maxexp_kernel<<<(Mp + 7) / 8, 256, 0, s>>>(g.A, srA, skA, g.M, g.K, g.shA, Mp, expA);
+    BTA_LAUNCH_CHECK();
+    row_maxexp_kernel<<<(Np + 7) / 8, 256, 0, s>>>(g.B, srB, skB, g.N, g.K, shBt, Np, expB);
+    BTA_LAUNCH_CHECK();
+    split_digits_kernel<<<dim3(Kp / SPLIT_K, Mp / SPLIT_ROWS), 256, 0, s>>>(g.A, srA, skA, g.M, g.K, g.shA, Mp, Kp,
+                                                                           expA, digA);
+    BTA_LAUNCH_CHECK();
+    split_digits_kernel<<<dim3(Kp / SPLIT_K, Np / SPLIT_ROWS), 256, 0, s>>>(g.B, srB, skB, g.N, g.K, shBt, Np, Kp,
+                                                                           expB, digB);
+    BTA_LAUNCH_CHECK();
+    CUtensorMap mA, mB;
+    BTA_TRY(make_map(&mA, digA, S * Mp, Kp));
+    BTA_TRY(make_map(&mB, digB, S * Np, Kp));
+    // C = beta Cin first (the tensor-core kernel adds into C)
+    const bool inplace = (g.Cin == g.C && g.ldci == g.ldc && g.beta == 1.0);
+    if (!inplace) BTA_TRY(scale_into64(s, g.M, g.N, g.Cin, g.ldci, g.beta, g.C, g.ldc, g.lowerC));
+    const int gm = Mp / TM, gn = Np / TN;
+    long long tiles = (long long)gm * gn;
+    if (g.lowerC) tiles = (tiles + gm) / 2;
+    int groups = 1;
+    while (groups < 5 && tiles * groups < 152) ++groups;
+    const int per = (NPAIRS + groups - 1) / groups;
+    groups = (NPAIRS + per - 1) / per;
+    Args a;
+    a.M = g.M; a.N = g.N; a.Mp = Mp; a.Np = Np; a.kblocks = Kp / TK;
+    a.expA = expA; a.expB = expB;
+    a.C = g.C; a.ldc = g.ldc; a.alpha = g.alpha;
+    a.pairs_per_group = per;
+    a.atomic = groups > 1;
+    a.lowerC = g.lowerC;
+    a.err = err;
+    static bool attr = false;
+    if (!attr) {
+        BTA_CUDA_TRY(cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)SMEM_BYTES));
+        attr = true;
+    }
+    ozaki_gemm_kernel<<<dim3(gm, gn, groups), THREADS, SMEM_BYTES, s>>>(mA, mB, a);
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}

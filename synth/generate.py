@@ -221,6 +221,8 @@ CONFIGS = {
     "c1": dict(nv=1, mesh=("grid", 10), nt=8, nr=2, seed=1, m_total=400),
     # univariate, ns=1024, nt=64, nr=4, N=65,540; 1024 observations per step
     "c2": dict(nv=1, mesh=("grid", 32), nt=64, nr=4, seed=2, per_step=1024),
+    # c2 with 8 time steps (same block size b=1024; for kernel profiling)
+    "c2s": dict(nv=1, mesh=("grid", 32), nt=8, nr=4, seed=2, per_step=1024),
     # trivariate coregional, b=3072, nt=48, a=6, N=147,462; 300 sites per step
     "c3": dict(nv=3, mesh=("grid", 32), nt=48, nr=2, seed=3, per_step=300,
                shared_sites=True),
