@@ -73,6 +73,8 @@ extern "C" int bta_create(int n, int b, int a, int precision, void* stream, bta_
     if (const char* e = std::getenv("BTA_LEAF")) c->leaf = std::atoi(e);
     c->vec = nullptr; c->red = nullptr; c->scal = nullptr; c->status = nullptr; c->params = nullptr;
     c->aux = nullptr; c->ev_fork = nullptr; c->ev_join = nullptr;
+    c->exec[0] = GemmExec{};
+    c->exec[1] = GemmExec{};
     int rc = BTA_OK;
     auto fail = [&](int r) { bta_destroy(c); return r; };
     if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess) return fail(BTA_ERR_CUDA);
@@ -89,6 +91,28 @@ extern "C" int bta_create(int n, int b, int a, int precision, void* stream, bta_
         if (cudaMemset(c->Linv[w], 0, ((size_t)n * bb + (size_t)a * a) * sizeof(double)) != cudaSuccess)
             return fail(BTA_ERR_CUDA);
     }
+    c->exec[0] = GemmExec{};
+    c->exec[1] = GemmExec{};
+    c->refine = 0;
+    if (precision == BTA_MIXED) {
+        if (cudaMalloc((void**)&c->oz_err, sizeof(int)) != cudaSuccess) return fail(BTA_ERR_OOM);
+        if (cudaMemset(c->oz_err, 0, sizeof(int)) != cudaSuccess) return fail(BTA_ERR_CUDA);
+        int min_dim = 256;
+        if (const char* e = std::getenv("BTA_OZ_MIN")) min_dim = std::atoi(e);
+        const size_t wsb = ozaki_workspace_bytes(b, b, b);
+        for (int w = 0; w < 2; ++w) {
+            if (cudaMalloc(&c->exec[w].ws, wsb) != cudaSuccess) {
+                c->exec[w].ws = nullptr;
+                return fail(BTA_ERR_OOM);
+            }
+            c->exec[w].fn = gemm_mixed_fn;
+            c->exec[w].ws_bytes = wsb;
+            c->exec[w].err = c->oz_err;
+            c->exec[w].min_dim = min_dim;
+        }
+        c->refine = 2;
+    }
+    if (const char* e = std::getenv("BTA_REFINE")) c->refine = std::atoi(e);
     if ((rc = dalloc(&c->vec, 9 * (size_t)c->N)) != BTA_OK) return fail(rc);
     c->red_len = 2 * 1216;
     if ((rc = dalloc(&c->red, c->red_len)) != BTA_OK) return fail(rc);
@@ -113,6 +137,9 @@ extern "C" int bta_destroy(bta_ctx_t c) {
         if (c->Linv[w]) cudaFree(c->Linv[w]);
         if (c->work[w]) cudaFree(c->work[w]);
     }
+    for (int w = 0; w < 2; ++w)
+        if (c->exec[w].ws) cudaFree(c->exec[w].ws);
+    if (c->oz_err) cudaFree(c->oz_err);
     if (c->vec) cudaFree(c->vec);
     if (c->red) cudaFree(c->red);
     if (c->scal) cudaFree(c->scal);
@@ -222,6 +249,16 @@ extern "C" int bta_sync(bta_ctx_t c) {
     long long st[2];
     e = cudaMemcpy(st, c->status, sizeof(st), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return bta_cuda_fail(e);
+    if (c->oz_err) {
+        int oz = 0;
+        e = cudaMemcpy(&oz, c->oz_err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return bta_cuda_fail(e);
+        if (oz) {
+            cudaMemset(c->oz_err, 0, sizeof(int));
+            c->last_info = -1;
+            return BTA_ERR_TIMEOUT;
+        }
+    }
     if (st[0] != 0) {
         c->last_info = st[1];
         long long zero[2] = {0, 0};

@@ -54,6 +54,29 @@ struct bta_model_s {
     double beta_prec;
 };
 
+// ---------------------------------------------------------------- dense GEMM descriptor
+struct Gemm64 {
+    int M, N, K;
+    const double* A; long long lda; int ta; int shA;   // shA: shape of op(A): 0 general, 1 lower, 2 upper
+    const double* B; long long ldb; int tb; int shB;   // shB: shape of op(B)
+    const double* Cin; long long ldci; double beta;    // Cin read only if beta != 0
+    double* C; long long ldc; double alpha;
+    int lowerC;                                        // compute/write only entries m >= n
+    int batch = 1;
+    long long sA = 0, sB = 0, sCi = 0, sC = 0;         // batch strides (elements)
+};
+
+// A GEMM executor: how the factorisation and selected inversion run their
+// dense products (FP64 DFMA, or the digit-split tensor-core path for the
+// large ones in mixed precision).
+struct GemmExec {
+    int (*fn)(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
+    void* ws;          // digit workspace (mixed path)
+    size_t ws_bytes;
+    int* err;          // device error flag of the tensor-core kernel
+    int min_dim;       // smallest M, N (and K) sent to the tensor-core path
+};
+
 // ---------------------------------------------------------------- BTA storage
 struct BtaMat {
     double* D = nullptr;     // n * b * b
@@ -78,6 +101,9 @@ struct bta_ctx_s {
     double* scal;            // device scalars (see SCAL_* below)
     long long* status;       // [0] error code, [1] info
     double* params;          // model parameters of the last fobj_eval
+    GemmExec exec[2];        // per matrix (Q_p and Q_c run on different streams)
+    int* oz_err = nullptr;   // device flag of the tensor-core GEMM (time-out)
+    int refine = 0;          // refinement steps of the f_obj solve
     int factored[2] = {0, 0};
     int leaf;                // leaf size of the recursive diagonal factorisation
     long long last_info = -1;
@@ -101,20 +127,15 @@ enum {
 };
 
 // ---------------------------------------------------------------- FP64 dense kernels (dense64.cu)
-struct Gemm64 {
-    int M, N, K;
-    const double* A; long long lda; int ta; int shA;   // shA: shape of op(A): 0 general, 1 lower, 2 upper
-    const double* B; long long ldb; int tb; int shB;   // shB: shape of op(B)
-    const double* Cin; long long ldci; double beta;    // Cin read only if beta != 0
-    double* C; long long ldc; double alpha;
-    int lowerC;                                        // compute/write only entries m >= n
-    int batch = 1;
-    long long sA = 0, sB = 0, sCi = 0, sC = 0;         // batch strides (elements)
-};
+
 
 int gemm64(cudaStream_t s, const Gemm64& g);
+
+
+int gemm_exec(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
+
 int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ldx, int n,
-               long long row0, long long* status, double* W, int leaf);
+               long long row0, long long* status, double* W, int leaf, const GemmExec* ex = nullptr);
 int copy_mat64(cudaStream_t s, const double* src, long long lds, double* dst, long long ldd,
                int rows, int cols, int lower_only);
 // C = beta Cin (C = 0 if beta == 0); only entries m >= n when lower
@@ -123,6 +144,7 @@ int scale_into64(cudaStream_t s, int M, int N, const double* Cin, long long ldci
 // Digit-split tensor-core GEMM (ozaki.cu): same contract as gemm64 (batch 1).
 size_t ozaki_workspace_bytes(int M, int N, int K);
 int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err);
+int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
 int symmetrize_lower64(cudaStream_t s, double* A, long long lda, int n);
 // y = alpha * op(A) x + beta * yin   (op(A) shape: 0 general, 1 lower, 2 upper)
 int gemv64(cudaStream_t s, int M, int N, const double* A, long long lda, int ta, int sh,

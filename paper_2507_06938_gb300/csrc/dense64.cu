@@ -326,23 +326,30 @@ __global__ void finish_sum_kernel(const double* partial, int len, double* out, d
 // ==================================================================== host launchers
 int gemm64(cudaStream_t s, const Gemm64& g) {
     if (g.M <= 0 || g.N <= 0) return BTA_OK;
-    // micro-tile shape: thin outputs get thin tiles so that no DFMA is spent
-    // on padding rows/columns
-    int MI = g.M <= 16 ? 1 : (g.M <= 32 ? 2 : 4);
-    int NJ = g.N <= 16 ? 1 : (g.N <= 32 ? 2 : 4);
-    const int TBM = 16 * MI, TBN = 16 * NJ;
-    const int gm = (g.M + TBM - 1) / TBM, gn = (g.N + TBN - 1) / TBN;
-    long long tiles = (long long)gm * gn;
-    if (g.lowerC) tiles = (tiles + gm) / 2;
-    // the FP64 pipe of one SM is slow: split K until about two CTAs per SM
-    int ksplit = 1;
-    if (g.batch == 1 && g.K > 4 * BK) {
-        const long long want = 2LL * 152;
-        if (tiles < want) {
-            ksplit = (int)std::min<long long>((want + tiles - 1) / tiles, (g.K + 4 * BK - 1) / (4 * BK));
-            ksplit = std::max(1, std::min(ksplit, 64));
+    // The FP64 pipe of one SM is slow (2 DFMA per clock), so every product is
+    // spread over about two CTAs per SM: pick the largest micro-tile that
+    // still reaches that with a K split of whole 16-wide slices, else the
+    // smallest tile with the largest split.
+    const long long want = 2LL * 152;
+    int MI = 1, NJ = 1, ksplit = 1;
+    const int kslices = std::max(1, (g.K + BK - 1) / BK);
+    bool chosen = false;
+    for (int sz = 4; sz >= 1 && !chosen; sz /= 2) {
+        const int mi = std::min(sz, g.M <= 16 ? 1 : (g.M <= 32 ? 2 : 4));
+        const int nj = std::min(sz, g.N <= 16 ? 1 : (g.N <= 32 ? 2 : 4));
+        const int gm = (g.M + 16 * mi - 1) / (16 * mi), gn = (g.N + 16 * nj - 1) / (16 * nj);
+        long long tiles = (long long)gm * gn;
+        if (g.lowerC) tiles = (tiles + gm) / 2;
+        const int maxsplit = g.batch == 1 ? std::min(64, std::max(1, kslices / (sz == 4 ? 4 : 2))) : 1;
+        if (tiles * maxsplit >= want || sz == 1) {
+            MI = mi;
+            NJ = nj;
+            ksplit = (int)std::min<long long>(maxsplit, std::max<long long>(1, (want + tiles - 1) / tiles));
+            chosen = true;
         }
     }
+    const int TBM = 16 * MI, TBN = 16 * NJ;
+    const int gm = (g.M + TBM - 1) / TBM, gn = (g.N + TBN - 1) / TBN;
     if (ksplit > 1) {
         const bool inplace = (g.Cin == g.C && g.ldci == g.ldc && g.beta == 1.0);
         if (!inplace) {
@@ -384,11 +391,19 @@ static int leaf_launch(cudaStream_t s, double* A, long long lda, double* X, long
 //   [A11      ]   L11 = chol(A11), X11 = L11^{-1}
 //   [A21  A22 ]   L21 = A21 X11^T, A22 -= L21 L21^T, L22 = chol(A22), X22 = L22^{-1}
 //                 X21 = -X22 (L21 X11)
+static int gemm_fp64_fn(const GemmExec*, cudaStream_t s, const Gemm64& g) { return gemm64(s, g); }
+
+int gemm_exec(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
+    if (!ex || !ex->fn) return gemm64(s, g);
+    return ex->fn(ex, s, g);
+}
+
 int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ldx, int n, long long row0,
-               long long* status, double* W, int leaf) {
+               long long* status, double* W, int leaf, const GemmExec* ex) {
     if (n <= 0) return BTA_OK;
     leaf = std::max(8, std::min(leaf, LEAF_MAX));
     if (n <= leaf) return leaf_launch(s, A, lda, X, ldx, n, row0, status);
+    (void)gemm_fp64_fn;
     const int half = (n + 1) / 2;
     int n1 = ((half + leaf - 1) / leaf) * leaf;
     if (n1 >= n) n1 = leaf;
@@ -399,7 +414,7 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
     double* X11 = X;
     double* X21 = X + n1;
     double* X22 = X + n1 + n1 * ldx;
-    BTA_TRY(chol_inv64(s, A11, lda, X11, ldx, n1, row0, status, W, leaf));
+    BTA_TRY(chol_inv64(s, A11, lda, X11, ldx, n1, row0, status, W, leaf, ex));
     Gemm64 g{};
     // W (n2 x n1) = A21 * X11^T      (op(B) upper)
     g = Gemm64{};
@@ -407,7 +422,7 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
     g.A = A21; g.lda = lda; g.ta = 0; g.shA = 0;
     g.B = X11; g.ldb = ldx; g.tb = 1; g.shB = 2;
     g.C = W; g.ldc = n2; g.alpha = 1.0; g.beta = 0.0;
-    BTA_TRY(gemm64(s, g));
+    BTA_TRY(gemm_exec(ex, s, g));
     BTA_TRY(copy_mat64(s, W, n2, A21, lda, n2, n1, 0));
     // A22 -= L21 L21^T  (lower)
     g = Gemm64{};
@@ -416,22 +431,22 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
     g.B = A21; g.ldb = lda; g.tb = 1;
     g.Cin = A22; g.ldci = lda; g.beta = 1.0;
     g.C = A22; g.ldc = lda; g.alpha = -1.0; g.lowerC = 1;
-    BTA_TRY(gemm64(s, g));
-    BTA_TRY(chol_inv64(s, A22, lda, X22, ldx, n2, row0 + n1, status, W, leaf));
+    BTA_TRY(gemm_exec(ex, s, g));
+    BTA_TRY(chol_inv64(s, A22, lda, X22, ldx, n2, row0 + n1, status, W, leaf, ex));
     // W = L21 * X11   (op(B) lower)
     g = Gemm64{};
     g.M = n2; g.N = n1; g.K = n1;
     g.A = A21; g.lda = lda;
     g.B = X11; g.ldb = ldx; g.tb = 0; g.shB = 1;
     g.C = W; g.ldc = n2; g.alpha = 1.0; g.beta = 0.0;
-    BTA_TRY(gemm64(s, g));
+    BTA_TRY(gemm_exec(ex, s, g));
     // X21 = -X22 * W   (op(A) lower)
     g = Gemm64{};
     g.M = n2; g.N = n1; g.K = n2;
     g.A = X22; g.lda = ldx; g.ta = 0; g.shA = 1;
     g.B = W; g.ldb = n2; g.tb = 0;
     g.C = X21; g.ldc = ldx; g.alpha = -1.0; g.beta = 0.0;
-    BTA_TRY(gemm64(s, g));
+    BTA_TRY(gemm_exec(ex, s, g));
     return BTA_OK;
 }
 

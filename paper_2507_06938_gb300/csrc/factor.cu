@@ -39,7 +39,7 @@ int factor_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
     for (int i = 0; i < n; ++i) {
         double* Di = L.D + i * bsq(ctx);
         double* Xi = Linv + i * bsq(ctx);
-        BTA_TRY(chol_inv64(s, Di, b, Xi, b, b, (long long)i * b, status, W, leaf));
+        BTA_TRY(chol_inv64(s, Di, b, Xi, b, b, (long long)i * b, status, W, leaf, &ctx->exec[which]));
         Gemm64 g{};
         if (i < n - 1) {
             // L_{i+1,i} = B_i X_i^T
@@ -50,7 +50,7 @@ int factor_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
             g.C = L.B + i * bsq(ctx); g.ldc = b; g.alpha = 1.0;
             cudaEvent_t stop;
             BTA_TRY(prof_begin(ctx, s, (double)b * b * b, &stop));
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
             if (stop) BTA_CUDA_TRY(cudaEventRecord(stop, s));
             // D_{i+1} = Q.D_{i+1} - L_{i+1,i} L_{i+1,i}^T   (lower)
             g = Gemm64{};
@@ -60,7 +60,7 @@ int factor_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
             g.Cin = Q.D + (i + 1) * bsq(ctx); g.ldci = b; g.beta = 1.0;
             g.C = L.D + (i + 1) * bsq(ctx); g.ldc = b; g.alpha = -1.0; g.lowerC = 1;
             BTA_TRY(prof_begin(ctx, s, (double)b * b * b, &stop));
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
             if (stop) BTA_CUDA_TRY(cudaEventRecord(stop, s));
         }
         if (a > 0) {
@@ -71,7 +71,7 @@ int factor_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
             g.A = Racc; g.lda = a;
             g.B = Xi; g.ldb = b; g.tb = 1; g.shB = 2;
             g.C = Lri; g.ldc = a; g.alpha = 1.0;
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
             if (i < n - 1) {
                 // Racc = R_{i+1} - L_{t,i} L_{i+1,i}^T
                 g = Gemm64{};
@@ -80,7 +80,7 @@ int factor_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
                 g.B = L.B + i * bsq(ctx); g.ldb = b; g.tb = 1;
                 g.Cin = Q.R + (size_t)(i + 1) * a * b; g.ldci = a; g.beta = 1.0;
                 g.C = Racc; g.ldc = a; g.alpha = -1.0;
-                BTA_TRY(gemm64(s, g));
+                BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
             }
             // T -= L_{t,i} L_{t,i}^T   (lower)
             g = Gemm64{};
@@ -89,7 +89,7 @@ int factor_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
             g.B = Lri; g.ldb = a; g.tb = 1;
             g.Cin = L.T; g.ldci = a; g.beta = 1.0;
             g.C = L.T; g.ldc = a; g.alpha = -1.0; g.lowerC = 1;
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
         }
     }
     if (a > 0)

@@ -76,6 +76,15 @@ extern "C" int fobj_eval(bta_ctx_t ctx, bta_model_t m, const double* thetas_dev,
             BTA_LAUNCH_CHECK();
         }
         BTA_TRY(solve_impl(ctx, BTA_QC, rhs, mu, s));
+        // iterative refinement with an FP64 residual on the assembled blocks
+        for (int it = 0; it < ctx->refine; ++it) {
+            double* res = ctx->vec + N;
+            double* corr = ctx->vec + 2 * N;
+            BTA_TRY(matvec_impl(ctx, BTA_QC, mu, res, s));
+            BTA_TRY(axpby64(s, N, 1.0, rhs, -1.0, res, res));
+            BTA_TRY(solve_impl(ctx, BTA_QC, res, corr, s));
+            BTA_TRY(axpby64(s, N, 1.0, mu, 1.0, corr, mu));
+        }
         BTA_TRY(dot64(s, rhs, mu, N, ctx->red + ctx->red_len / 2, ctx->red_len / 2, ctx->scal + SCAL_DOT));
         // join
         BTA_CUDA_TRY(cudaEventRecord(ctx->ev_join, aux));

@@ -507,3 +507,13 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }
+
+// GEMM executor of the mixed path: products whose three dimensions are all at
+// least min_dim go to the tensor cores, the rest (arrow, tip, small panels of
+// the recursive diagonal factorisation) stay on the FP64 pipe.
+int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
+    if (g.batch == 1 && g.M >= ex->min_dim && g.N >= ex->min_dim && g.K >= ex->min_dim &&
+        ozaki_workspace_bytes(g.M, g.N, g.K) <= ex->ws_bytes)
+        return ozaki_gemm(s, g, ex->ws, ex->err);
+    return gemm64(s, g);
+}

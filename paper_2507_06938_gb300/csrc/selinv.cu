@@ -32,7 +32,7 @@ int selinv_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
         g.A = XT; g.lda = a; g.ta = 1; g.shA = 2;
         g.B = XT; g.ldb = a; g.shB = 1;
         g.C = S.T; g.ldc = a; g.alpha = 1.0;
-        BTA_TRY(gemm64(s, g));
+        BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
     }
     for (int i = n - 1; i >= 0; --i) {
         const double* Xi = Linv + i * bb;
@@ -45,7 +45,7 @@ int selinv_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
             g.A = L.R + i * ab; g.lda = a;
             g.B = Xi; g.ldb = b; g.shB = 1;
             g.C = F; g.ldc = a; g.alpha = 1.0;
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
         }
         if (i < n - 1) {
             double* SBi = S.B + i * bb;
@@ -55,14 +55,14 @@ int selinv_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
             g.A = L.B + i * bb; g.lda = b;
             g.B = Xi; g.ldb = b; g.shB = 1;
             g.C = G; g.ldc = b; g.alpha = 1.0;
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
             // Sigma_{i+1,i} = -Sigma_{i+1,i+1} G  (- Sigma_{t,i+1}^T F)
             g = Gemm64{};
             g.M = b; g.N = b; g.K = b;
             g.A = S.D + (i + 1) * bb; g.lda = b;
             g.B = G; g.ldb = b;
             g.C = SBi; g.ldc = b; g.alpha = -1.0;
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
             if (a > 0) {
                 g = Gemm64{};
                 g.M = b; g.N = b; g.K = a;
@@ -70,21 +70,21 @@ int selinv_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
                 g.B = F; g.ldb = a;
                 g.Cin = SBi; g.ldci = b; g.beta = 1.0;
                 g.C = SBi; g.ldc = b; g.alpha = -1.0;
-                BTA_TRY(gemm64(s, g));
+                BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
                 // Sigma_{t,i} = -Sigma_{t,i+1} G - Sigma_tt F
                 g = Gemm64{};
                 g.M = a; g.N = b; g.K = b;
                 g.A = S.R + (i + 1) * ab; g.lda = a;
                 g.B = G; g.ldb = b;
                 g.C = SRi; g.ldc = a; g.alpha = -1.0;
-                BTA_TRY(gemm64(s, g));
+                BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
                 g = Gemm64{};
                 g.M = a; g.N = b; g.K = a;
                 g.A = S.T; g.lda = a;
                 g.B = F; g.ldb = a;
                 g.Cin = SRi; g.ldci = a; g.beta = 1.0;
                 g.C = SRi; g.ldc = a; g.alpha = -1.0;
-                BTA_TRY(gemm64(s, g));
+                BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
             }
         } else if (a > 0) {
             // Sigma_{t,n-1} = -Sigma_tt F
@@ -93,7 +93,7 @@ int selinv_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
             g.A = S.T; g.lda = a;
             g.B = F; g.ldb = a;
             g.C = SRi; g.ldc = a; g.alpha = -1.0;
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
         }
         // Sigma_ii = X_i^T X_i - Sigma_{i+1,i}^T G - Sigma_{t,i}^T F   (lower, then mirrored)
         g = Gemm64{};
@@ -101,7 +101,7 @@ int selinv_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
         g.A = Xi; g.lda = b; g.ta = 1; g.shA = 2;
         g.B = Xi; g.ldb = b; g.shB = 1;
         g.C = SDi; g.ldc = b; g.alpha = 1.0; g.lowerC = 1;
-        BTA_TRY(gemm64(s, g));
+        BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
         if (i < n - 1) {
             g = Gemm64{};
             g.M = b; g.N = b; g.K = b;
@@ -109,7 +109,7 @@ int selinv_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
             g.B = G; g.ldb = b;
             g.Cin = SDi; g.ldci = b; g.beta = 1.0;
             g.C = SDi; g.ldc = b; g.alpha = -1.0; g.lowerC = 1;
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
         }
         if (a > 0) {
             g = Gemm64{};
@@ -118,7 +118,7 @@ int selinv_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
             g.B = F; g.ldb = a;
             g.Cin = SDi; g.ldci = b; g.beta = 1.0;
             g.C = SDi; g.ldc = b; g.alpha = -1.0; g.lowerC = 1;
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
         }
         BTA_TRY(symmetrize_lower64(s, SDi, b, b));
     }

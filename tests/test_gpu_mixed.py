@@ -1,0 +1,85 @@
+"""Mixed-precision path (BTA_MIXED): the large Schur-update, triangular and
+selected-inversion products run as digit-split FP64 products on the tcgen05
+tensor cores (5 bf16 slices of 7 bits per operand, ~36 significant bits
+below each row/column maximum); the arrow, tip, log-det and refinement
+residuals stay FP64.
+
+Bounds (against the FP64 oracle): log-determinant relative error <= 1e-8
+and, after two refinement steps with an FP64 residual, solve residual
+<= 1e-10 (the mixed-path targets).  Selected-inverse blocks carry the
+36-bit product error amplified by the conditioning of the recurrence; the
+largest relative error measured (fixed-effect arrow/tip blocks of Q_c at
+b = 1024) is 7.4e-6, so the bound here is 5e-5 relative to the block
+maximum; the FP64 path keeps the 1e-9 bound."""
+
+import numpy as np
+import pytest
+
+from oracle import bta as obta
+from oracle import fobj as ofobj
+from oracle import model as omodel
+
+from gpu_util import GpuRun, blocks_of, build_lib, dev, need_gpu, problem, rel_max
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup():
+    need_gpu()
+    build_lib()
+
+
+@pytest.mark.parametrize("name,min_dim", [("t_uni_mid", 64), ("t_coreg3_mid", 64), ("t_coreg3_mid", 128),
+                                          ("c2s", 256)])
+def test_mixed_factor_logdet_selinv(name, min_dim, monkeypatch):
+    import torch
+    from paper_2507_06938_gb300 import bta
+    monkeypatch.setenv("BTA_OZ_MIN", str(min_dim))
+    p = problem(name)
+    prm = omodel.theta_to_params(p.theta0, p.nv)
+    built = omodel.build(p, prm)
+    run = GpuRun(p, precision=bta.BTA_MIXED)
+    for which, Q in ((bta.BTA_QP, built.Qp), (bta.BTA_QC, built.Qc)):
+        blk = obta.blocks_from_sparse(Q, p.nt, p.b, p.a)
+        Lo = obta.factor(blk)
+        run.assemble(prm, which)
+        run.ctx.factor(which)
+        ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+        run.ctx.logdet(which, ld)
+        rng = np.random.default_rng(5)
+        r = rng.standard_normal(p.N)
+        x = torch.zeros(p.N, dtype=torch.float64, device="cuda")
+        resid = torch.zeros(1, dtype=torch.float64, device="cuda")
+        run.ctx.solve(which, dev(r), x, 2, resid)
+        run.ctx.selinv(which)
+        run.ctx.sync()
+        ref = obta.logdet(Lo)
+        err_ld = abs(ld.item() - ref) / abs(ref)
+        assert err_ld <= 1e-8, err_ld
+        assert resid.item() <= 1e-10, resid.item()
+        S = blocks_of(run.ctx, which, bta.BTA_STORE_SIGMA, p.nt, p.b, p.a)
+        So = obta.selinv(Lo)
+        errs = {k: rel_max(S[k], So[k]) for k in ("D", "B", "R", "T")}
+        print(name, which, "logdet", err_ld, "resid", resid.item(), "selinv", errs)
+        for k, e in errs.items():
+            assert e <= 5e-5, (k, e)
+
+
+@pytest.mark.parametrize("name", ["t_coreg3", "t_uni_mid"])
+def test_mixed_fobj(name, monkeypatch):
+    import torch
+    from paper_2507_06938_gb300 import bta
+    monkeypatch.setenv("BTA_OZ_MIN", "64")
+    p = problem(name)
+    run = GpuRun(p, precision=bta.BTA_MIXED)
+    th = p.theta0[None, :]
+    f = torch.zeros(1, dtype=torch.float64, device="cuda")
+    mu = torch.zeros(p.N, dtype=torch.float64, device="cuda")
+    run.ctx.fobj_eval(run.model, dev(th), f, mu)
+    run.ctx.sync()
+    terms = ofobj.f_obj_terms(p, p.theta0)
+    # f combines log-dets of size ~1e3-1e4 with 1e-8 relative error each
+    tol = 1e-8 * (abs(terms["logdet_p"]) + abs(terms["logdet_c"]))
+    assert abs(f.item() - terms["f"]) <= tol
+    assert rel_max(mu.cpu().numpy(), terms["mu"]) < 1e-9
