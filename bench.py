@@ -1,16 +1,18 @@
 #!/usr/bin/env python
 """Throughput of the BTA hot path of one f_obj(theta) evaluation on GB300.
 
-One step = one f_obj(theta) evaluation of the univariate AR(1) x SPDE model
-at working size (32 x 32 grid mesh: ns = 1024, nt = 64, nb = 4 fixed
-effects, m = 65,536 observations, N = 65,540): assembly, factorisation and
-log-determinant of Q_p and Q_c, the conditional-mean solve, the objective,
-and the selected inversion of Q_c.  Each step uses a different theta.
+One step = one BFGS gradient stencil of the univariate AR(1) x SPDE model at
+working size (32 x 32 grid mesh: ns = 1024, nt = 64, nb = 4 fixed effects,
+m = 65,536 observations, N = 65,540): f_obj(theta) at the 2 dim(theta) + 1 = 9
+central-difference points (Eq. 10), each with assembly, factorisation and
+log-determinant of Q_p and Q_c, the conditional-mean solve and the objective,
+plus the selected inversion of every Q_c.  All 18 BTA matrices of a step go
+through the same kernel launches.  Each step uses a different theta.
 
-value  = steps / s with inputs resident in HBM (device-timed, CUDA events)
-e2e    = the same through the C ABI with theta copied host->device and f,
-         mu and the marginal variances copied device->host inside the timed
-         region (pinned host buffers)
+value  = f_obj evaluations / s with inputs resident in HBM (device-timed)
+e2e    = the same through the C ABI with the thetas copied host->device and
+         f, mu and the marginal variances copied device->host inside the
+         timed region (pinned host buffers)
 --impl reference times the CPU FP64 oracle (oracle/) on the host cores.
 """
 
@@ -32,12 +34,22 @@ sys.path.insert(0, ROOT)
 METRIC = "f_obj evals/s and BTA Cholesky+selinv TFLOP/s: mixed vs FP64 on one GB300"
 UNIT = "f_obj evals/s"
 WORKLOAD = ("univariate AR(1) x SPDE Matern, 32x32 grid mesh ns=1024, nt=64, nb=4 fixed effects, "
-            "m=65536 observations, N=65540; per step: assemble+factor+log-det of Q_p and Q_c, "
-            "conditional-mean solve, f_obj, selected inversion of Q_c")
+            "m=65536 observations, N=65540; per step: the 2 dim(theta)+1 = 9 central-difference theta points, "
+            "each assemble+factor+log-det of Q_p and Q_c, conditional-mean solve, f_obj, selected inversion of Q_c")
 CONFIG_NAME = "c2"
 # FP64 peak of the GB300: the nominal FP64 rate (no FP64 figure is measured by
 # the driver); a DFMA throughput probe on this machine read 1.20 TFLOP/s at 1995 MHz.
 FP64_PEAK_TFLOPS = 1.25
+
+
+def _measured_bf16():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        return 1900.0   # fallback figure of the profiling recipe
+
+
+BF16_PEAK_TFLOPS = _measured_bf16()
 
 
 def parse():
@@ -48,6 +60,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--config", default=CONFIG_NAME)
+    ap.add_argument("--batch", type=int, default=0, help="theta points per step (default 2 dim(theta) + 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -154,10 +167,22 @@ def oracle_step(problem, theta, fd):
     return terms["f"]
 
 
+def stencil(center, h=1e-3):
+    """The 2 dim + 1 points of the central-difference gradient (Eq. 10)."""
+    import numpy as np
+    pts = [center]
+    for i in range(center.shape[0]):
+        e = np.zeros_like(center)
+        e[i] = h
+        pts += [center + e, center - e]
+    return np.stack(pts)
+
+
 def thetas_for(problem, count, rank):
+    """One stencil per step around a different seeded center."""
     import numpy as np
     rng = np.random.default_rng(1000 + rank)
-    return [problem.theta0 + 0.02 * rng.standard_normal(problem.theta0.shape) for _ in range(count)]
+    return [stencil(problem.theta0 + 0.02 * rng.standard_normal(problem.theta0.shape)) for _ in range(count)]
 
 
 def run_reference(args):
@@ -168,12 +193,14 @@ def run_reference(args):
     from oracle import model as omodel
     p = synth.problem_from_config(args.config)
     fd = omodel.fem_data(p)
+    # bounded sample: one theta point of each step's stencil (the oracle takes
+    # tens of seconds per point at this size); value in f_obj evaluations / s
     thetas = thetas_for(p, args.warmup + args.steps, 0)
-    for j in range(args.warmup):
-        oracle_step(p, thetas[j], fd)
+    for j in range(min(args.warmup, 1)):     # the CPU path has nothing further to warm up
+        oracle_step(p, thetas[j][0], fd)
     t0 = time.perf_counter()
     for j in range(args.steps):
-        oracle_step(p, thetas[args.warmup + j], fd)
+        oracle_step(p, thetas[args.warmup + j][0], fd)
     dt = time.perf_counter() - t0
     value = args.steps / dt
     line = {
@@ -182,7 +209,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "name": args.config},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                         "sample": "whole workload per step (numpy/scipy FP64 block recurrences)"},
+                         "sample": "one theta point (f_obj + selinv of Q_c) of each step's 9-point stencil, "
+                                   "numpy/scipy FP64 block recurrences"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -211,19 +239,21 @@ def run_ours(args):
 
     p = synth.problem_from_config(args.config)
     precision = bta.BTA_FP64 if args.precision == "fp64" else bta.BTA_MIXED
+    B = args.batch or (2 * p.theta0.shape[0] + 1)
     stream = torch.cuda.Stream()
     model = bta.BtaModel(p)
-    ctx = bta.BtaContext(p.nt, p.b, p.a, precision, stream)
+    ctx = bta.BtaContext(p.nt, p.b, p.a, precision, stream, B)
     nsteps = args.warmup + args.steps
-    thetas_h = np.stack(thetas_for(p, nsteps, rank))
+    thetas_h = np.stack([t[:B] if t.shape[0] >= B else np.resize(t, (B, t.shape[1]))
+                         for t in thetas_for(p, nsteps, rank)])          # steps x B x dim
     thetas_d = torch.tensor(thetas_h, dtype=torch.float64, device="cuda")
-    f_d = torch.zeros(nsteps, dtype=torch.float64, device="cuda")
-    mu_d = torch.zeros(p.N, dtype=torch.float64, device="cuda")
-    var_d = torch.zeros(p.N, dtype=torch.float64, device="cuda")
+    f_d = torch.zeros((nsteps, B), dtype=torch.float64, device="cuda")
+    mu_d = torch.zeros((B, p.N), dtype=torch.float64, device="cuda")
+    var_d = torch.zeros((B, p.N), dtype=torch.float64, device="cuda")
 
-    def step(j, theta_dev):
-        ctx.fobj_eval(model, theta_dev, f_d[j:j + 1], mu_d)
-        ctx.selinv(bta.BTA_QC)
+    def step(j, theta_dev, f_out):
+        ctx.fobj_eval(model, theta_dev, f_out, mu_d)
+        ctx.selinv_batch(bta.BTA_QC)
 
     def barrier_sync():
         torch.cuda.synchronize()
@@ -233,7 +263,7 @@ def run_ours(args):
 
     with torch.cuda.stream(stream):
         for j in range(args.warmup):
-            step(j, thetas_d[j:j + 1])
+            step(j, thetas_d[j], f_d[j])
         ctx.sync()
         barrier_sync()
         # ---- device-resident timed region
@@ -244,7 +274,7 @@ def run_ours(args):
         with ClockSampler(local) as clk:
             e0.record(stream)
             for j in range(args.steps):
-                step(args.warmup + j, thetas_d[args.warmup + j:args.warmup + j + 1])
+                step(args.warmup + j, thetas_d[args.warmup + j], f_d[args.warmup + j])
             e1.record(stream)
             e1.synchronize()
         ctx.sync()
@@ -255,19 +285,20 @@ def run_ours(args):
         barrier_sync()
         # ---- end-to-end through the C ABI with host buffers
         th_pin = torch.tensor(thetas_h, dtype=torch.float64).pin_memory()
-        f_pin = torch.zeros(args.steps, dtype=torch.float64).pin_memory()
-        mu_pin = torch.zeros(p.N, dtype=torch.float64).pin_memory()
-        var_pin = torch.zeros(p.N, dtype=torch.float64).pin_memory()
-        theta_stage = torch.zeros((1, p.theta0.shape[0]), dtype=torch.float64, device="cuda")
+        f_pin = torch.zeros((args.steps, B), dtype=torch.float64).pin_memory()
+        mu_pin = torch.zeros((B, p.N), dtype=torch.float64).pin_memory()
+        var_pin = torch.zeros((B, p.N), dtype=torch.float64).pin_memory()
+        theta_stage = torch.zeros((B, p.theta0.shape[0]), dtype=torch.float64, device="cuda")
         g0 = torch.cuda.Event(enable_timing=True)
         g1 = torch.cuda.Event(enable_timing=True)
         g0.record(stream)
         for j in range(args.steps):
-            theta_stage.copy_(th_pin[args.warmup + j:args.warmup + j + 1], non_blocking=True)
-            ctx.fobj_eval(model, theta_stage, f_d[j:j + 1], mu_d)
-            ctx.selinv(bta.BTA_QC)
-            ctx.selinv_diag(bta.BTA_QC, var_d)
-            f_pin[j:j + 1].copy_(f_d[j:j + 1], non_blocking=True)
+            theta_stage.copy_(th_pin[args.warmup + j], non_blocking=True)
+            ctx.fobj_eval(model, theta_stage, f_d[j], mu_d)
+            ctx.selinv_batch(bta.BTA_QC)
+            for k in range(B):
+                ctx.selinv_diag(2 * k + bta.BTA_QC, var_d[k])
+            f_pin[j].copy_(f_d[j], non_blocking=True)
             mu_pin.copy_(mu_d, non_blocking=True)
             var_pin.copy_(var_d, non_blocking=True)
         g1.record(stream)
@@ -279,49 +310,65 @@ def run_ours(args):
     if dist is not None:
         dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
     ms, ms_e2e = float(t_local[0]), float(t_local[1])
-    total_steps = args.steps * world
-    value = total_steps / (ms / 1e3)
-    e2e_value = total_steps / (ms_e2e / 1e3)
-    flops_step = 2 * bta.bta_flops_factor(p.nt, p.b, p.a) + bta.bta_flops_selinv(p.nt, p.b, p.a)
-    tflops = flops_step * total_steps / (ms / 1e3) / 1e12
+    total_evals = args.steps * world * B
+    value = total_evals / (ms / 1e3)
+    e2e_value = total_evals / (ms_e2e / 1e3)
+    flops_eval = 2 * bta.bta_flops_factor(p.nt, p.b, p.a) + bta.bta_flops_selinv(p.nt, p.b, p.a)
+    tflops = flops_eval * total_evals / (ms / 1e3) / 1e12
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
     achieved = (prof_flops / (prof_ms / 1e3) / 1e12) if prof_ms > 0 else None
-    roof = {
-        "bound": "alu", "kernel": "gemm64_kernel<4,4> (FP64 DFMA Schur-update GEMM, b x b x b)",
-        "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-        "traffic": traffic_record("gemm64_bxbxb"),
-        "launches_timed": prof_n, "flops_per_launch": (prof_flops / prof_n) if prof_n else None,
-        "peak_source": "nominal GB300 FP64 rate (no FP64 entry in the measured peaks)",
-    }
+    if args.precision == "fp64":
+        roof = {
+            "bound": "alu", "kernel": "gemm64_kernel (FP64 DFMA Schur-update GEMMs L_{i+1,i}=B_i L_ii^-T and "
+                                      "D_{i+1}-=L L^T, batched over the step's matrices)",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+            "traffic": traffic_record("gemm64_bxbxb"),
+            "launches_timed": prof_n, "flops_per_launch": (prof_flops / prof_n) if prof_n else None,
+            "peak_source": "nominal GB300 FP64 rate (no FP64 entry in the measured peaks)",
+        }
+    else:
+        # executed bf16 tensor flops: 15 digit-pair products per FP64-equivalent flop
+        tensor = 15.0 * achieved if achieved else None
+        peak = BF16_PEAK_TFLOPS
+        roof = {
+            "bound": "tensor", "kernel": "ozaki_gemm (digit split + tcgen05 bf16 15-pair products) for the "
+                                        "Schur-update GEMMs, batched over the step's matrices",
+            "achieved": tensor, "peak": peak, "unit": "TFLOP/s", "frac": (tensor / peak) if tensor else None,
+            "achieved_fp64_equivalent": achieved,
+            "traffic": traffic_record("ozaki_bxbxb"),
+            "launches_timed": prof_n, "flops_per_launch": (prof_flops / prof_n) if prof_n else None,
+            "peak_source": "measured bf16 dense (burst) of this pool, of measured",
+        }
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "mixed",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "name": args.config, "precision": args.precision,
+        "config": {"workload": WORKLOAD, "name": args.config, "precision": args.precision, "theta_points": B,
                    "l2": "inputs larger than L2 (BTA blocks ~1.07 GB per matrix)",
                    "parallelism": f"replicas x{world} (independent theta points per GPU)"},
         "tflops": tflops, "tflops_unit": "nominal (2 F_fact + F_selinv) per step / step time",
         "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(p.theta0.shape[0] * 8),
-                "d2h_bytes_per_step": int(8 + 2 * p.N * 8)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B * p.theta0.shape[0] * 8),
+                "d2h_bytes_per_step": int(B * (8 + 2 * p.N * 8))},
+        "batch": B,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
     if world == 1 and not args.no_cpu_baseline:
         from oracle import model as omodel
         fd = omodel.fem_data(p)
-        th = thetas_h[args.warmup]
+        th = thetas_h[args.warmup][0]
         t0 = time.perf_counter()
         oracle_step(p, th, fd)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                                "sample": "one step of the same workload (one theta) on the FP64 "
+                                "sample": "one theta point of the stencil (f_obj + selinv of Q_c) on the FP64 "
                                           "numpy/scipy block recurrences"}
     print(json.dumps(line))
     if dist is not None:

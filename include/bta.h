@@ -55,7 +55,9 @@ extern "C" {
 #define BTA_ERR_CUDA 6       /* a CUDA runtime call failed                       */
 #define BTA_ERR_STATE 7      /* call out of order (e.g. solve before factor)     */
 
-/* Which matrix of the pair. */
+/* Which matrix of a pair.  A context holds `batch` pairs (parameter slots);
+ * the matrix argument `which` of the per-matrix calls is 2 * slot + kind,
+ * so for a context of one slot it is BTA_QP or BTA_QC. */
 #define BTA_QP 0             /* prior precision Q_p (Eq. 1)                      */
 #define BTA_QC 1             /* conditional precision Q_c = Q_p + A^T D A (Eq. 4) */
 
@@ -132,6 +134,13 @@ int bta_model_dims(bta_model_t model, int* n, int* b, int* a, int* dim_theta);
  * Synchronous.  BTA_ERR_OOM if the device memory does not suffice.
  */
 int bta_create(int n, int b, int a, int precision, void* stream, bta_ctx_t* out);
+/* bta_create_batched -- the same with `batch` parameter slots, i.e. storage
+ * for batch pairs (Q_p, Q_c).  fobj_eval runs every slot's pair through the
+ * same kernel launches (the 2 dim(theta) + 1 central-difference points of
+ * Eq. 10 and the two matrices of each are independent, Sections IV-D.1 and
+ * IV-D.2).  bta_create is bta_create_batched with batch = 1. */
+int bta_create_batched(int n, int b, int a, int precision, int batch, void* stream, bta_ctx_t* out);
+int bta_batch_size(bta_ctx_t ctx, int* batch);
 int bta_destroy(bta_ctx_t ctx);
 
 /*
@@ -165,6 +174,9 @@ int bta_theta_to_params(bta_ctx_t ctx, bta_model_t model, const double* theta_de
  * A non-positive pivot records BTA_ERR_NOT_PD in the status word.
  */
 int bta_factor(bta_ctx_t ctx, int which);
+/* bta_factor_batch -- bta_factor of every slot's matrix of kind BTA_QP or
+ * BTA_QC in one pass (all matrices in the same launches). */
+int bta_factor_batch(bta_ctx_t ctx, int kind);
 
 /* bta_logdet -- log|Q| = 2 sum_k log L_kk of factored matrix `which`
  * (Eq. 1), accumulated in FP64, written to the device scalar *out_dev. */
@@ -190,6 +202,9 @@ int bta_solve(bta_ctx_t ctx, int which, const double* rhs_dev, double* x_dev,
  *   Sigma_ii      = L_ii^{-T} L_ii^{-1} - Sigma_{i+1,i}^T G_i - Sigma_{t,i}^T F_i.
  */
 int bta_selinv(bta_ctx_t ctx, int which);
+/* bta_selinv_batch -- bta_selinv of every slot's matrix of kind BTA_QP or
+ * BTA_QC in one pass; all of them must be factored. */
+int bta_selinv_batch(bta_ctx_t ctx, int kind);
 
 /* bta_selinv_diag -- gather the diagonal of the selected inverse of matrix
  * `which` (the marginal variances of Section III, latent marginals) into
@@ -216,8 +231,12 @@ int bta_matvec(bta_ctx_t ctx, int which, const double* x_dev, double* y_dev);
  * which equals log p(theta) + log l(y|theta,mu) + log p(mu|theta)
  * - log p_G(mu|theta,y) because y^T D y - b^T mu = (y - A mu)^T D (y - A mu)
  * + mu^T Q_p mu.  f_out_dev receives n_theta values.  If mu_out_dev is not
- * NULL it receives mu (length N) of the last theta.  The context's Q_p and
- * Q_c hold the last theta's matrices and factors afterwards.
+ * NULL it receives the n_theta conditional means (n_theta x N, row j for
+ * theta j).  The thetas are evaluated in groups of the context's batch size,
+ * each group's 2 x batch matrices going through the same launches; in
+ * mixed precision the solve takes two refinement steps with an FP64
+ * residual.  Afterwards slot j holds the matrices and factors of theta
+ * (last group start + j).
  */
 int fobj_eval(bta_ctx_t ctx, bta_model_t model, const double* thetas_dev, int n_theta,
               double* f_out_dev, double* mu_out_dev);
@@ -226,8 +245,11 @@ int fobj_eval(bta_ctx_t ctx, bta_model_t model, const double* thetas_dev, int n_
  * device recorded since the last bta_sync (and clear it), else BTA_OK. */
 int bta_sync(bta_ctx_t ctx);
 /* bta_last_info -- detail of the last device error: for BTA_ERR_NOT_PD the
- * global row index (0..N-1) of the first non-positive pivot, else -1. */
+ * global row index (0..N-1) of the first non-positive pivot, else -1.
+ * bta_last_error_matrix -- the matrix (2 * slot + kind) it occurred in, -1
+ * if none. */
 int bta_last_info(bta_ctx_t ctx, long long* info);
+int bta_last_error_matrix(bta_ctx_t ctx, int* which);
 /* bta_strerror -- static text of a return code. */
 const char* bta_strerror(int code);
 

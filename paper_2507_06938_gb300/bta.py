@@ -63,6 +63,11 @@ def lib():
         "bta_model_destroy": (ip, [vp]),
         "bta_model_dims": (ip, [vp, C.POINTER(ip), C.POINTER(ip), C.POINTER(ip), C.POINTER(ip)]),
         "bta_create": (ip, [ip, ip, ip, ip, vp, C.POINTER(vp)]),
+        "bta_create_batched": (ip, [ip, ip, ip, ip, ip, vp, C.POINTER(vp)]),
+        "bta_batch_size": (ip, [vp, C.POINTER(ip)]),
+        "bta_factor_batch": (ip, [vp, ip]),
+        "bta_selinv_batch": (ip, [vp, ip]),
+        "bta_last_error_matrix": (ip, [vp, C.POINTER(ip)]),
         "bta_destroy": (ip, [vp]),
         "bta_assemble": (ip, [vp, vp, vp, ip]),
         "bta_theta_to_params": (ip, [vp, vp, vp, vp]),
@@ -98,7 +103,9 @@ def exported_symbols():
             "bta_assemble", "bta_theta_to_params", "bta_factor", "bta_logdet", "bta_solve",
             "bta_selinv", "bta_block_ptr", "bta_matvec", "fobj_eval", "bta_sync", "bta_last_info",
             "bta_strerror", "bta_flops_factor", "bta_flops_selinv", "bta_selinv_diag",
-            "bta_launch_count", "bta_profile", "bta_profile_read", "bta_chol_inv_noalloc"]
+            "bta_launch_count", "bta_profile", "bta_profile_read", "bta_chol_inv_noalloc",
+            "bta_create_batched", "bta_batch_size", "bta_factor_batch", "bta_selinv_batch",
+            "bta_last_error_matrix"]
 
 
 def _check(code: int, where: str):
@@ -186,13 +193,14 @@ class BtaContext:
     """bta_ctx_t: device storage of Q_p and Q_c, their factors and selected
     inverses, bound to a CUDA stream."""
 
-    def __init__(self, n: int, b: int, a: int, precision: int = BTA_FP64, stream=None):
+    def __init__(self, n: int, b: int, a: int, precision: int = BTA_FP64, stream=None, batch: int = 1):
         L = lib()
         self._stream_obj = stream
         h = C.c_void_p()
-        _check(L.bta_create(n, b, a, precision, C.c_void_p(_stream_handle(stream)), C.byref(h)), "bta_create")
+        _check(L.bta_create_batched(n, b, a, precision, batch, C.c_void_p(_stream_handle(stream)), C.byref(h)),
+               "bta_create_batched")
         self.handle = h
-        self.n, self.b, self.a = n, b, a
+        self.n, self.b, self.a, self.batch = n, b, a, batch
         self.N = n * b + a
 
     def __del__(self):
@@ -220,6 +228,12 @@ class BtaContext:
     def selinv(self, which: int):
         _check(lib().bta_selinv(self.handle, which), "bta_selinv")
 
+    def factor_batch(self, kind: int):
+        _check(lib().bta_factor_batch(self.handle, kind), "bta_factor_batch")
+
+    def selinv_batch(self, kind: int):
+        _check(lib().bta_selinv_batch(self.handle, kind), "bta_selinv_batch")
+
     def matvec(self, which: int, x, y):
         _check(lib().bta_matvec(self.handle, which, _ptr(x), _ptr(y)), "bta_matvec")
 
@@ -243,8 +257,12 @@ class BtaContext:
         code = lib().bta_sync(self.handle)
         if code != BTA_OK:
             info = C.c_longlong()
+            mat = C.c_int()
             lib().bta_last_info(self.handle, C.byref(info))
-            raise BtaError(code, "bta_sync", info.value)
+            lib().bta_last_error_matrix(self.handle, C.byref(mat))
+            err = BtaError(code, "bta_sync", info.value)
+            err.matrix = mat.value
+            raise err
 
     def block(self, which: int, store: int, kind: int, i: int = 0):
         """Zero-copy torch view of one stored block (rows x cols, column-major)."""
@@ -266,6 +284,18 @@ def bta_model_create(problem) -> BtaModel:
 
 def bta_create(n, b, a, precision=BTA_FP64, stream=None) -> BtaContext:
     return BtaContext(n, b, a, precision, stream)
+
+
+def bta_create_batched(n, b, a, precision=BTA_FP64, batch=1, stream=None) -> BtaContext:
+    return BtaContext(n, b, a, precision, stream, batch)
+
+
+def bta_factor_batch(ctx: BtaContext, kind: int):
+    ctx.factor_batch(kind)
+
+
+def bta_selinv_batch(ctx: BtaContext, kind: int):
+    ctx.selinv_batch(kind)
 
 
 def bta_assemble(ctx: BtaContext, model: BtaModel, params, which: int):

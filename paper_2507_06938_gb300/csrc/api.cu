@@ -1,13 +1,12 @@
 // Context life cycle, storage accessors, status and error reporting of the
 // C ABI declared in include/bta.h.
 
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 
 #include "common.cuh"
-
-#include <atomic>
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
 static std::atomic<long long> g_launches{0};
@@ -36,93 +35,106 @@ int dalloc(double** p, size_t elems) {
     return BTA_OK;
 }
 
-void mat_free(BtaMat& M) {
+void store_free(BtaStore& M) {
     if (M.D) cudaFree(M.D);
     if (M.B) cudaFree(M.B);
     if (M.R) cudaFree(M.R);
     if (M.T) cudaFree(M.T);
-    M = BtaMat{};
+    M = BtaStore{};
 }
 
-int mat_alloc(BtaMat& M, int n, int b, int a) {
-    const size_t bb = (size_t)b * b;
-    BTA_TRY(dalloc(&M.D, (size_t)n * bb));
-    BTA_TRY(dalloc(&M.B, (size_t)(n > 1 ? n - 1 : 0) * bb));
-    BTA_TRY(dalloc(&M.R, (size_t)n * a * b));
-    BTA_TRY(dalloc(&M.T, (size_t)a * a));
+int store_alloc(BtaStore& M, int nmat, int n, int b, int a) {
+    const long long bb = (long long)b * b;
+    M.sD = n * bb;
+    M.sB = (n > 1 ? n - 1 : 0) * bb;
+    M.sR = (long long)n * a * b;
+    M.sT = (long long)a * a;
+    BTA_TRY(dalloc(&M.D, (size_t)nmat * M.sD));
+    BTA_TRY(dalloc(&M.B, (size_t)nmat * M.sB));
+    BTA_TRY(dalloc(&M.R, (size_t)nmat * M.sR));
+    BTA_TRY(dalloc(&M.T, (size_t)nmat * M.sT));
     return BTA_OK;
 }
 
 }  // namespace
 
-int ensure_sigma(bta_ctx_t ctx, int which) {
-    if (ctx->S[which].D) return BTA_OK;
-    int rc = mat_alloc(ctx->S[which], ctx->n, ctx->b, ctx->a);
-    if (rc != BTA_OK) mat_free(ctx->S[which]);
+int ensure_sigma(bta_ctx_t ctx) {
+    if (ctx->S.D) return BTA_OK;
+    int rc = store_alloc(ctx->S, ctx->nmat, ctx->n, ctx->b, ctx->a);
+    if (rc != BTA_OK) store_free(ctx->S);
     return rc;
 }
 
-extern "C" int bta_create(int n, int b, int a, int precision, void* stream, bta_ctx_t* out) {
-    if (!out || n < 1 || b < 1 || a < 0 || (precision != BTA_FP64 && precision != BTA_MIXED)) return BTA_ERR_ARG;
+extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch, void* stream, bta_ctx_t* out) {
+    if (!out || n < 1 || b < 1 || a < 0 || batch < 1 || (precision != BTA_FP64 && precision != BTA_MIXED))
+        return BTA_ERR_ARG;
     *out = nullptr;
     bta_ctx_s* c = new bta_ctx_s();
     c->n = n; c->b = b; c->a = a; c->precision = precision;
+    c->batch = batch; c->nmat = 2 * batch;
     c->N = (long long)n * b + a;
     c->stream = (cudaStream_t)stream;
     c->leaf = 32;
     if (const char* e = std::getenv("BTA_LEAF")) c->leaf = std::atoi(e);
-    c->vec = nullptr; c->red = nullptr; c->scal = nullptr; c->status = nullptr; c->params = nullptr;
+    c->status = nullptr; c->params = nullptr;
     c->aux = nullptr; c->ev_fork = nullptr; c->ev_join = nullptr;
-    c->exec[0] = GemmExec{};
-    c->exec[1] = GemmExec{};
+    c->exec = GemmExec{};
+    c->factored.assign(c->nmat, 0);
     int rc = BTA_OK;
     auto fail = [&](int r) { bta_destroy(c); return r; };
     if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess) return fail(BTA_ERR_CUDA);
     if (cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) return fail(BTA_ERR_CUDA);
     if (cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) return fail(BTA_ERR_CUDA);
-    const size_t bb = (size_t)b * b;
-    c->work_elems = bb + bb / 2 + 2 * (size_t)b + 2 * (size_t)a * b + (size_t)a * a + 64;
-    for (int w = 0; w < 2; ++w) {
-        if ((rc = mat_alloc(c->Q[w], n, b, a)) != BTA_OK) return fail(rc);
-        if ((rc = mat_alloc(c->L[w], n, b, a)) != BTA_OK) return fail(rc);
-        if ((rc = dalloc(&c->Linv[w], (size_t)n * bb + (size_t)a * a)) != BTA_OK) return fail(rc);
-        if ((rc = dalloc(&c->work[w], c->work_elems)) != BTA_OK) return fail(rc);
-        // the strict upper triangles of the inverse blocks are never written by the factor
-        if (cudaMemset(c->Linv[w], 0, ((size_t)n * bb + (size_t)a * a) * sizeof(double)) != cudaSuccess)
-            return fail(BTA_ERR_CUDA);
-    }
-    c->exec[0] = GemmExec{};
-    c->exec[1] = GemmExec{};
+    const long long bb = (long long)b * b;
+    const int nm = c->nmat;
+    if ((rc = store_alloc(c->Q, nm, n, b, a)) != BTA_OK) return fail(rc);
+    if ((rc = store_alloc(c->L, nm, n, b, a)) != BTA_OK) return fail(rc);
+    c->sLinv = n * bb + (long long)a * a;
+    if ((rc = dalloc(&c->Linv, (size_t)nm * c->sLinv)) != BTA_OK) return fail(rc);
+    // the strict upper triangles of the inverse blocks are never written by the factor
+    if (cudaMemset(c->Linv, 0, (size_t)nm * c->sLinv * sizeof(double)) != cudaSuccess) return fail(BTA_ERR_CUDA);
+    c->sWork = bb + bb / 2 + 2LL * b + 2LL * a * b + (long long)a * a + 64;
+    if ((rc = dalloc(&c->work, (size_t)nm * c->sWork)) != BTA_OK) return fail(rc);
+    if ((rc = dalloc(&c->vec, (size_t)VEC_ROWS * nm * c->N)) != BTA_OK) return fail(rc);
+    c->red_chunks = 256;
+    if ((rc = dalloc(&c->red, (size_t)nm * c->red_chunks)) != BTA_OK) return fail(rc);
+    if ((rc = dalloc(&c->ld, nm)) != BTA_OK) return fail(rc);
+    if ((rc = dalloc(&c->dots, 3 * (size_t)nm)) != BTA_OK) return fail(rc);
+    if ((rc = dalloc(&c->params, (size_t)batch * BTA_PSTRIDE)) != BTA_OK) return fail(rc);
+    if (cudaMemset(c->params, 0, (size_t)batch * BTA_PSTRIDE * sizeof(double)) != cudaSuccess)
+        return fail(BTA_ERR_CUDA);
+    if (cudaMalloc((void**)&c->status, 4 * sizeof(long long)) != cudaSuccess) return fail(BTA_ERR_OOM);
+    if (cudaMemset(c->status, 0, 4 * sizeof(long long)) != cudaSuccess) return fail(BTA_ERR_CUDA);
     c->refine = 0;
     if (precision == BTA_MIXED) {
         if (cudaMalloc((void**)&c->oz_err, sizeof(int)) != cudaSuccess) return fail(BTA_ERR_OOM);
         if (cudaMemset(c->oz_err, 0, sizeof(int)) != cudaSuccess) return fail(BTA_ERR_CUDA);
         int min_dim = 256;
         if (const char* e = std::getenv("BTA_OZ_MIN")) min_dim = std::atoi(e);
-        const size_t wsb = ozaki_workspace_bytes(b, b, b);
-        for (int w = 0; w < 2; ++w) {
-            if (cudaMalloc(&c->exec[w].ws, wsb) != cudaSuccess) {
-                c->exec[w].ws = nullptr;
-                return fail(BTA_ERR_OOM);
-            }
-            c->exec[w].fn = gemm_mixed_fn;
-            c->exec[w].ws_bytes = wsb;
-            c->exec[w].err = c->oz_err;
-            c->exec[w].min_dim = min_dim;
+        const size_t wsb = (size_t)nm * ozaki_workspace_bytes(b, b, b);
+        if (cudaMalloc(&c->exec.ws, wsb) != cudaSuccess) {
+            c->exec.ws = nullptr;
+            return fail(BTA_ERR_OOM);
         }
+        c->exec.fn = gemm_mixed_fn;
+        c->exec.ws_bytes = wsb;
+        c->exec.err = c->oz_err;
+        c->exec.min_dim = min_dim;
         c->refine = 2;
     }
     if (const char* e = std::getenv("BTA_REFINE")) c->refine = std::atoi(e);
-    if ((rc = dalloc(&c->vec, 9 * (size_t)c->N)) != BTA_OK) return fail(rc);
-    c->red_len = 2 * 1216;
-    if ((rc = dalloc(&c->red, c->red_len)) != BTA_OK) return fail(rc);
-    if ((rc = dalloc(&c->scal, SCAL_COUNT)) != BTA_OK) return fail(rc);
-    if ((rc = dalloc(&c->params, 5 * BTA_MAX_NV + BTA_MAX_NV * BTA_MAX_NV)) != BTA_OK) return fail(rc);
-    if (cudaMalloc((void**)&c->status, 2 * sizeof(long long)) != cudaSuccess) return fail(BTA_ERR_OOM);
-    if (cudaMemset(c->status, 0, 2 * sizeof(long long)) != cudaSuccess) return fail(BTA_ERR_CUDA);
-    if (cudaMemset(c->scal, 0, SCAL_COUNT * sizeof(double)) != cudaSuccess) return fail(BTA_ERR_CUDA);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(BTA_ERR_CUDA);
     *out = c;
+    return BTA_OK;
+}
+
+extern "C" int bta_create(int n, int b, int a, int precision, void* stream, bta_ctx_t* out) {
+    return bta_create_batched(n, b, a, precision, 1, stream, out);
+}
+
+extern "C" int bta_batch_size(bta_ctx_t c, int* batch) {
+    if (!c || !batch) return BTA_ERR_ARG;
+    *batch = c->batch;
     return BTA_OK;
 }
 
@@ -130,20 +142,14 @@ extern "C" int bta_destroy(bta_ctx_t c) {
     if (!c) return BTA_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->aux) cudaStreamSynchronize(c->aux);
-    for (int w = 0; w < 2; ++w) {
-        mat_free(c->Q[w]);
-        mat_free(c->L[w]);
-        mat_free(c->S[w]);
-        if (c->Linv[w]) cudaFree(c->Linv[w]);
-        if (c->work[w]) cudaFree(c->work[w]);
-    }
-    for (int w = 0; w < 2; ++w)
-        if (c->exec[w].ws) cudaFree(c->exec[w].ws);
+    store_free(c->Q);
+    store_free(c->L);
+    store_free(c->S);
+    double* bufs[] = {c->Linv, c->work, c->vec, c->red, c->ld, c->dots, c->params};
+    for (double* p : bufs)
+        if (p) cudaFree(p);
+    if (c->exec.ws) cudaFree(c->exec.ws);
     if (c->oz_err) cudaFree(c->oz_err);
-    if (c->vec) cudaFree(c->vec);
-    if (c->red) cudaFree(c->red);
-    if (c->scal) cudaFree(c->scal);
-    if (c->params) cudaFree(c->params);
     if (c->status) cudaFree(c->status);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -154,45 +160,48 @@ extern "C" int bta_destroy(bta_ctx_t c) {
 }
 
 extern "C" int bta_block_ptr(bta_ctx_t c, int which, int store, int kind, int i, double** ptr_out, int* ld_out) {
-    if (!c || !ptr_out || (which != BTA_QP && which != BTA_QC)) return BTA_ERR_ARG;
-    const size_t bb = (size_t)c->b * c->b, ab = (size_t)c->a * c->b;
-    const BtaMat* M = nullptr;
-    if (store == BTA_STORE_Q) M = &c->Q[which];
-    else if (store == BTA_STORE_L) M = &c->L[which];
-    else if (store == BTA_STORE_SIGMA) M = &c->S[which];
-    else if (store != BTA_STORE_LINV) return BTA_ERR_ARG;
+    if (!c || !ptr_out) return BTA_ERR_ARG;
+    const int m = storage_index(c, which);
+    if (m < 0) return BTA_ERR_ARG;
+    const long long bb = (long long)c->b * c->b, ab = (long long)c->a * c->b;
     if (store == BTA_STORE_LINV) {
+        double* base = c->Linv + m * c->sLinv;
         if (kind == BTA_BLK_D && i >= 0 && i < c->n) {
-            *ptr_out = c->Linv[which] + i * bb;
+            *ptr_out = base + i * bb;
             if (ld_out) *ld_out = c->b;
             return BTA_OK;
         }
         if (kind == BTA_BLK_T) {
-            *ptr_out = c->Linv[which] + (size_t)c->n * bb;
+            *ptr_out = base + (long long)c->n * bb;
             if (ld_out) *ld_out = c->a;
             return BTA_OK;
         }
         return BTA_ERR_ARG;
     }
+    const BtaStore* M = nullptr;
+    if (store == BTA_STORE_Q) M = &c->Q;
+    else if (store == BTA_STORE_L) M = &c->L;
+    else if (store == BTA_STORE_SIGMA) M = &c->S;
+    else return BTA_ERR_ARG;
     if (!M->D) return BTA_ERR_STATE;
     switch (kind) {
         case BTA_BLK_D:
             if (i < 0 || i >= c->n) return BTA_ERR_ARG;
-            *ptr_out = M->D + i * bb;
+            *ptr_out = M->D + m * M->sD + i * bb;
             if (ld_out) *ld_out = c->b;
             return BTA_OK;
         case BTA_BLK_B:
             if (i < 0 || i >= c->n - 1) return BTA_ERR_ARG;
-            *ptr_out = M->B + i * bb;
+            *ptr_out = M->B + m * M->sB + i * bb;
             if (ld_out) *ld_out = c->b;
             return BTA_OK;
         case BTA_BLK_R:
             if (i < 0 || i >= c->n) return BTA_ERR_ARG;
-            *ptr_out = M->R + i * ab;
+            *ptr_out = M->R + m * M->sR + i * ab;
             if (ld_out) *ld_out = c->a;
             return BTA_OK;
         case BTA_BLK_T:
-            *ptr_out = M->T;
+            *ptr_out = M->T + m * M->sT;
             if (ld_out) *ld_out = c->a;
             return BTA_OK;
         default:
@@ -246,7 +255,7 @@ extern "C" int bta_sync(bta_ctx_t c) {
     if (cudaStreamSynchronize(c->aux) != cudaSuccess) return bta_cuda_fail(cudaGetLastError());
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bta_cuda_fail(e);
-    long long st[2];
+    long long st[3];
     e = cudaMemcpy(st, c->status, sizeof(st), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return bta_cuda_fail(e);
     if (c->oz_err) {
@@ -256,22 +265,31 @@ extern "C" int bta_sync(bta_ctx_t c) {
         if (oz) {
             cudaMemset(c->oz_err, 0, sizeof(int));
             c->last_info = -1;
+            c->last_matrix = -1;
             return BTA_ERR_TIMEOUT;
         }
     }
     if (st[0] != 0) {
         c->last_info = st[1];
-        long long zero[2] = {0, 0};
+        c->last_matrix = (int)st[2];
+        long long zero[3] = {0, 0, 0};
         cudaMemcpy(c->status, zero, sizeof(zero), cudaMemcpyHostToDevice);
         return (int)st[0];
     }
     c->last_info = -1;
+    c->last_matrix = -1;
     return BTA_OK;
 }
 
 extern "C" int bta_last_info(bta_ctx_t c, long long* info) {
     if (!c || !info) return BTA_ERR_ARG;
     *info = c->last_info;
+    return BTA_OK;
+}
+
+extern "C" int bta_last_error_matrix(bta_ctx_t c, int* which) {
+    if (!c || !which) return BTA_ERR_ARG;
+    *which = c->last_matrix;
     return BTA_OK;
 }
 

@@ -14,6 +14,7 @@
 // out with coalesced stores: the kernel is bound by the HBM write of the
 // dense blocks.
 
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -43,7 +44,9 @@ __device__ __forceinline__ double ar1_entry(double rho, int nt, int ti, int tj) 
 }
 
 struct AsmArgs {
-    int n, b, a, ns, nv, nr, nt, nnz, with_obs;
+    int n, b, a, ns, nv, nr, nt, nnz;
+    int m0, batch;           // matrices m0 + blockIdx.z; kind = m / batch, slot = m % batch
+    long long sD, sB, sR, sT;
     const int* rowptr;
     const int* col;
     const double* cval;
@@ -52,7 +55,8 @@ struct AsmArgs {
     const double* gram;
     const double* arrow;
     const double* tipgram;
-    const double* params;
+    const double* params;    // parameter slots, pstride apart (0: one vector for all)
+    long long pstride;
     double beta_prec;
     double* D;
     double* B;
@@ -60,11 +64,15 @@ struct AsmArgs {
     double* T;
 };
 
-// grid: x = column j (0..b-1), y = block: 0..n-1 -> D_y, n..2n-2 -> B_{y-n}
+// grid: x = column j (0..b-1), y = block: 0..n-1 -> D_y, n..2n-2 -> B_{y-n},
+// z = matrix
 __global__ void __launch_bounds__(ASM_THREADS) assemble_db_kernel(AsmArgs p) {
     extern __shared__ double colbuf[];   // b doubles
     __shared__ double coef[BTA_MAX_NV][3];
     __shared__ double obsw[BTA_MAX_NV];
+    const int mat = p.m0 + blockIdx.z;
+    const int with_obs = mat / p.batch;           // 0: Q_p, 1: Q_c
+    const double* params = p.params + (long long)(mat % p.batch) * p.pstride;
     const int j = blockIdx.x;
     const int blk = blockIdx.y;
     const bool diag = blk < p.n;
@@ -72,12 +80,12 @@ __global__ void __launch_bounds__(ASM_THREADS) assemble_db_kernel(AsmArgs p) {
     const int trow = diag ? t : t + 1;                 // row time index
     const int vp = j / p.ns, sp = j % p.ns;
     const int nv = p.nv;
-    const double* lam = p.params + 5 * nv;
+    const double* lam = params + 5 * nv;
     if (threadIdx.x < nv) {
         const int v = threadIdx.x;
         double ca = 0, cb = 0, cg = 0;
         for (int u = 0; u < nv; ++u) {
-            const double* pu = p.params + 5 * u;
+            const double* pu = params + 5 * u;
             const double kappa = pu[0], tau = pu[1], rho = pu[2], sigma = pu[3];
             double c = minv_entry(lam, nv, u, v) * minv_entry(lam, nv, u, vp) / (sigma * sigma);
             if (c == 0.0) continue;
@@ -90,7 +98,7 @@ __global__ void __launch_bounds__(ASM_THREADS) assemble_db_kernel(AsmArgs p) {
         coef[v][0] = ca;
         coef[v][1] = cb;
         coef[v][2] = cg;
-        obsw[v] = (p.with_obs && diag && v == vp) ? p.params[5 * v + 4] : 0.0;
+        obsw[v] = (with_obs && diag && v == vp) ? params[5 * v + 4] : 0.0;
     }
     for (int r = threadIdx.x; r < p.b; r += ASM_THREADS) colbuf[r] = 0.0;
     __syncthreads();
@@ -106,17 +114,22 @@ __global__ void __launch_bounds__(ASM_THREADS) assemble_db_kernel(AsmArgs p) {
         colbuf[v * p.ns + s] = val;
     }
     __syncthreads();
-    double* out = diag ? p.D + (size_t)t * p.b * p.b : p.B + (size_t)t * p.b * p.b;
+    double* out = diag ? p.D + mat * p.sD + (size_t)t * p.b * p.b : p.B + mat * p.sB + (size_t)t * p.b * p.b;
     out += (size_t)j * p.b;
     for (int r = threadIdx.x; r < p.b; r += ASM_THREADS) out[r] = colbuf[r];
 }
 
 // R_t and T: one thread per entry.  Entries 0..n*a*b-1 are R (column-major
-// per block), then a*a entries of T.
+// per block), then a*a entries of T; blockIdx.y = matrix.
 __global__ void assemble_rt_kernel(AsmArgs p) {
     const long long total = (long long)p.n * p.a * p.b + (long long)p.a * p.a;
     const int nv = p.nv, nr = p.nr;
-    const double* lam = p.params + 5 * nv;
+    const int mat = p.m0 + blockIdx.y;
+    const int with_obs = mat / p.batch;
+    const double* params = p.params + (long long)(mat % p.batch) * p.pstride;
+    const double* lam = params + 5 * nv;
+    double* R = p.R + mat * p.sR;
+    double* T = p.T + mat * p.sT;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const long long nab = (long long)p.n * p.a * p.b;
@@ -127,10 +140,9 @@ __global__ void assemble_rt_kernel(AsmArgs p) {
             const int v = row / nr, r = row % nr;
             const int vp = colj / p.ns, s = colj % p.ns;
             double val = 0.0;
-            if (p.with_obs && v == vp)
-                val = p.params[5 * v + 4] *
-                      p.arrow[(((size_t)t * nv + v) * nr + r) * p.ns + s];
-            p.R[idx] = val;
+            if (with_obs && v == vp)
+                val = params[5 * v + 4] * p.arrow[(((size_t)t * nv + v) * nr + r) * p.ns + s];
+            R[idx] = val;
         } else {
             const int e = (int)(idx - nab);
             const int colj = e / p.a, row = e % p.a;
@@ -139,19 +151,22 @@ __global__ void assemble_rt_kernel(AsmArgs p) {
             double val = 0.0;
             if (r == rp) {
                 for (int u = 0; u < nv; ++u) {
-                    const double sigma = p.params[5 * u + 3];
+                    const double sigma = params[5 * u + 3];
                     val += minv_entry(lam, nv, u, v) * minv_entry(lam, nv, u, vp) / (sigma * sigma);
                 }
                 val *= p.beta_prec;
             }
-            if (p.with_obs && v == vp)
-                val += p.params[5 * v + 4] * p.tipgram[((size_t)v * nr + r) * nr + rp];
-            p.T[e] = val;
+            if (with_obs && v == vp)
+                val += params[5 * v + 4] * p.tipgram[((size_t)v * nr + r) * nr + rp];
+            T[e] = val;
         }
     }
 }
 
-__global__ void theta_to_params_kernel(const double* theta, int nv, double* params) {
+// blockIdx.x = slot: theta + slot dim_theta -> params + slot BTA_PSTRIDE
+__global__ void theta_to_params_kernel(const double* theta, int nv, int dim_theta, double* params) {
+    theta += (long long)blockIdx.x * dim_theta;
+    params += (long long)blockIdx.x * BTA_PSTRIDE;
     const int i = threadIdx.x;
     if (i < nv) {
         const double range_s = exp(theta[4 * i + 0]);
@@ -169,49 +184,59 @@ __global__ void theta_to_params_kernel(const double* theta, int nv, double* para
 
 }  // namespace
 
-int theta_to_params_impl(bta_model_t m, const double* theta, double* params, cudaStream_t s) {
-    theta_to_params_kernel<<<1, 64, 0, s>>>(theta, m->nv, params);
+int theta_to_params_impl(bta_model_t m, const double* theta, int count, double* params, cudaStream_t s) {
+    if (count <= 0) return BTA_OK;
+    theta_to_params_kernel<<<count, 64, 0, s>>>(theta, m->nv, m->dim_theta, params);
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }
 
-int assemble_impl(bta_ctx_t ctx, bta_model_t m, const double* params, int which, cudaStream_t s) {
+static int assemble_run(bta_ctx_t ctx, bta_model_t m, const double* params, long long pstride, int m0, int count,
+                        cudaStream_t s) {
+    if (count <= 0) return BTA_OK;
     AsmArgs p;
     p.n = ctx->n; p.b = ctx->b; p.a = ctx->a;
     p.ns = m->ns; p.nv = m->nv; p.nr = m->nr; p.nt = m->nt; p.nnz = m->nnz;
-    p.with_obs = (which == BTA_QC);
+    p.m0 = m0; p.batch = ctx->batch;
     p.rowptr = m->rowptr; p.col = m->col;
     p.cval = m->cval; p.gval = m->gval; p.kval = m->kval; p.gram = m->gram;
     p.arrow = m->arrow; p.tipgram = m->tipgram;
     p.params = params;
+    p.pstride = pstride;
     p.beta_prec = m->beta_prec;
-    const BtaMat& Q = ctx->Q[which];
+    const BtaStore& Q = ctx->Q;
     p.D = Q.D; p.B = Q.B; p.R = Q.R; p.T = Q.T;
+    p.sD = Q.sD; p.sB = Q.sB; p.sR = Q.sR; p.sT = Q.sT;
     const size_t smem = (size_t)p.b * sizeof(double);
     if (smem > 48 * 1024)
         BTA_CUDA_TRY(cudaFuncSetAttribute(assemble_db_kernel,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid(p.b, 2 * p.n - 1);
+    dim3 grid(p.b, 2 * p.n - 1, count);
     assemble_db_kernel<<<grid, ASM_THREADS, smem, s>>>(p);
     BTA_LAUNCH_CHECK();
     const long long total = (long long)p.n * p.a * p.b + (long long)p.a * p.a;
     if (total > 0) {
         int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 16);
-        assemble_rt_kernel<<<blocks, 256, 0, s>>>(p);
+        assemble_rt_kernel<<<dim3(blocks, count), 256, 0, s>>>(p);
         BTA_LAUNCH_CHECK();
     }
-    ctx->factored[which] = 0;
+    for (int k = m0; k < m0 + count; ++k) ctx->factored[k] = 0;
     return BTA_OK;
 }
 
-extern "C" int bta_assemble(bta_ctx_t ctx, bta_model_t m, const double* params_dev, int which) {
-    if (!ctx || !m || !params_dev || (which != BTA_QP && which != BTA_QC)) return BTA_ERR_ARG;
-    if (m->n != ctx->n || m->b != ctx->b || m->a != ctx->a) return BTA_ERR_ARG;
-    return assemble_impl(ctx, m, params_dev, which, ctx->stream);
+int assemble_impl(bta_ctx_t ctx, bta_model_t m, const double* params, int m0, int count, cudaStream_t s) {
+    return assemble_run(ctx, m, params, BTA_PSTRIDE, m0, count, s);
 }
 
-extern "C" int bta_theta_to_params(bta_ctx_t ctx, bta_model_t m, const double* theta_dev,
-                                   double* params_dev) {
+extern "C" int bta_assemble(bta_ctx_t ctx, bta_model_t m, const double* params_dev, int which) {
+    if (!ctx || !m || !params_dev) return BTA_ERR_ARG;
+    if (m->n != ctx->n || m->b != ctx->b || m->a != ctx->a || m->nv > BTA_MAX_NV) return BTA_ERR_ARG;
+    const int mat = storage_index(ctx, which);
+    if (mat < 0) return BTA_ERR_ARG;
+    return assemble_run(ctx, m, params_dev, 0, mat, 1, ctx->stream);
+}
+
+extern "C" int bta_theta_to_params(bta_ctx_t ctx, bta_model_t m, const double* theta_dev, double* params_dev) {
     if (!ctx || !m || !theta_dev || !params_dev) return BTA_ERR_ARG;
-    return theta_to_params_impl(m, theta_dev, params_dev, ctx->stream);
+    return theta_to_params_impl(m, theta_dev, 1, params_dev, ctx->stream);
 }

@@ -9,6 +9,8 @@
 #include "bta.h"
 
 #define BTA_MAX_NV 8
+// doubles per parameter slot: [kappa, tau, rho, sigma, tau_eps] x nv + lambda
+#define BTA_PSTRIDE (5 * BTA_MAX_NV + BTA_MAX_NV * BTA_MAX_NV)
 
 // ---------------------------------------------------------------- error plumbing
 #define BTA_CUDA_TRY(expr)                                   \
@@ -55,6 +57,8 @@ struct bta_model_s {
 };
 
 // ---------------------------------------------------------------- dense GEMM descriptor
+// C = alpha op(A) op(B) + beta Cin for `batch` independent products whose
+// operands are `sA`, `sB`, `sCi`, `sC` elements apart.
 struct Gemm64 {
     int M, N, K;
     const double* A; long long lda; int ta; int shA;   // shA: shape of op(A): 0 general, 1 lower, 2 upper
@@ -71,42 +75,53 @@ struct Gemm64 {
 // large ones in mixed precision).
 struct GemmExec {
     int (*fn)(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
-    void* ws;          // digit workspace (mixed path)
+    void* ws;          // digit workspace (mixed path), for all matrices of a batch
     size_t ws_bytes;
     int* err;          // device error flag of the tensor-core kernel
     int min_dim;       // smallest M, N (and K) sent to the tensor-core path
 };
 
 // ---------------------------------------------------------------- BTA storage
-struct BtaMat {
-    double* D = nullptr;     // n * b * b
+// `nmat` BTA matrices of one shape, matrix after matrix: the blocks of matrix
+// m start at D + m sD, B + m sB, R + m sR, T + m sT.
+struct BtaStore {
+    double* D = nullptr;     // n * b * b per matrix
     double* B = nullptr;     // (n-1) * b * b
     double* R = nullptr;     // n * a * b
     double* T = nullptr;     // a * a
+    long long sD = 0, sB = 0, sR = 0, sT = 0;
 };
+
+// Scratch vectors: row r of matrix m is vec + (r * nmat + m) * N.
+enum { VEC_RCOPY = 0, VEC_RES, VEC_CORR, VEC_Z, VEC_TMP, VEC_RHS, VEC_MU, VEC_ROWS };
 
 struct bta_ctx_s {
     int n, b, a, precision;
+    int batch;               // parameter slots; matrix storage index m = kind * batch + slot
+    int nmat;                // 2 * batch
     long long N;
     cudaStream_t stream;
-    cudaStream_t aux;        // second stream: Q_p runs beside Q_c inside fobj_eval
+    cudaStream_t aux;        // second stream for a partial batch (Q_p beside Q_c)
     cudaEvent_t ev_fork, ev_join;
-    BtaMat Q[2], L[2], S[2];
-    double* Linv[2] = {nullptr, nullptr};   // n * b * b, then a * a (tip)
-    double* work[2] = {nullptr, nullptr};   // per-matrix scratch for the factor / selinv
-    size_t work_elems;
-    double* vec;             // vectors: 4 * N
-    double* red;             // reduction partials
-    int red_len;
-    double* scal;            // device scalars (see SCAL_* below)
-    long long* status;       // [0] error code, [1] info
-    double* params;          // model parameters of the last fobj_eval
-    GemmExec exec[2];        // per matrix (Q_p and Q_c run on different streams)
+    BtaStore Q, L, S;
+    double* Linv = nullptr;  // per matrix: n b^2, then a^2 (tip)
+    long long sLinv = 0;
+    double* work = nullptr;  // per-matrix scratch of the factor / selinv
+    long long sWork = 0;
+    double* vec = nullptr;   // VEC_ROWS x nmat x N
+    double* red = nullptr;   // reduction partials
+    int red_chunks = 0;      // partial sums per matrix
+    double* ld = nullptr;    // log-determinant of every matrix (nmat)
+    double* dots = nullptr;  // per-matrix scalars: [0] b^T mu, [1] |r|^2, [2] |b|^2 (3 x nmat)
+    long long* status;       // [0] error code, [1] row, [2] matrix (public index)
+    double* params;          // parameter slots (batch x BTA_PSTRIDE)
+    GemmExec exec;
     int* oz_err = nullptr;   // device flag of the tensor-core GEMM (time-out)
     int refine = 0;          // refinement steps of the f_obj solve
-    int factored[2] = {0, 0};
+    std::vector<int> factored;   // per storage index
     int leaf;                // leaf size of the recursive diagonal factorisation
     long long last_info = -1;
+    int last_matrix = -1;
     // optional event timing of the b x b x b Schur-update GEMM launches
     int prof = 0;
     std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
@@ -114,58 +129,66 @@ struct bta_ctx_s {
     double prof_flops = 0.0;
 };
 
+// public matrix index (2 slot + kind) <-> storage index (kind batch + slot)
+inline int storage_index(const bta_ctx_s* c, int which) {
+    if (which < 0 || which >= 2 * c->batch) return -1;
+    return (which % 2) * c->batch + which / 2;
+}
+inline int public_index(const bta_ctx_s* c, int m) { return 2 * (m % c->batch) + m / c->batch; }
+
 // Record an event pair around the next launch on stream s when profiling.
 int prof_begin(bta_ctx_t ctx, cudaStream_t s, double flops, cudaEvent_t* stop_out);
 
-enum {
-    SCAL_LOGDET_P = 0,
-    SCAL_LOGDET_C = 1,
-    SCAL_DOT = 2,
-    SCAL_NRM_R = 3,
-    SCAL_NRM_B = 4,
-    SCAL_COUNT = 16
-};
-
 // ---------------------------------------------------------------- FP64 dense kernels (dense64.cu)
-
-
 int gemm64(cudaStream_t s, const Gemm64& g);
-
-
 int gemm_exec(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
 
+// Recursive Cholesky + inverse of `batch` lower n x n matrices (strides sA, sX;
+// scratch W with stride sW).  status receives the first non-positive pivot:
+// row row0 + k of the matrix with storage index m_first + instance, reported
+// by its public index for a context of `nbatch` parameter slots.
 int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ldx, int n,
-               long long row0, long long* status, double* W, int leaf, const GemmExec* ex = nullptr);
+               long long row0, long long* status, double* W, int leaf, const GemmExec* ex = nullptr,
+               int batch = 1, long long sA = 0, long long sX = 0, long long sW = 0, int m_first = 0,
+               int nbatch = 1);
 int copy_mat64(cudaStream_t s, const double* src, long long lds, double* dst, long long ldd,
-               int rows, int cols, int lower_only);
+               int rows, int cols, int lower_only, int batch = 1, long long ss = 0, long long sd = 0);
 // C = beta Cin (C = 0 if beta == 0); only entries m >= n when lower
 int scale_into64(cudaStream_t s, int M, int N, const double* Cin, long long ldci, double beta, double* C,
-                 long long ldc, int lower);
-// Digit-split tensor-core GEMM (ozaki.cu): same contract as gemm64 (batch 1).
-size_t ozaki_workspace_bytes(int M, int N, int K);
-int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err);
-int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
-int symmetrize_lower64(cudaStream_t s, double* A, long long lda, int n);
+                 long long ldc, int lower, int batch = 1, long long sCi = 0, long long sC = 0);
+int symmetrize_lower64(cudaStream_t s, double* A, long long lda, int n, int batch = 1, long long sA = 0);
 // y = alpha * op(A) x + beta * yin   (op(A) shape: 0 general, 1 lower, 2 upper)
 int gemv64(cudaStream_t s, int M, int N, const double* A, long long lda, int ta, int sh,
            const double* x, double alpha, const double* yin, double beta, double* y, int batch = 1,
            long long sA = 0, long long sx = 0, long long sy = 0);
-// out[0] = sum_i log(A[i*(lda+1)]) for the diagonals of `count` blocks spaced by `stride`
-int logdiag_sum64(cudaStream_t s, const double* A, long long lda, int dim, int count,
-                  long long stride, double* partial, int partial_len, double* out, double scale,
-                  int accumulate);
-// out = sum x_i y_i (two-pass, deterministic)
-int dot64(cudaStream_t s, const double* x, const double* y, long long len, double* partial,
-          int partial_len, double* out);
+// out[m] = scale * (sum_k log A_m[k (lda+1)] over `nblk` diagonal blocks of
+// dimension dim spaced by `stride`, + sum_k log T_m[k (a+1)] over the tip)
+int logdet_batch64(cudaStream_t s, const double* A, long long lda, int dim, int nblk, long long stride,
+                   long long sA, const double* T, int a, long long sT, int count, double* partial,
+                   int chunks, double* out, double scale);
+// out[m * ostride] = sum_i x_m[i] y_m[i] for `count` vector pairs of length len
+int dot_batch64(cudaStream_t s, const double* x, const double* y, long long len, int count, double* partial,
+                int chunks, double* out, long long ostride);
 
-// ---------------------------------------------------------------- internal drivers
-int factor_impl(bta_ctx_t ctx, int which, cudaStream_t s);
-int logdet_impl(bta_ctx_t ctx, int which, double* out, cudaStream_t s);
-int solve_impl(bta_ctx_t ctx, int which, const double* rhs, double* x, cudaStream_t s);
-int matvec_impl(bta_ctx_t ctx, int which, const double* x, double* y, cudaStream_t s);
-int assemble_impl(bta_ctx_t ctx, bta_model_t m, const double* params, int which, cudaStream_t s);
-int theta_to_params_impl(bta_model_t m, const double* theta, double* params, cudaStream_t s);
-int ensure_sigma(bta_ctx_t ctx, int which);
-int selinv_impl(bta_ctx_t ctx, int which, cudaStream_t s);
+// ---------------------------------------------------------------- tensor cores (ozaki.cu)
+size_t ozaki_workspace_bytes(int M, int N, int K);
+// same contract as gemm64 (any batch); ws holds batch x ozaki_workspace_bytes
+int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err);
+int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
+
+// ---------------------------------------------------------------- drivers on matrices m0 .. m0+count-1
+int factor_impl(bta_ctx_t ctx, int m0, int count, cudaStream_t s);
+int logdet_impl(bta_ctx_t ctx, int m0, int count, double* out, cudaStream_t s);
+// x_j = Q_{m0+j}^{-1} r_j, vectors N apart
+int solve_impl(bta_ctx_t ctx, int m0, int count, const double* r, double* x, cudaStream_t s);
+int matvec_impl(bta_ctx_t ctx, int m0, int count, const double* x, double* y, cudaStream_t s);
+int selinv_impl(bta_ctx_t ctx, int m0, int count, cudaStream_t s);
+// assemble matrices m0.. (kind = m / batch, parameters of slot m % batch at
+// params + slot * BTA_PSTRIDE)
+int assemble_impl(bta_ctx_t ctx, bta_model_t m, const double* params, int m0, int count, cudaStream_t s);
+// theta (count x dim_theta) -> parameter slots (count x BTA_PSTRIDE)
+int theta_to_params_impl(bta_model_t m, const double* theta, int count, double* params, cudaStream_t s);
+int ensure_sigma(bta_ctx_t ctx);
 int axpby64(cudaStream_t s, long long len, double alpha, const double* x, double beta, const double* y,
             double* out);
+inline double* vec_row(bta_ctx_t c, int row, int m) { return c->vec + ((long long)row * c->nmat + m) * c->N; }

@@ -1,9 +1,10 @@
 // FP64 dense building blocks of the BTA factorisation, solve and selected
 // inversion: a tiled DFMA GEMM with triangular-operand and lower-output
 // variants, the recursive diagonal-block Cholesky + inverse, matrix copies,
-// GEMV and deterministic reductions.  On GB300 the FP64 pipe (measured about
-// 1.2 TFLOP/s for DFMA, below DMMA's 1.05) bounds all of these except the
-// GEMV and copies, which are bound by HBM.
+// GEMV and deterministic reductions, all batched over independent matrices
+// (blockIdx.z / blockIdx.y = matrix).  On GB300 the FP64 pipe (measured
+// 1.2 TFLOP/s for DFMA, 1.05 for DMMA) bounds the GEMM and the Cholesky;
+// the GEMV and copies are bound by HBM.
 
 #include <algorithm>
 #include <cmath>
@@ -16,8 +17,8 @@ namespace {
 // Tile (16 MI) x (16 NJ) x 16 per CTA of 256 threads; thread (tx, ty),
 // tx = tid % 16 along m, ty = tid / 16 along n, owns rows m0 + tx + 16 i and
 // columns n0 + ty + 16 j.  Column-major output: lanes write consecutive rows.
-// blockIdx.z is the batch index, or the K split when ksplit > 1 (then every
-// split atomically adds alpha * partial into a C that already holds beta Cin).
+// blockIdx.z = matrix * ksplit + split; with ksplit > 1 every split atomically
+// adds alpha * partial into a C that already holds beta Cin.
 constexpr int BK = 16, GT = 256;
 
 __device__ __forceinline__ double load_opA(const Gemm64& p, const double* A, int m, int k, int kend) {
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(GT) gemm64_kernel(Gemm64 p, int ksplit) {
     __shared__ double Bs[BK][TBN + 1];
     const int m0 = blockIdx.x * TBM, n0 = blockIdx.y * TBN;
     if (p.lowerC && m0 + TBM - 1 < n0) return;
-    const int z = ksplit > 1 ? 0 : blockIdx.z;
+    const int z = blockIdx.z / ksplit, split = blockIdx.z % ksplit;
     const double* A = p.A + z * p.sA;
     const double* B = p.B + z * p.sB;
     const double* Cin = p.Cin ? p.Cin + z * p.sCi : nullptr;
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(GT) gemm64_kernel(Gemm64 p, int ksplit) {
         // split [kb, ke) into ksplit chunks of whole BK tiles
         const int tiles = (ke - kb + BK - 1) / BK;
         const int per = (tiles + ksplit - 1) / ksplit;
-        const int s0 = kb + blockIdx.z * per * BK;
+        const int s0 = kb + split * per * BK;
         const int s1 = min(ke, s0 + per * BK);
         kb = s0;
         ke = s1;
@@ -118,35 +119,56 @@ __global__ void __launch_bounds__(GT) gemm64_kernel(Gemm64 p, int ksplit) {
 }
 
 // C = beta Cin (entries m >= n only when lower), the start of a split-K GEMM.
+// blockIdx.y = matrix.
 __global__ void scale_into_kernel(int M, int N, const double* Cin, long long ldci, double beta, double* C,
-                                  long long ldc, int lower, int batch, long long sCi, long long sC) {
-    const long long total = (long long)M * N * batch;
+                                  long long ldc, int lower, long long sCi, long long sC) {
+    const long long total = (long long)M * N;
+    C += blockIdx.y * sC;
+    if (Cin) Cin += blockIdx.y * sCi;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const long long z = e / ((long long)M * N);
-        const long long r = e - z * M * N;
-        const int i = (int)(r % M), j = (int)(r / M);
+        const int i = (int)(e % M), j = (int)(e / M);
         if (lower && i < j) continue;
-        C[z * sC + i + j * ldc] = (beta != 0.0 && Cin) ? beta * Cin[z * sCi + i + j * ldci] : 0.0;
+        C[i + j * ldc] = (beta != 0.0 && Cin) ? beta * Cin[i + j * ldci] : 0.0;
     }
 }
 
 // ---------------------------------------------------------------- leaf Cholesky + inverse
-// One CTA factors an n x n (n <= 64) lower block A = L L^T in shared memory and
-// forms X = L^{-1} by right-looking forward elimination of L X = I.  Iteration
-// k updates the trailing matrix with column k and eliminates with column k-1
-// of L, so each iteration needs a single barrier.  Output: L and X (lower; the
+// One CTA per matrix factors an n x n (n <= 64) lower block A = L L^T in
+// shared memory and forms X = L^{-1} by right-looking forward elimination of
+// L X = I.  Iteration k updates the trailing matrix with column k of L and
+// eliminates with column k-1, so each iteration needs one barrier.  The
+// reciprocal square root of pivot k+1 is computed by the thread that finishes
+// that pivot in iteration k (Newton-Raphson for 1/sqrt, seeded in FP32), so
+// no FP64 division or square root sits on the critical path: FP64 latency,
+// not throughput, bounds this kernel on GB300.  Output: L and X (lower; the
 // strict upper parts of both tiles are written as zeros).
 constexpr int LEAF_MAX = 64;
 constexpr int LDS = LEAF_MAX + 1;
 
-__global__ void __launch_bounds__(256) chol_inv_leaf_kernel(double* A, long long lda, double* X,
-                                                            long long ldx, int n, long long row0,
-                                                            long long* status) {
+// 1/sqrt(d) by two Newton-Raphson steps y <- y (3 - d y^2) / 2 from an FP32
+// estimate, after scaling d by an even power of two into [1, 4); NaN unless
+// d > 0.
+__device__ __forceinline__ double newton_rsqrt(double d) {
+    if (!(d > 0.0) || isinf(d)) return nan("");
+    const int e = ilogb(d) & ~1;
+    const double m = ldexp(d, -e);
+    double y = (double)rsqrtf((float)m);
+    y = y * (1.5 - 0.5 * m * y * y);
+    y = y * (1.5 - 0.5 * m * y * y);
+    return ldexp(y, -e / 2);
+}
+
+__global__ void __launch_bounds__(256) chol_inv_leaf_kernel(double* A, long long lda, long long sA, double* X,
+                                                            long long ldx, long long sX, int n, long long row0,
+                                                            long long* status, int m_first, int nbatch) {
     extern __shared__ double sm[];
     double* S = sm;                 // working matrix, column-major, ld LDS
     double* L = sm + LDS * LEAF_MAX;
     double* W = sm + 2 * LDS * LEAF_MAX;
+    double* ys = sm + 3 * LDS * LEAF_MAX;   // 1/L_kk
+    A += blockIdx.x * sA;
+    X += blockIdx.x * sX;
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
     for (int e = tid; e < n * n; e += nthr) {
@@ -155,6 +177,8 @@ __global__ void __launch_bounds__(256) chol_inv_leaf_kernel(double* A, long long
         W[j * LDS + i] = (i == j) ? 1.0 : 0.0;
         L[j * LDS + i] = 0.0;
     }
+    __syncthreads();
+    if (tid == 0) ys[0] = newton_rsqrt(S[0]);
     const int rows_per = n <= 32 ? 32 : LEAF_MAX;
     const int row = tid % rows_per;      // row handled by this thread
     const int lane_q = tid / rows_per;   // column phase
@@ -162,29 +186,33 @@ __global__ void __launch_bounds__(256) chol_inv_leaf_kernel(double* A, long long
     for (int k = 0; k <= n; ++k) {
         __syncthreads();
         if (k < n) {
-            const double dkk = S[k * LDS + k];
-            if (tid == 0 && !(dkk > 0.0) && status) {
-                if (atomicCAS((unsigned long long*)status, 0ull, (unsigned long long)BTA_ERR_NOT_PD) == 0ull)
+            const double y = ys[k];
+            if (tid == 0 && !(y > 0.0) && status) {
+                if (atomicCAS((unsigned long long*)status, 0ull, (unsigned long long)BTA_ERR_NOT_PD) == 0ull) {
                     status[1] = row0 + k;
+                    const int mm = m_first + (int)blockIdx.x;   // storage index -> public index
+                    status[2] = 2 * (mm % nbatch) + mm / nbatch;
+                }
             }
-            const double rk = dkk > 0.0 ? sqrt(dkk) : nan("");
-            const double rinv = 1.0 / rk;
-            const double dinv = rinv * rinv;
-            if (row >= k && row < n && lane_q == 0) L[k * LDS + row] = S[k * LDS + row] * rinv;
+            if (row >= k && row < n && lane_q == 0) L[k * LDS + row] = S[k * LDS + row] * y;
             if (row > k && row < n) {
-                const double sik = S[k * LDS + row] * dinv;
-                for (int j = k + 1 + lane_q; j <= row; j += nq) S[j * LDS + row] -= sik * S[k * LDS + j];
+                const double sik = S[k * LDS + row] * (y * y);
+                for (int j = k + 1 + lane_q; j <= row; j += nq) {
+                    const double v = S[j * LDS + row] - sik * S[k * LDS + j];
+                    S[j * LDS + row] = v;
+                    if (j == k + 1 && row == k + 1) ys[k + 1] = newton_rsqrt(v);   // next pivot is final
+                }
             }
         }
         if (k > 0) {
             const int c = k - 1;   // eliminate with column c of L (complete since iteration c)
-            const double lcc = L[c * LDS + c];
+            const double yc = ys[c];
             if (row > c && row < n) {
-                const double f = L[c * LDS + row] / lcc;
+                const double f = L[c * LDS + row] * yc;
                 for (int j = lane_q; j <= c; j += nq) W[j * LDS + row] -= f * W[j * LDS + c];
             }
             // row c of X is final: W[c][:] / L[c][c]
-            if (tid <= c) X[c + (long long)tid * ldx] = W[tid * LDS + c] / lcc;
+            if (tid <= c) X[c + (long long)tid * ldx] = W[tid * LDS + c] * yc;
         }
     }
     __syncthreads();
@@ -195,9 +223,11 @@ __global__ void __launch_bounds__(256) chol_inv_leaf_kernel(double* A, long long
     }
 }
 
-// ---------------------------------------------------------------- copies
+// ---------------------------------------------------------------- copies (blockIdx.y = matrix)
 __global__ void copy_mat_kernel(const double* src, long long lds, double* dst, long long ldd, int rows,
-                                int cols, int lower_only) {
+                                int cols, int lower_only, long long ss, long long sd) {
+    src += blockIdx.y * ss;
+    dst += blockIdx.y * sd;
     const long long total = (long long)rows * cols;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
@@ -207,7 +237,8 @@ __global__ void copy_mat_kernel(const double* src, long long lds, double* dst, l
     }
 }
 
-__global__ void symmetrize_kernel(double* A, long long lda, int n) {
+__global__ void symmetrize_kernel(double* A, long long lda, int n, long long sA) {
+    A += blockIdx.y * sA;
     const long long total = (long long)n * n;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
@@ -216,7 +247,7 @@ __global__ void symmetrize_kernel(double* A, long long lda, int n) {
     }
 }
 
-// ---------------------------------------------------------------- GEMV
+// ---------------------------------------------------------------- GEMV (blockIdx.y = matrix)
 // y[m] = alpha sum_n op(A)[m][n] x[n] + beta yin[m]
 // Non-transposed: a CTA owns 32 rows; 8 warps split the columns; lanes read
 // consecutive rows (coalesced).  Transposed: a warp owns one output, lanes
@@ -254,11 +285,11 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(int M, int N, const double*
                                                      const double* x, double alpha, const double* yin,
                                                      double beta, double* y, long long sA, long long sx,
                                                      long long sy) {
+    // op(A) = A^T: op(A)[m][n] = A[n + m*lda], op(A) is M x N, A stored N x M.
     A += blockIdx.y * sA;
     x += blockIdx.y * sx;
     y += blockIdx.y * sy;
     if (yin) yin += blockIdx.y * sy;
-    // op(A) = A^T: op(A)[m][n] = A[n + m*lda], op(A) is M x N, A stored N x M.
     const int lane = threadIdx.x % 32;
     const int m = blockIdx.x * 8 + threadIdx.x / 32;
     if (m >= M) return;
@@ -276,7 +307,7 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(int M, int N, const double*
     }
 }
 
-// ---------------------------------------------------------------- reductions
+// ---------------------------------------------------------------- reductions (blockIdx.y = matrix)
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -292,9 +323,10 @@ __device__ __forceinline__ double block_sum(double v) {
     return s;
 }
 
-__global__ void logdiag_partial_kernel(const double* A, long long lda, int dim, int count, long long stride,
-                                       double* partial) {
-    const long long total = (long long)dim * count;
+__global__ void logdiag_partial_kernel(const double* A, long long lda, int dim, int nblk, long long stride,
+                                       long long sA, double* partial) {
+    A += blockIdx.y * sA;
+    const long long total = (long long)dim * nblk;
     double acc = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
@@ -302,30 +334,44 @@ __global__ void logdiag_partial_kernel(const double* A, long long lda, int dim, 
         acc += log(A[blk * stride + k * (lda + 1)]);
     }
     double s = block_sum(acc);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (threadIdx.x == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void logdet_finish_kernel(const double* partial, int chunks, const double* T, int a, long long sT,
+                                     double* out, double scale) {
+    const int m = blockIdx.x;
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < chunks; e += blockDim.x) acc += partial[m * chunks + e];
+    if (T)
+        for (int k = threadIdx.x; k < a; k += blockDim.x) acc += log(T[m * sT + k * (a + 1)]);
+    double s = block_sum(acc);
+    if (threadIdx.x == 0) out[m] = scale * s;
 }
 
 __global__ void dot_partial_kernel(const double* x, const double* y, long long len, double* partial) {
+    x += blockIdx.y * len;
+    y += blockIdx.y * len;
     double acc = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
          e += (long long)gridDim.x * blockDim.x)
         acc = fma(x[e], y[e], acc);
     double s = block_sum(acc);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (threadIdx.x == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
-__global__ void finish_sum_kernel(const double* partial, int len, double* out, double scale, int accumulate) {
+__global__ void dot_finish_kernel(const double* partial, int chunks, double* out, long long ostride) {
+    const int m = blockIdx.x;
     double acc = 0.0;
-    for (int e = threadIdx.x; e < len; e += blockDim.x) acc += partial[e];
+    for (int e = threadIdx.x; e < chunks; e += blockDim.x) acc += partial[m * chunks + e];
     double s = block_sum(acc);
-    if (threadIdx.x == 0) *out = (accumulate ? *out : 0.0) + scale * s;
+    if (threadIdx.x == 0) out[m * ostride] = s;
 }
 
 }  // namespace
 
 // ==================================================================== host launchers
 int gemm64(cudaStream_t s, const Gemm64& g) {
-    if (g.M <= 0 || g.N <= 0) return BTA_OK;
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return BTA_OK;
     // The FP64 pipe of one SM is slow (2 DFMA per clock), so every product is
     // spread over about two CTAs per SM: pick the largest micro-tile that
     // still reaches that with a K split of whole 16-wide slices, else the
@@ -333,34 +379,29 @@ int gemm64(cudaStream_t s, const Gemm64& g) {
     const long long want = 2LL * 152;
     int MI = 1, NJ = 1, ksplit = 1;
     const int kslices = std::max(1, (g.K + BK - 1) / BK);
-    bool chosen = false;
-    for (int sz = 4; sz >= 1 && !chosen; sz /= 2) {
+    for (int sz = 4; sz >= 1; sz /= 2) {
         const int mi = std::min(sz, g.M <= 16 ? 1 : (g.M <= 32 ? 2 : 4));
         const int nj = std::min(sz, g.N <= 16 ? 1 : (g.N <= 32 ? 2 : 4));
         const int gm = (g.M + 16 * mi - 1) / (16 * mi), gn = (g.N + 16 * nj - 1) / (16 * nj);
         long long tiles = (long long)gm * gn;
         if (g.lowerC) tiles = (tiles + gm) / 2;
-        const int maxsplit = g.batch == 1 ? std::min(64, std::max(1, kslices / (sz == 4 ? 4 : 2))) : 1;
+        tiles *= g.batch;
+        const int maxsplit = std::min(64, std::max(1, kslices / (sz == 4 ? 4 : 2)));
         if (tiles * maxsplit >= want || sz == 1) {
             MI = mi;
             NJ = nj;
             ksplit = (int)std::min<long long>(maxsplit, std::max<long long>(1, (want + tiles - 1) / tiles));
-            chosen = true;
+            break;
         }
     }
+    if ((long long)g.batch * ksplit > 65535) ksplit = std::max(1, 65535 / g.batch);
     const int TBM = 16 * MI, TBN = 16 * NJ;
     const int gm = (g.M + TBM - 1) / TBM, gn = (g.N + TBN - 1) / TBN;
     if (ksplit > 1) {
-        const bool inplace = (g.Cin == g.C && g.ldci == g.ldc && g.beta == 1.0);
-        if (!inplace) {
-            long long total = (long long)g.M * g.N;
-            int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
-            scale_into_kernel<<<blocks, 256, 0, s>>>(g.M, g.N, g.Cin, g.ldci, g.beta, g.C, g.ldc, g.lowerC,
-                                                     1, 0, 0);
-            BTA_LAUNCH_CHECK();
-        }
+        const bool inplace = (g.Cin == g.C && g.ldci == g.ldc && g.beta == 1.0 && g.sCi == g.sC);
+        if (!inplace) BTA_TRY(scale_into64(s, g.M, g.N, g.Cin, g.ldci, g.beta, g.C, g.ldc, g.lowerC, g.batch, g.sCi, g.sC));
     }
-    dim3 grid(gm, gn, ksplit > 1 ? ksplit : g.batch);
+    dim3 grid(gm, gn, g.batch * ksplit);
 #define BTA_GEMM_CASE(mi, nj) \
     if (MI == mi && NJ == nj) gemm64_kernel<mi, nj><<<grid, GT, 0, s>>>(g, ksplit);
     BTA_GEMM_CASE(1, 1) BTA_GEMM_CASE(1, 2) BTA_GEMM_CASE(1, 4)
@@ -371,39 +412,38 @@ int gemm64(cudaStream_t s, const Gemm64& g) {
     return BTA_OK;
 }
 
-static int leaf_launch(cudaStream_t s, double* A, long long lda, double* X, long long ldx, int n,
-                       long long row0, long long* status) {
-    static bool attr_set = false;
-    const size_t smem = 3 * LDS * LEAF_MAX * sizeof(double);
-    if (!attr_set) {
-        BTA_CUDA_TRY(cudaFuncSetAttribute(chol_inv_leaf_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
-    const int threads = n <= 32 ? 128 : 256;
-    chol_inv_leaf_kernel<<<1, threads, smem, s>>>(A, lda, X, ldx, n, row0, status);
-    BTA_LAUNCH_CHECK();
-    return BTA_OK;
-}
-
-// Recursive Cholesky + inverse of the lower n x n matrix at A (in place) into
-// X (lower).  W: scratch of at least ceil(n/2)^2 doubles.
-//   [A11      ]   L11 = chol(A11), X11 = L11^{-1}
-//   [A21  A22 ]   L21 = A21 X11^T, A22 -= L21 L21^T, L22 = chol(A22), X22 = L22^{-1}
-//                 X21 = -X22 (L21 X11)
-static int gemm_fp64_fn(const GemmExec*, cudaStream_t s, const Gemm64& g) { return gemm64(s, g); }
-
 int gemm_exec(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
     if (!ex || !ex->fn) return gemm64(s, g);
     return ex->fn(ex, s, g);
 }
 
+static int leaf_launch(cudaStream_t s, double* A, long long lda, long long sA, double* X, long long ldx,
+                       long long sX, int n, long long row0, long long* status, int batch, int m_first, int nbatch) {
+    static bool attr_set = false;
+    const size_t smem = (3 * LDS * LEAF_MAX + LEAF_MAX + 1) * sizeof(double);
+    if (!attr_set) {
+        BTA_CUDA_TRY(cudaFuncSetAttribute(chol_inv_leaf_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    const int threads = 256;
+    chol_inv_leaf_kernel<<<batch, threads, smem, s>>>(A, lda, sA, X, ldx, sX, n, row0, status, m_first, nbatch);
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}
+
+// Recursive Cholesky + inverse of the lower n x n matrix at A (in place) into
+// X (lower), for `batch` matrices at once.  W: scratch of at least
+// ceil(n/2)^2 + n doubles per matrix.
+//   [A11      ]   L11 = chol(A11), X11 = L11^{-1}
+//   [A21  A22 ]   L21 = A21 X11^T, A22 -= L21 L21^T, L22 = chol(A22), X22 = L22^{-1}
+//                 X21 = -X22 (L21 X11)
 int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ldx, int n, long long row0,
-               long long* status, double* W, int leaf, const GemmExec* ex) {
-    if (n <= 0) return BTA_OK;
+               long long* status, double* W, int leaf, const GemmExec* ex, int batch, long long sA,
+               long long sX, long long sW, int m_first, int nbatch) {
+    if (n <= 0 || batch <= 0) return BTA_OK;
     leaf = std::max(8, std::min(leaf, LEAF_MAX));
-    if (n <= leaf) return leaf_launch(s, A, lda, X, ldx, n, row0, status);
-    (void)gemm_fp64_fn;
+    if (n <= leaf) return leaf_launch(s, A, lda, sA, X, ldx, sX, n, row0, status, batch, m_first, nbatch);
     const int half = (n + 1) / 2;
     int n1 = ((half + leaf - 1) / leaf) * leaf;
     if (n1 >= n) n1 = leaf;
@@ -414,7 +454,7 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
     double* X11 = X;
     double* X21 = X + n1;
     double* X22 = X + n1 + n1 * ldx;
-    BTA_TRY(chol_inv64(s, A11, lda, X11, ldx, n1, row0, status, W, leaf, ex));
+    BTA_TRY(chol_inv64(s, A11, lda, X11, ldx, n1, row0, status, W, leaf, ex, batch, sA, sX, sW, m_first, nbatch));
     Gemm64 g{};
     // W (n2 x n1) = A21 * X11^T      (op(B) upper)
     g = Gemm64{};
@@ -422,8 +462,9 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
     g.A = A21; g.lda = lda; g.ta = 0; g.shA = 0;
     g.B = X11; g.ldb = ldx; g.tb = 1; g.shB = 2;
     g.C = W; g.ldc = n2; g.alpha = 1.0; g.beta = 0.0;
+    g.batch = batch; g.sA = sA; g.sB = sX; g.sC = sW;
     BTA_TRY(gemm_exec(ex, s, g));
-    BTA_TRY(copy_mat64(s, W, n2, A21, lda, n2, n1, 0));
+    BTA_TRY(copy_mat64(s, W, n2, A21, lda, n2, n1, 0, batch, sW, sA));
     // A22 -= L21 L21^T  (lower)
     g = Gemm64{};
     g.M = n2; g.N = n2; g.K = n1;
@@ -431,14 +472,17 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
     g.B = A21; g.ldb = lda; g.tb = 1;
     g.Cin = A22; g.ldci = lda; g.beta = 1.0;
     g.C = A22; g.ldc = lda; g.alpha = -1.0; g.lowerC = 1;
+    g.batch = batch; g.sA = sA; g.sB = sA; g.sCi = sA; g.sC = sA;
     BTA_TRY(gemm_exec(ex, s, g));
-    BTA_TRY(chol_inv64(s, A22, lda, X22, ldx, n2, row0 + n1, status, W, leaf, ex));
+    BTA_TRY(chol_inv64(s, A22, lda, X22, ldx, n2, row0 + n1, status, W, leaf, ex, batch, sA, sX, sW, m_first,
+                       nbatch));
     // W = L21 * X11   (op(B) lower)
     g = Gemm64{};
     g.M = n2; g.N = n1; g.K = n1;
     g.A = A21; g.lda = lda;
     g.B = X11; g.ldb = ldx; g.tb = 0; g.shB = 1;
     g.C = W; g.ldc = n2; g.alpha = 1.0; g.beta = 0.0;
+    g.batch = batch; g.sA = sA; g.sB = sX; g.sC = sW;
     BTA_TRY(gemm_exec(ex, s, g));
     // X21 = -X22 * W   (op(A) lower)
     g = Gemm64{};
@@ -446,35 +490,40 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
     g.A = X22; g.lda = ldx; g.ta = 0; g.shA = 1;
     g.B = W; g.ldb = n2; g.tb = 0;
     g.C = X21; g.ldc = ldx; g.alpha = -1.0; g.beta = 0.0;
+    g.batch = batch; g.sA = sX; g.sB = sW; g.sC = sX;
     BTA_TRY(gemm_exec(ex, s, g));
     return BTA_OK;
 }
 
+static int grid_for(long long total) {
+    return (int)std::min<long long>(std::max<long long>(1, (total + 255) / 256), 152 * 8);
+}
+
 int scale_into64(cudaStream_t s, int M, int N, const double* Cin, long long ldci, double beta, double* C,
-                 long long ldc, int lower) {
+                 long long ldc, int lower, int batch, long long sCi, long long sC) {
     long long total = (long long)M * N;
-    if (total <= 0) return BTA_OK;
-    int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
-    scale_into_kernel<<<blocks, 256, 0, s>>>(M, N, Cin, ldci, beta, C, ldc, lower, 1, 0, 0);
+    if (total <= 0 || batch <= 0) return BTA_OK;
+    dim3 grid(std::max(1, grid_for(total) / batch), batch);
+    scale_into_kernel<<<grid, 256, 0, s>>>(M, N, Cin, ldci, beta, C, ldc, lower, sCi, sC);
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }
 
-int copy_mat64(cudaStream_t s, const double* src, long long lds, double* dst, long long ldd, int rows,
-               int cols, int lower_only) {
+int copy_mat64(cudaStream_t s, const double* src, long long lds, double* dst, long long ldd, int rows, int cols,
+               int lower_only, int batch, long long ss, long long sd) {
     long long total = (long long)rows * cols;
-    if (total <= 0) return BTA_OK;
-    int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
-    copy_mat_kernel<<<blocks, 256, 0, s>>>(src, lds, dst, ldd, rows, cols, lower_only);
+    if (total <= 0 || batch <= 0) return BTA_OK;
+    dim3 grid(std::max(1, grid_for(total) / batch), batch);
+    copy_mat_kernel<<<grid, 256, 0, s>>>(src, lds, dst, ldd, rows, cols, lower_only, ss, sd);
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }
 
-int symmetrize_lower64(cudaStream_t s, double* A, long long lda, int n) {
+int symmetrize_lower64(cudaStream_t s, double* A, long long lda, int n, int batch, long long sA) {
     long long total = (long long)n * n;
-    if (total <= 0) return BTA_OK;
-    int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 8);
-    symmetrize_kernel<<<blocks, 256, 0, s>>>(A, lda, n);
+    if (total <= 0 || batch <= 0) return BTA_OK;
+    dim3 grid(std::max(1, grid_for(total) / batch), batch);
+    symmetrize_kernel<<<grid, 256, 0, s>>>(A, lda, n, sA);
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }
@@ -494,23 +543,25 @@ int gemv64(cudaStream_t s, int M, int N, const double* A, long long lda, int ta,
     return BTA_OK;
 }
 
-int logdiag_sum64(cudaStream_t s, const double* A, long long lda, int dim, int count, long long stride,
-                  double* partial, int partial_len, double* out, double scale, int accumulate) {
-    long long total = (long long)dim * count;
-    int blocks = (int)std::min<long long>(std::max<long long>(1, (total + 255) / 256), partial_len);
-    logdiag_partial_kernel<<<blocks, 256, 0, s>>>(A, lda, dim, count, stride, partial);
+int logdet_batch64(cudaStream_t s, const double* A, long long lda, int dim, int nblk, long long stride,
+                   long long sA, const double* T, int a, long long sT, int count, double* partial, int chunks,
+                   double* out, double scale) {
+    if (count <= 0) return BTA_OK;
+    dim3 grid(chunks, count);
+    logdiag_partial_kernel<<<grid, 256, 0, s>>>(A, lda, dim, nblk, stride, sA, partial);
     BTA_LAUNCH_CHECK();
-    finish_sum_kernel<<<1, 256, 0, s>>>(partial, blocks, out, scale, accumulate);
+    logdet_finish_kernel<<<count, 256, 0, s>>>(partial, chunks, a > 0 ? T : nullptr, a, sT, out, scale);
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }
 
-int dot64(cudaStream_t s, const double* x, const double* y, long long len, double* partial, int partial_len,
-          double* out) {
-    int blocks = (int)std::min<long long>(std::max<long long>(1, (len + 255) / 256), partial_len);
-    dot_partial_kernel<<<blocks, 256, 0, s>>>(x, y, len, partial);
+int dot_batch64(cudaStream_t s, const double* x, const double* y, long long len, int count, double* partial,
+                int chunks, double* out, long long ostride) {
+    if (count <= 0) return BTA_OK;
+    dim3 grid(chunks, count);
+    dot_partial_kernel<<<grid, 256, 0, s>>>(x, y, len, partial);
     BTA_LAUNCH_CHECK();
-    finish_sum_kernel<<<1, 256, 0, s>>>(partial, blocks, out, 1.0, 0);
+    dot_finish_kernel<<<count, 256, 0, s>>>(partial, chunks, out, ostride);
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }

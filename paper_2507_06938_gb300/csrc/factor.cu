@@ -1,5 +1,6 @@
-// Block Cholesky of a BTA matrix and its log-determinant (Section III-A,
-// cost O(n (b^3 + a^3)) of Section IV-D.2).
+// Block Cholesky of BTA matrices and their log-determinants (Section III-A,
+// cost O(n (b^3 + a^3)) of Section IV-D.2), for a range of matrices of one
+// shape at once: every launch below carries all matrices of the range.
 //
 //   for i = 0..n-1:
 //     (L_ii, L_ii^{-1}) = chol_inv(D_i)                 recursive, FP64 leaves
@@ -8,116 +9,135 @@
 //     L_{t,i}   = Racc_i L_ii^{-T}                       Racc_0 = R_0
 //     Racc_{i+1} = R_{i+1} - L_{t,i} L_{i+1,i}^T
 //     T        <- T - L_{t,i} L_{t,i}^T
-//   (L_tt, L_tt^{-1}) = chol_inv(T)
+//   (L_tt, L_tt^{-1}) = chol_inv(T)                      FP64
 // The assembled blocks Q are only read, so they stay available for residuals.
 
 #include <algorithm>
 
 #include "common.cuh"
 
-namespace {
-
-size_t bsq(const bta_ctx_t c) { return (size_t)c->b * c->b; }
-
-}  // namespace
-
-int factor_impl(bta_ctx_t ctx, int which, cudaStream_t s) {
+int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
     const int n = ctx->n, b = ctx->b, a = ctx->a;
-    const BtaMat& Q = ctx->Q[which];
-    const BtaMat& L = ctx->L[which];
-    double* Linv = ctx->Linv[which];
-    double* W = ctx->work[which];                 // chol_inv scratch (b*b/2 + b)
-    double* Racc = W + bsq(ctx) / 2 + b;          // a*b
+    const long long bb = (long long)b * b, ab = (long long)a * b;
+    const BtaStore& Q = ctx->Q;
+    const BtaStore& L = ctx->L;
+    double* QD = Q.D + m0 * Q.sD;
+    double* QB = Q.B + m0 * Q.sB;
+    double* QR = Q.R + m0 * Q.sR;
+    double* QT = Q.T + m0 * Q.sT;
+    double* LD = L.D + m0 * L.sD;
+    double* LB = L.B + m0 * L.sB;
+    double* LR = L.R + m0 * L.sR;
+    double* LT = L.T + m0 * L.sT;
+    double* Linv = ctx->Linv + m0 * ctx->sLinv;
+    double* W = ctx->work + m0 * ctx->sWork;          // chol_inv scratch (b*b/2 + 2b)
+    double* Racc = W + bb / 2 + 2 * b;               // a*b
+    const long long sW = ctx->sWork, sX = ctx->sLinv;
     long long* status = ctx->status;
     const int leaf = ctx->leaf;
+    const GemmExec* ex = &ctx->exec;
 
-    BTA_TRY(copy_mat64(s, Q.D, b, L.D, b, b, b, 1));
+    BTA_TRY(copy_mat64(s, QD, b, LD, b, b, b, 1, cnt, Q.sD, L.sD));
     if (a > 0) {
-        BTA_TRY(copy_mat64(s, Q.T, a, L.T, a, a, a, 1));
-        BTA_TRY(copy_mat64(s, Q.R, a, Racc, a, a, b, 0));
+        BTA_TRY(copy_mat64(s, QT, a, LT, a, a, a, 1, cnt, Q.sT, L.sT));
+        BTA_TRY(copy_mat64(s, QR, a, Racc, a, a, b, 0, cnt, Q.sR, sW));
     }
     for (int i = 0; i < n; ++i) {
-        double* Di = L.D + i * bsq(ctx);
-        double* Xi = Linv + i * bsq(ctx);
-        BTA_TRY(chol_inv64(s, Di, b, Xi, b, b, (long long)i * b, status, W, leaf, &ctx->exec[which]));
+        double* Di = LD + i * bb;
+        double* Xi = Linv + i * bb;
+        BTA_TRY(chol_inv64(s, Di, b, Xi, b, b, (long long)i * b, status, W, leaf, ex, cnt, L.sD, sX, sW, m0,
+                           ctx->batch));
         Gemm64 g{};
         if (i < n - 1) {
             // L_{i+1,i} = B_i X_i^T
             g = Gemm64{};
             g.M = b; g.N = b; g.K = b;
-            g.A = Q.B + i * bsq(ctx); g.lda = b;
+            g.A = QB + i * bb; g.lda = b;
             g.B = Xi; g.ldb = b; g.tb = 1; g.shB = 2;
-            g.C = L.B + i * bsq(ctx); g.ldc = b; g.alpha = 1.0;
+            g.C = LB + i * bb; g.ldc = b; g.alpha = 1.0;
+            g.batch = cnt; g.sA = Q.sB; g.sB = sX; g.sC = L.sB;
             cudaEvent_t stop;
-            BTA_TRY(prof_begin(ctx, s, (double)b * b * b, &stop));
-            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
+            BTA_TRY(prof_begin(ctx, s, (double)cnt * b * b * b, &stop));
+            BTA_TRY(gemm_exec(ex, s, g));
             if (stop) BTA_CUDA_TRY(cudaEventRecord(stop, s));
             // D_{i+1} = Q.D_{i+1} - L_{i+1,i} L_{i+1,i}^T   (lower)
             g = Gemm64{};
             g.M = b; g.N = b; g.K = b;
-            g.A = L.B + i * bsq(ctx); g.lda = b;
-            g.B = L.B + i * bsq(ctx); g.ldb = b; g.tb = 1;
-            g.Cin = Q.D + (i + 1) * bsq(ctx); g.ldci = b; g.beta = 1.0;
-            g.C = L.D + (i + 1) * bsq(ctx); g.ldc = b; g.alpha = -1.0; g.lowerC = 1;
-            BTA_TRY(prof_begin(ctx, s, (double)b * b * b, &stop));
-            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
+            g.A = LB + i * bb; g.lda = b;
+            g.B = LB + i * bb; g.ldb = b; g.tb = 1;
+            g.Cin = QD + (i + 1) * bb; g.ldci = b; g.beta = 1.0;
+            g.C = LD + (i + 1) * bb; g.ldc = b; g.alpha = -1.0; g.lowerC = 1;
+            g.batch = cnt; g.sA = L.sB; g.sB = L.sB; g.sCi = Q.sD; g.sC = L.sD;
+            BTA_TRY(prof_begin(ctx, s, (double)cnt * b * b * b, &stop));
+            BTA_TRY(gemm_exec(ex, s, g));
             if (stop) BTA_CUDA_TRY(cudaEventRecord(stop, s));
         }
         if (a > 0) {
-            double* Lri = L.R + (size_t)i * a * b;
+            double* Lri = LR + i * ab;
             // L_{t,i} = Racc X_i^T
             g = Gemm64{};
             g.M = a; g.N = b; g.K = b;
             g.A = Racc; g.lda = a;
             g.B = Xi; g.ldb = b; g.tb = 1; g.shB = 2;
             g.C = Lri; g.ldc = a; g.alpha = 1.0;
-            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
+            g.batch = cnt; g.sA = sW; g.sB = sX; g.sC = L.sR;
+            BTA_TRY(gemm64(s, g));
             if (i < n - 1) {
                 // Racc = R_{i+1} - L_{t,i} L_{i+1,i}^T
                 g = Gemm64{};
                 g.M = a; g.N = b; g.K = b;
                 g.A = Lri; g.lda = a;
-                g.B = L.B + i * bsq(ctx); g.ldb = b; g.tb = 1;
-                g.Cin = Q.R + (size_t)(i + 1) * a * b; g.ldci = a; g.beta = 1.0;
+                g.B = LB + i * bb; g.ldb = b; g.tb = 1;
+                g.Cin = QR + (i + 1) * ab; g.ldci = a; g.beta = 1.0;
                 g.C = Racc; g.ldc = a; g.alpha = -1.0;
-                BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
+                g.batch = cnt; g.sA = L.sR; g.sB = L.sB; g.sCi = Q.sR; g.sC = sW;
+                BTA_TRY(gemm64(s, g));
             }
-            // T -= L_{t,i} L_{t,i}^T   (lower)
+            // T -= L_{t,i} L_{t,i}^T   (lower, FP64)
             g = Gemm64{};
             g.M = a; g.N = a; g.K = b;
             g.A = Lri; g.lda = a;
             g.B = Lri; g.ldb = a; g.tb = 1;
-            g.Cin = L.T; g.ldci = a; g.beta = 1.0;
-            g.C = L.T; g.ldc = a; g.alpha = -1.0; g.lowerC = 1;
-            BTA_TRY(gemm_exec(&ctx->exec[which], s, g));
+            g.Cin = LT; g.ldci = a; g.beta = 1.0;
+            g.C = LT; g.ldc = a; g.alpha = -1.0; g.lowerC = 1;
+            g.batch = cnt; g.sA = L.sR; g.sB = L.sR; g.sCi = L.sT; g.sC = L.sT;
+            BTA_TRY(gemm64(s, g));
         }
     }
     if (a > 0)
-        BTA_TRY(chol_inv64(s, L.T, a, Linv + (size_t)n * bsq(ctx), a, a, (long long)n * b, status, W, leaf));
-    ctx->factored[which] = 1;
+        BTA_TRY(chol_inv64(s, LT, a, Linv + (long long)n * bb, a, a, (long long)n * b, status, W, leaf, nullptr, cnt,
+                           L.sT, sX, sW, m0, ctx->batch));
+    for (int m = m0; m < m0 + cnt; ++m) ctx->factored[m] = 1;
     return BTA_OK;
 }
 
-int logdet_impl(bta_ctx_t ctx, int which, double* out, cudaStream_t s) {
+int logdet_impl(bta_ctx_t ctx, int m0, int cnt, double* out, cudaStream_t s) {
     const int n = ctx->n, b = ctx->b, a = ctx->a;
-    const BtaMat& L = ctx->L[which];
-    // 2 sum log diag over the n diagonal blocks, then the tip
-    double* part = ctx->red + (which ? ctx->red_len / 2 : 0);
-    const int plen = ctx->red_len / 2;
-    BTA_TRY(logdiag_sum64(s, L.D, b, b, n, bsq(ctx), part, plen, out, 2.0, 0));
-    if (a > 0) BTA_TRY(logdiag_sum64(s, L.T, a, a, 1, 0, part, plen, out, 2.0, 1));
-    return BTA_OK;
+    const BtaStore& L = ctx->L;
+    // 2 sum log diag over the n diagonal blocks and the tip of every matrix
+    double* part = ctx->red + (long long)m0 * ctx->red_chunks;
+    return logdet_batch64(s, L.D + m0 * L.sD, b, b, n, (long long)b * b, L.sD, L.T + m0 * L.sT, a, L.sT, cnt, part,
+                          ctx->red_chunks, out, 2.0);
 }
 
 extern "C" int bta_factor(bta_ctx_t ctx, int which) {
-    if (!ctx || (which != BTA_QP && which != BTA_QC)) return BTA_ERR_ARG;
-    return factor_impl(ctx, which, ctx->stream);
+    if (!ctx) return BTA_ERR_ARG;
+    const int m = storage_index(ctx, which);
+    if (m < 0) return BTA_ERR_ARG;
+    return factor_impl(ctx, m, 1, ctx->stream);
+}
+
+extern "C" int bta_factor_batch(bta_ctx_t ctx, int kind) {
+    if (!ctx || (kind != BTA_QP && kind != BTA_QC)) return BTA_ERR_ARG;
+    return factor_impl(ctx, kind * ctx->batch, ctx->batch, ctx->stream);
 }
 
 extern "C" int bta_logdet(bta_ctx_t ctx, int which, double* out_dev) {
-    if (!ctx || !out_dev || (which != BTA_QP && which != BTA_QC)) return BTA_ERR_ARG;
-    if (!ctx->factored[which]) return BTA_ERR_STATE;
-    return logdet_impl(ctx, which, out_dev, ctx->stream);
+    if (!ctx || !out_dev) return BTA_ERR_ARG;
+    const int m = storage_index(ctx, which);
+    if (m < 0) return BTA_ERR_ARG;
+    if (!ctx->factored[m]) return BTA_ERR_STATE;
+    return logdet_impl(ctx, m, 1, out_dev, ctx->stream);
 }
 
 extern "C" double bta_flops_factor(int n, int b, int a) {

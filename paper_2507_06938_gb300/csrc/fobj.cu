@@ -1,10 +1,14 @@
 // The INLA objective f_obj(theta) of Eq. 8 for a Gaussian likelihood,
 // evaluated at the conditional mean x = mu (Section III, approximation of the
-// joint posterior; Section IV-D.2 for the two independent factorisations).
+// joint posterior), for a batch of hyperparameter vectors at once: the
+// 2 dim(theta) + 1 points of the central-difference gradient (Eq. 10) are
+// independent (Section IV-D.1), and so are Q_p and Q_c of each point
+// (Section IV-D.2).  All 2 x batch BTA matrices go through the same kernel
+// launches (one matrix per grid slice).
 //
-// Per theta: params = map(theta); Q_p is assembled, factored and its
-// log-determinant taken on the auxiliary stream while Q_c is assembled and
-// factored on the main stream; then mu = Q_c^{-1} b, b = A^T D y, and
+// Per theta: params = map(theta); Q_p and Q_c are assembled, factored and
+// their log-determinants taken; then mu = Q_c^{-1} b, b = A^T D y (with FP64
+// iterative refinement in mixed precision), and
 //   f = log p(theta) + 1/2 log|Q_p| - 1/2 log|Q_c| - 1/2 (y^T D y - b^T mu)
 //       + 1/2 sum_v m_v log tau_eps_v - (m/2) log 2 pi
 // with y^T D y - b^T mu = (y - A mu)^T D (y - A mu) + mu^T Q_p mu.
@@ -16,9 +20,11 @@
 
 namespace {
 
-// b[i] = tau_eps(variable of i) * (A^T y)[i]
+// b_j[i] = tau_eps(variable of i) * (A^T y)[i], blockIdx.y = slot j
 __global__ void fobj_rhs_kernel(const double* aty, const double* params, long long nb, int b, int ns, int nr,
                                 long long N, double* rhs) {
+    params += (long long)blockIdx.y * BTA_PSTRIDE;
+    rhs += blockIdx.y * N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
          i += (long long)gridDim.x * blockDim.x) {
         const int v = i < nb ? (int)((i % b) / ns) : (int)((i - nb) / nr);
@@ -26,9 +32,13 @@ __global__ void fobj_rhs_kernel(const double* aty, const double* params, long lo
     }
 }
 
+// blockIdx.x = slot j
 __global__ void fobj_final_kernel(const double* theta, const double* theta0, int dim, const double* params,
-                                  const double* var_stats, int nv, double m_total, const double* scal,
-                                  double* f_out) {
+                                  const double* var_stats, int nv, double m_total, const double* ld_p,
+                                  const double* ld_c, const double* dots, double* f_out) {
+    const int j = blockIdx.x;
+    theta += (long long)j * dim;
+    params += (long long)j * BTA_PSTRIDE;
     const double LOG_2PI = 1.8378770664093453;
     double lp = 0.0;
     for (int i = 0; i < dim; ++i) {
@@ -42,8 +52,8 @@ __global__ void fobj_final_kernel(const double* theta, const double* theta0, int
         yDy += te * var_stats[v];
         logd += var_stats[nv + v] * log(te);
     }
-    const double ld_p = scal[SCAL_LOGDET_P], ld_c = scal[SCAL_LOGDET_C], btmu = scal[SCAL_DOT];
-    *f_out = lp + 0.5 * ld_p - 0.5 * ld_c - 0.5 * (yDy - btmu) + 0.5 * logd - 0.5 * m_total * LOG_2PI;
+    const double btmu = dots[3 * j];
+    f_out[j] = lp + 0.5 * ld_p[j] - 0.5 * ld_c[j] - 0.5 * (yDy - btmu) + 0.5 * logd - 0.5 * m_total * LOG_2PI;
 }
 
 }  // namespace
@@ -51,49 +61,52 @@ __global__ void fobj_final_kernel(const double* theta, const double* theta0, int
 extern "C" int fobj_eval(bta_ctx_t ctx, bta_model_t m, const double* thetas_dev, int n_theta, double* f_out_dev,
                          double* mu_out_dev) {
     if (!ctx || !m || !thetas_dev || !f_out_dev || n_theta < 1) return BTA_ERR_ARG;
-    if (m->n != ctx->n || m->b != ctx->b || m->a != ctx->a) return BTA_ERR_ARG;
-    cudaStream_t s = ctx->stream, aux = ctx->aux;
+    if (m->n != ctx->n || m->b != ctx->b || m->a != ctx->a || m->nv > BTA_MAX_NV) return BTA_ERR_ARG;
+    cudaStream_t s = ctx->stream;
+    const int B = ctx->batch;
     const long long N = ctx->N, nb = (long long)ctx->n * ctx->b;
-    double* rhs = ctx->vec + 7 * N;
-    double* mu = ctx->vec + 8 * N;
-    for (int j = 0; j < n_theta; ++j) {
-        const double* theta = thetas_dev + (long long)j * m->dim_theta;
-        BTA_TRY(theta_to_params_impl(m, theta, ctx->params, s));
-        // fork: Q_p on the auxiliary stream
-        BTA_CUDA_TRY(cudaEventRecord(ctx->ev_fork, s));
-        BTA_CUDA_TRY(cudaStreamWaitEvent(aux, ctx->ev_fork, 0));
-        BTA_TRY(assemble_impl(ctx, m, ctx->params, BTA_QP, aux));
-        BTA_TRY(factor_impl(ctx, BTA_QP, aux));
-        BTA_TRY(logdet_impl(ctx, BTA_QP, ctx->scal + SCAL_LOGDET_P, aux));
-        // Q_c, its log-determinant and the conditional mean on the main stream
-        BTA_TRY(assemble_impl(ctx, m, ctx->params, BTA_QC, s));
-        BTA_TRY(factor_impl(ctx, BTA_QC, s));
-        BTA_TRY(logdet_impl(ctx, BTA_QC, ctx->scal + SCAL_LOGDET_C, s));
+    for (int r0 = 0; r0 < n_theta; r0 += B) {
+        const int cnt = std::min(B, n_theta - r0);
+        const double* theta = thetas_dev + (long long)r0 * m->dim_theta;
+        BTA_TRY(theta_to_params_impl(m, theta, cnt, ctx->params, s));
+        if (cnt == B) {
+            // all Q_p and Q_c of the batch in one pass
+            BTA_TRY(assemble_impl(ctx, m, ctx->params, 0, 2 * B, s));
+            BTA_TRY(factor_impl(ctx, 0, 2 * B, s));
+            BTA_TRY(logdet_impl(ctx, 0, 2 * B, ctx->ld, s));
+        } else {
+            for (int kind = 0; kind < 2; ++kind) {
+                BTA_TRY(assemble_impl(ctx, m, ctx->params, kind * B, cnt, s));
+                BTA_TRY(factor_impl(ctx, kind * B, cnt, s));
+                BTA_TRY(logdet_impl(ctx, kind * B, cnt, ctx->ld + kind * B, s));
+            }
+        }
+        double* rhs = vec_row(ctx, VEC_RHS, B);
+        double* mu = vec_row(ctx, VEC_MU, B);
         {
-            int blocks = (int)std::min<long long>((N + 255) / 256, 152 * 8);
-            fobj_rhs_kernel<<<blocks, 256, 0, s>>>(m->aty, ctx->params, nb, ctx->b, m->ns, m->nr > 0 ? m->nr : 1,
-                                                  N, rhs);
+            int blocks = (int)std::min<long long>((N + 255) / 256, 152 * 8 / cnt + 1);
+            fobj_rhs_kernel<<<dim3(blocks, cnt), 256, 0, s>>>(m->aty, ctx->params, nb, ctx->b, m->ns,
+                                                              m->nr > 0 ? m->nr : 1, N, rhs);
             BTA_LAUNCH_CHECK();
         }
-        BTA_TRY(solve_impl(ctx, BTA_QC, rhs, mu, s));
+        BTA_TRY(solve_impl(ctx, B, cnt, rhs, mu, s));
         // iterative refinement with an FP64 residual on the assembled blocks
         for (int it = 0; it < ctx->refine; ++it) {
-            double* res = ctx->vec + N;
-            double* corr = ctx->vec + 2 * N;
-            BTA_TRY(matvec_impl(ctx, BTA_QC, mu, res, s));
-            BTA_TRY(axpby64(s, N, 1.0, rhs, -1.0, res, res));
-            BTA_TRY(solve_impl(ctx, BTA_QC, res, corr, s));
-            BTA_TRY(axpby64(s, N, 1.0, mu, 1.0, corr, mu));
+            double* res = vec_row(ctx, VEC_RES, B);
+            double* corr = vec_row(ctx, VEC_CORR, B);
+            BTA_TRY(matvec_impl(ctx, B, cnt, mu, res, s));
+            BTA_TRY(axpby64(s, cnt * N, 1.0, rhs, -1.0, res, res));
+            BTA_TRY(solve_impl(ctx, B, cnt, res, corr, s));
+            BTA_TRY(axpby64(s, cnt * N, 1.0, mu, 1.0, corr, mu));
         }
-        BTA_TRY(dot64(s, rhs, mu, N, ctx->red + ctx->red_len / 2, ctx->red_len / 2, ctx->scal + SCAL_DOT));
-        // join
-        BTA_CUDA_TRY(cudaEventRecord(ctx->ev_join, aux));
-        BTA_CUDA_TRY(cudaStreamWaitEvent(s, ctx->ev_join, 0));
-        fobj_final_kernel<<<1, 1, 0, s>>>(theta, m->theta0, m->dim_theta, ctx->params, m->var_stats, m->nv,
-                                          (double)m->m, ctx->scal, f_out_dev + j);
+        BTA_TRY(dot_batch64(s, rhs, mu, N, cnt, ctx->red + (long long)B * ctx->red_chunks, ctx->red_chunks,
+                            ctx->dots + 3 * B, 3));
+        fobj_final_kernel<<<cnt, 1, 0, s>>>(theta, m->theta0, m->dim_theta, ctx->params, m->var_stats, m->nv,
+                                            (double)m->m, ctx->ld, ctx->ld + B, ctx->dots + 3 * B, f_out_dev + r0);
         BTA_LAUNCH_CHECK();
+        if (mu_out_dev)
+            BTA_CUDA_TRY(cudaMemcpyAsync(mu_out_dev + (long long)r0 * N, mu, cnt * N * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, s));
     }
-    if (mu_out_dev)
-        BTA_CUDA_TRY(cudaMemcpyAsync(mu_out_dev, mu, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return BTA_OK;
 }

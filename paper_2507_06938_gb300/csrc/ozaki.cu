@@ -54,6 +54,8 @@ __constant__ int c_pair_q[NPAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0
 
 struct Args {
     int M, N;            // output extent
+    int groups;          // pair groups per matrix (blockIdx.z = matrix * groups + group)
+    long long sC;        // matrix stride of C
     int Mp, Np;          // padded rows per digit slice (multiples of 128)
     int kblocks;         // padded K / 64
     const int* expA;     // Mp exponents of the rows of op(A)
@@ -190,7 +192,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int pb = blockIdx.z * a.pairs_per_group;
+    const int inst = blockIdx.z / a.groups;
+    const int pb = (blockIdx.z % a.groups) * a.pairs_per_group;
     const int pe = min(NPAIRS, pb + a.pairs_per_group);
     const int nchunks = (a.kblocks + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
     const int units = (pe - pb) * nchunks;
@@ -234,8 +237,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                     uint8_t* sA = smem + st * STAGE_BYTES;
                     uint8_t* sB = sA + TM * TK * 2;
                     mbar_expect_tx(&full[st], STAGE_BYTES);
-                    tma_load_2d(smem_u32(sA), &tmA, &full[st], kb * TK, p * a.Mp + m0);
-                    tma_load_2d(smem_u32(sB), &tmB, &full[st], kb * TK, q * a.Np + n0);
+                    tma_load_2d(smem_u32(sA), &tmA, &full[st], kb * TK, (inst * S + p) * a.Mp + m0);
+                    tma_load_2d(smem_u32(sB), &tmB, &full[st], kb * TK, (inst * S + q) * a.Np + n0);
                 }
             }
             if (*abort_flag) {
@@ -324,13 +327,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         const int i = m0 + row;
         if (ok && i < a.M) {
-            const int ea = a.expA[i];
+            const int ea = a.expA[(long long)inst * a.Mp + i];
+            const int* expB = a.expB + (long long)inst * a.Np;
+            double* Cm = a.C + inst * a.sC;
 #pragma unroll
             for (int j = 0; j < 64; ++j) {
                 const int nn = n0 + colbase + j;
                 if (nn >= a.N || (a.lowerC && i < nn)) continue;
-                const double v = ((double)hi[j] + (double)lo[j]) * ldexp(a.alpha, ea + a.expB[nn] - 14);
-                double* c = a.C + i + (long long)nn * a.ldc;
+                const double v = ((double)hi[j] + (double)lo[j]) * ldexp(a.alpha, ea + expB[nn] - 14);
+                double* c = Cm + i + (long long)nn * a.ldc;
                 if (a.atomic) atomicAdd(c, v);
                 else *c += v;
             }
@@ -356,8 +361,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 constexpr int SPLIT_ROWS = 32, SPLIT_K = 64;
 
 __global__ void __launch_bounds__(256) row_maxexp_kernel(const double* P, long long sr, long long sk, int R, int K,
-                                                         int shape, int Rp, int* expo) {
-    // one warp per row
+                                                         int shape, int Rp, int* expo, long long sP) {
+    // one warp per row; blockIdx.y = matrix
+    P += blockIdx.y * sP;
+    expo += (long long)blockIdx.y * Rp;
     const int r = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
     if (r >= Rp) return;
     double mx = 0.0;
@@ -377,7 +384,11 @@ __global__ void __launch_bounds__(256) row_maxexp_kernel(const double* P, long l
 
 __global__ void __launch_bounds__(256) split_digits_kernel(const double* P, long long sr, long long sk, int R, int K,
                                                            int shape, int Rp, int Kp, const int* expo,
-                                                           __nv_bfloat16* dig) {
+                                                           __nv_bfloat16* dig, long long sP) {
+    // blockIdx.z = matrix: digits of matrix z start at dig + z S Rp Kp
+    P += blockIdx.z * sP;
+    expo += (long long)blockIdx.z * Rp;
+    dig += (long long)blockIdx.z * S * Rp * Kp;
     // tile: SPLIT_ROWS rows x SPLIT_K columns; staged through shared memory so
     // that both the FP64 read and the bf16 write are coalesced whatever the
     // stride direction of P
@@ -418,7 +429,8 @@ EncodeTiledFn encode_fn() {
     std::call_once(once, [] {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = reinterpret_cast<EncodeTiledFn>(p);
     });
@@ -440,7 +452,8 @@ int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int kp) {
 
 }  // namespace oz
 
-// Workspace needed by ozaki_gemm for an M x N x K product (bytes).
+// Workspace needed by ozaki_gemm for one M x N x K product (bytes; a batch of
+// products needs batch times this).
 size_t ozaki_workspace_bytes(int M, int N, int K) {
     const size_t Mp = ((size_t)M + 127) / 128 * 128, Np = ((size_t)N + 127) / 128 * 128;
     const size_t Kp = ((size_t)K + oz::TK - 1) / oz::TK * oz::TK;
@@ -451,46 +464,48 @@ size_t ozaki_workspace_bytes(int M, int N, int K) {
 // ws: device workspace of ozaki_workspace_bytes(M, N, K); err: device int.
 int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     using namespace oz;
-    if (g.M <= 0 || g.N <= 0) return BTA_OK;
-    if (g.batch != 1) return BTA_ERR_ARG;
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return BTA_OK;
+    const int nb = g.batch;
     const int Mp = (g.M + 127) / 128 * 128, Np = (g.N + 127) / 128 * 128;
     const int Kp = std::max(TK, (g.K + TK - 1) / TK * TK);
     uint8_t* w = static_cast<uint8_t*>(ws);
     __nv_bfloat16* digA = reinterpret_cast<__nv_bfloat16*>(w);
-    __nv_bfloat16* digB = digA + (size_t)S * Mp * Kp;
-    int* expA = reinterpret_cast<int*>(digB + (size_t)S * Np * Kp);
-    int* expB = expA + Mp;
+    __nv_bfloat16* digB = digA + (size_t)nb * S * Mp * Kp;
+    int* expA = reinterpret_cast<int*>(digB + (size_t)nb * S * Np * Kp);
+    int* expB = expA + (size_t)nb * Mp;
     // rows of op(A): op(A)[i][k] = ta ? A[k + i lda] : A[i + k lda]
     const long long srA = g.ta ? g.lda : 1, skA = g.ta ? 1 : g.lda;
     // rows of op(B)^T: op(B)[k][j] = tb ? B[j + k ldb] : B[k + j ldb]
     const long long srB = g.tb ? 1 : g.ldb, skB = g.tb ? g.ldb : 1;
     // shape of op(B)^T: lower op(B) (zero for j > k) is upper in op(B)^T
     const int shBt = g.shB == 1 ? 2 : (g.shB == 2 ? 1 : 0);
-    row_maxexp_kernel<<<(Mp + 7) / 8, 256, 0, s>>>(g.A, srA, skA, g.M, g.K, g.shA, Mp, expA);
+    row_maxexp_kernel<<<dim3((Mp + 7) / 8, nb), 256, 0, s>>>(g.A, srA, skA, g.M, g.K, g.shA, Mp, expA, g.sA);
     BTA_LAUNCH_CHECK();
-    row_maxexp_kernel<<<(Np + 7) / 8, 256, 0, s>>>(g.B, srB, skB, g.N, g.K, shBt, Np, expB);
+    row_maxexp_kernel<<<dim3((Np + 7) / 8, nb), 256, 0, s>>>(g.B, srB, skB, g.N, g.K, shBt, Np, expB, g.sB);
     BTA_LAUNCH_CHECK();
-    split_digits_kernel<<<dim3(Kp / SPLIT_K, Mp / SPLIT_ROWS), 256, 0, s>>>(g.A, srA, skA, g.M, g.K, g.shA, Mp, Kp,
-                                                                           expA, digA);
+    split_digits_kernel<<<dim3(Kp / SPLIT_K, Mp / SPLIT_ROWS, nb), 256, 0, s>>>(g.A, srA, skA, g.M, g.K, g.shA,
+                                                                               Mp, Kp, expA, digA, g.sA);
     BTA_LAUNCH_CHECK();
-    split_digits_kernel<<<dim3(Kp / SPLIT_K, Np / SPLIT_ROWS), 256, 0, s>>>(g.B, srB, skB, g.N, g.K, shBt, Np, Kp,
-                                                                           expB, digB);
+    split_digits_kernel<<<dim3(Kp / SPLIT_K, Np / SPLIT_ROWS, nb), 256, 0, s>>>(g.B, srB, skB, g.N, g.K, shBt,
+                                                                               Np, Kp, expB, digB, g.sB);
     BTA_LAUNCH_CHECK();
     CUtensorMap mA, mB;
-    BTA_TRY(make_map(&mA, digA, S * Mp, Kp));
-    BTA_TRY(make_map(&mB, digB, S * Np, Kp));
+    BTA_TRY(make_map(&mA, digA, nb * S * Mp, Kp));
+    BTA_TRY(make_map(&mB, digB, nb * S * Np, Kp));
     // C = beta Cin first (the tensor-core kernel adds into C)
-    const bool inplace = (g.Cin == g.C && g.ldci == g.ldc && g.beta == 1.0);
-    if (!inplace) BTA_TRY(scale_into64(s, g.M, g.N, g.Cin, g.ldci, g.beta, g.C, g.ldc, g.lowerC));
+    const bool inplace = (g.Cin == g.C && g.ldci == g.ldc && g.beta == 1.0 && g.sCi == g.sC);
+    if (!inplace) BTA_TRY(scale_into64(s, g.M, g.N, g.Cin, g.ldci, g.beta, g.C, g.ldc, g.lowerC, nb, g.sCi, g.sC));
     const int gm = Mp / TM, gn = Np / TN;
     long long tiles = (long long)gm * gn;
     if (g.lowerC) tiles = (tiles + gm) / 2;
+    tiles *= nb;
     int groups = 1;
     while (groups < 5 && tiles * groups < 152) ++groups;
     const int per = (NPAIRS + groups - 1) / groups;
     groups = (NPAIRS + per - 1) / per;
     Args a;
-    a.M = g.M; a.N = g.N; a.Mp = Mp; a.Np = Np; a.kblocks = Kp / TK;
+    a.M = g.M; a.N = g.N; a.groups = groups; a.sC = g.sC;
+    a.Mp = Mp; a.Np = Np; a.kblocks = Kp / TK;
     a.expA = expA; a.expB = expB;
     a.C = g.C; a.ldc = g.ldc; a.alpha = g.alpha;
     a.pairs_per_group = per;
@@ -503,7 +518,7 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
                                           (int)SMEM_BYTES));
         attr = true;
     }
-    ozaki_gemm_kernel<<<dim3(gm, gn, groups), THREADS, SMEM_BYTES, s>>>(mA, mB, a);
+    ozaki_gemm_kernel<<<dim3(gm, gn, nb * groups), THREADS, SMEM_BYTES, s>>>(mA, mB, a);
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }
@@ -512,8 +527,8 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
 // least min_dim go to the tensor cores, the rest (arrow, tip, small panels of
 // the recursive diagonal factorisation) stay on the FP64 pipe.
 int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
-    if (g.batch == 1 && g.M >= ex->min_dim && g.N >= ex->min_dim && g.K >= ex->min_dim &&
-        ozaki_workspace_bytes(g.M, g.N, g.K) <= ex->ws_bytes)
+    if (g.M >= ex->min_dim && g.N >= ex->min_dim && g.K >= ex->min_dim &&
+        (size_t)g.batch * ozaki_workspace_bytes(g.M, g.N, g.K) <= ex->ws_bytes)
         return ozaki_gemm(s, g, ex->ws, ex->err);
     return gemm64(s, g);
 }

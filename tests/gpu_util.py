@@ -41,11 +41,11 @@ def blocks_of(ctx, which, store, n, b, a):
 class GpuRun:
     """A model + context for one problem; params given directly or by theta."""
 
-    def __init__(self, problem, precision=0, stream=None):
+    def __init__(self, problem, precision=0, stream=None, batch=1):
         from paper_2507_06938_gb300 import bta
         self.p = problem
         self.model = bta.BtaModel(problem)
-        self.ctx = bta.BtaContext(problem.nt, problem.b, problem.a, precision, stream)
+        self.ctx = bta.BtaContext(problem.nt, problem.b, problem.a, precision, stream, batch)
 
     def assemble(self, params: omodel.Params, which):
         self.params_dev = dev(omodel.params_vector(params))

@@ -114,13 +114,13 @@ def test_fobj_matches_oracle(name):
     rng = np.random.default_rng(11)
     thetas = np.stack([p.theta0, p.theta0 + 0.1 * rng.standard_normal(p.theta0.shape)])
     f = torch.zeros(2, dtype=torch.float64, device="cuda")
-    mu = torch.zeros(p.N, dtype=torch.float64, device="cuda")
+    mu = torch.zeros((2, p.N), dtype=torch.float64, device="cuda")
     run.ctx.fobj_eval(run.model, dev(thetas), f, mu)
     run.ctx.sync()
     for j in range(2):
         terms = ofobj.f_obj_terms(p, thetas[j], tier="dense")
         assert abs(f[j].item() - terms["f"]) <= 1e-9 * abs(terms["f"]), j
-    assert rel_max(mu.cpu().numpy(), terms["mu"]) < 1e-9
+        assert rel_max(mu[j].cpu().numpy(), terms["mu"]) < 1e-9
 
 
 @pytest.mark.parametrize("name", ["t_uni_mid", "t_coreg3_mid"])
