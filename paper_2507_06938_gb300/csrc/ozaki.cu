@@ -3,8 +3,8 @@
 //
 // C += alpha * op(A) op(B) with FP64 A, B, C.  Every row i of op(A) is written
 // as 2^{e_i} sum_{p<S} d_p 2^{-7(p+1)} with integer digits |d_p| <= 128 (S = 5
-// slices, 36 bits below the row maximum), and every column j of op(B) the same
-// way with exponent f_j.  A digit is exact in bf16, a digit product is below
+// slices, 35 bits below the row's largest binary exponent, rounded), and every
+// column j of op(B) the same way with exponent f_j.  A digit is exact in bf16, a digit product is below
 // 2^14, so a sum of up to 1024 products is an integer below 2^24: the FP32
 // accumulator of tcgen05.mma kind::f16 holds it exactly.  The product is
 //   (op(A) op(B))_ij ~ 2^{e_i + f_j - 14} sum_{p+q<S} 2^{-7(p+q)} acc_pq(i,j)
@@ -41,7 +41,7 @@ namespace oz {
 constexpr int S = 5;
 constexpr int NPAIRS = S * (S + 1) / 2;
 constexpr int TM = 128, TN = 128, TK = 64;
-constexpr int STAGES = 4;
+constexpr int STAGES = 6;
 constexpr int KB_PER_CHUNK = 1024 / TK;   // exactness bound of one FP32 accumulation
 constexpr int THREADS = 320;
 constexpr uint32_t TMEM_COLS = 256;
@@ -66,6 +66,7 @@ struct Args {
     int pairs_per_group;
     int atomic;          // several pair groups add into C
     int lowerC;          // only entries m >= n (tiles strictly above skipped)
+    int shA, shB;        // triangular shapes of op(A), op(B): K blocks outside them are zero, skipped
     int* err;            // set to 1 on a wait time-out
 };
 
@@ -195,7 +196,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int inst = blockIdx.z / a.groups;
     const int pb = (blockIdx.z % a.groups) * a.pairs_per_group;
     const int pe = min(NPAIRS, pb + a.pairs_per_group);
-    const int nchunks = (a.kblocks + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
+    // K blocks that can hold non-zero digits for this tile
+    int kbl = 0, kbh = a.kblocks;
+    if (a.shA == 1) kbh = min(kbh, (m0 + TM + TK - 1) / TK);   // op(A) lower: k <= m
+    if (a.shA == 2) kbl = max(kbl, m0 / TK);                    // op(A) upper: k >= m
+    if (a.shB == 1) kbl = max(kbl, n0 / TK);                    // op(B) lower: k >= n
+    if (a.shB == 2) kbh = min(kbh, (n0 + TN + TK - 1) / TK);    // op(B) upper: k <= n
+    const int kspan = max(0, kbh - kbl);
+    const int nchunks = (kspan + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
     const int units = (pe - pb) * nchunks;
 
     if (threadIdx.x == 0) {
@@ -229,7 +237,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int u = 0; u < units && !*abort_flag; ++u) {
                 const int pair = pb + u / nchunks, chunk = u % nchunks;
                 const int p = c_pair_p[pair], q = c_pair_q[pair];
-                const int kb0 = chunk * KB_PER_CHUNK, kb1 = min(a.kblocks, kb0 + KB_PER_CHUNK);
+                const int kb0 = kbl + chunk * KB_PER_CHUNK, kb1 = min(kbh, kb0 + KB_PER_CHUNK);
                 for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int st = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
@@ -258,7 +266,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             int it = 0;
             for (int u = 0; u < units && !*abort_flag; ++u) {
                 const int chunk = u % nchunks;
-                const int kb0 = chunk * KB_PER_CHUNK, kb1 = min(a.kblocks, kb0 + KB_PER_CHUNK);
+                const int kb0 = kbl + chunk * KB_PER_CHUNK, kb1 = min(kbh, kb0 + KB_PER_CHUNK);
                 const int buf = u & 1;
                 const uint32_t aph = (u >> 1) & 1;
                 if (!mbar_wait(&accempty[buf], aph ^ 1, abort_flag, a.err)) break;
@@ -354,10 +362,14 @@ __global__ void __launch_bounds__(THREADS, 1)
 // ------------------------------------------------------------------ digit split
 // Rows r < R of X (R x K, X[r][k] = P[r*sr + k*sk]) with an optional
 // triangular mask (shape 1: X[r][k] = 0 for k > r; shape 2: for k < r).
-// e_r = exponent of the row maximum (|X[r][k]| < 2^{e_r}); digits
-// d_s = rint(x * 128), x <- x * 128 - d_s, starting from x = X[r][k] 2^{-e_r}.
-// Output: dig[s][r][k] (bf16, rows padded to Rp, K padded to Kp with zeros)
-// and exp[r] (0 for padding rows).
+// e_r = exponent of the row maximum (|X[r][k]| < 2^{e_r}).  Each entry is
+// turned into the 35-bit fixed-point integer V = round(X[r][k] 2^{35 - e_r})
+// (|V| < 2^35) and V into balanced base-128 digits d_0..d_4,
+// V = sum_s d_s 128^{4-s}, |d_s| <= 64 for s >= 1 and |d_0| <= 128, so that
+// X[r][k] 2^{-e_r} = sum_s d_s 2^{-7(s+1)} up to 2^{-36}.  Only integer
+// operations on the FP64 bit pattern are used (the FP64 pipe of GB300 is the
+// slow one).  Output: dig[s][r][k] (bf16, rows padded to Rp, K padded to Kp
+// with zeros) and exp[r] (0 for padding rows).
 constexpr int SPLIT_ROWS = 32, SPLIT_K = 64;
 
 __global__ void __launch_bounds__(256) row_maxexp_kernel(const double* P, long long sr, long long sk, int R, int K,
@@ -367,32 +379,57 @@ __global__ void __launch_bounds__(256) row_maxexp_kernel(const double* P, long l
     expo += (long long)blockIdx.y * Rp;
     const int r = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
     if (r >= Rp) return;
-    double mx = 0.0;
+    // the largest biased exponent field of the row decides e_r
+    unsigned int emax = 0;
     if (r < R) {
         int kb = 0, ke = K;
         if (shape == 1) ke = min(K, r + 1);
         if (shape == 2) kb = r;
-        for (int k = kb + lane; k < ke; k += 32) mx = fmax(mx, fabs(P[r * sr + k * sk]));
+        for (int k = kb + lane; k < ke; k += 32) {
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(P[r * sr + k * sk]);
+            const unsigned int ef = (unsigned int)((bits >> 52) & 0x7FF);
+            if (ef > emax) emax = ef;
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
     if (lane == 0) {
-        int e = 0;
-        if (mx > 0.0) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1): |x| < 2^e
-        expo[r] = e;
+        // |x| < 2^(ef - 1023 + 1) for a normal number with exponent field ef;
+        // a NaN or Inf in the row gives a huge exponent, so the product
+        // overflows to a non-finite value instead of passing silently
+        expo[r] = emax == 0 ? 0 : (emax == 0x7FF ? 4096 : (int)emax - 1023 + 1);
     }
+}
+
+__device__ __forceinline__ long long fixed_point35(double x, int e) {
+    // round(x 2^{35 - e}) for |x| < 2^e, by shifting the 53-bit significand
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ef = (int)((bits >> 52) & 0x7FF);
+    if (ef == 0) return 0;   // zero (subnormals are far below the 36-bit resolution of any row here)
+    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // x = m 2^{ef - 1075}
+    const int sh = (ef - 1075) + 35 - e;                                           // V = m 2^{sh}
+    unsigned long long v;
+    if (sh >= 0) {
+        v = m << sh;                                   // cannot overflow: |x| < 2^e gives V < 2^35
+    } else if (sh > -64) {
+        const int rs = -sh;
+        v = (m >> rs) + ((m >> (rs - 1)) & 1ull);      // round half up on the magnitude
+    } else {
+        v = 0;
+    }
+    const long long sv = (long long)v;
+    return (bits >> 63) ? -sv : sv;
 }
 
 __global__ void __launch_bounds__(256) split_digits_kernel(const double* P, long long sr, long long sk, int R, int K,
                                                            int shape, int Rp, int Kp, const int* expo,
                                                            __nv_bfloat16* dig, long long sP) {
-    // blockIdx.z = matrix: digits of matrix z start at dig + z S Rp Kp
+    // blockIdx.z = matrix: digits of matrix z start at dig + z S Rp Kp.  The
+    // tile (SPLIT_ROWS x SPLIT_K) is staged through shared memory so that both
+    // the FP64 read and the bf16 write are coalesced for either stride order.
+    __shared__ double tile[SPLIT_ROWS][SPLIT_K + 1];
     P += blockIdx.z * sP;
     expo += (long long)blockIdx.z * Rp;
     dig += (long long)blockIdx.z * S * Rp * Kp;
-    // tile: SPLIT_ROWS rows x SPLIT_K columns; staged through shared memory so
-    // that both the FP64 read and the bf16 write are coalesced whatever the
-    // stride direction of P
-    __shared__ double tile[SPLIT_ROWS][SPLIT_K + 1];
     const int r0 = blockIdx.y * SPLIT_ROWS, k0 = blockIdx.x * SPLIT_K;
     for (int e = threadIdx.x; e < SPLIT_ROWS * SPLIT_K; e += 256) {
         int rr, kk;
@@ -407,14 +444,18 @@ __global__ void __launch_bounds__(256) split_digits_kernel(const double* P, long
         const int kk = e % SPLIT_K, rr = e / SPLIT_K;
         const int r = r0 + rr, k = k0 + kk;
         if (r >= Rp || k >= Kp) continue;
-        double x = (r < R) ? ldexp(tile[rr][kk], -expo[r]) : 0.0;
+        long long V = (r < R) ? fixed_point35(tile[rr][kk], expo[r]) : 0;
+        int d[S];
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            x *= 128.0;
-            const double d = rint(x);
-            x -= d;
-            dig[((size_t)s * Rp + r) * Kp + k] = __float2bfloat16_rn((float)d);
+        for (int s = S - 1; s >= 1; --s) {
+            int low = (int)(V & 127);          // V mod 128 in [0, 128)
+            if (low >= 64) low -= 128;         // balanced digit in [-64, 64)
+            d[s] = low;
+            V = (V - low) >> 7;                // exact: V - low is a multiple of 128
         }
+        d[0] = (int)V;                         // |d_0| <= 128
+#pragma unroll
+        for (int s = 0; s < S; ++s) dig[((size_t)s * Rp + r) * Kp + k] = __int2bfloat16_rn(d[s]);
     }
 }
 
@@ -511,6 +552,8 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     a.pairs_per_group = per;
     a.atomic = groups > 1;
     a.lowerC = g.lowerC;
+    a.shA = g.shA;
+    a.shB = g.shB;
     a.err = err;
     static bool attr = false;
     if (!attr) {
