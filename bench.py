@@ -262,13 +262,15 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     with torch.cuda.stream(stream):
+        # the dominant GEMM launches carry timing events; the f_obj graph that
+        # the timed steps replay is captured with them during the warm-up
+        ctx.profile(True)
         for j in range(args.warmup):
             step(j, thetas_d[j], f_d[j])
         ctx.sync()
         barrier_sync()
         # ---- device-resident timed region
         launches0 = bta.bta_launch_count()
-        ctx.profile(True)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
@@ -320,6 +322,7 @@ def run_ours(args):
         if dist is not None:
             dist.destroy_process_group()
         return
+    # events of the last timed step (the graph replays the same launches every step)
     achieved = (prof_flops / (prof_ms / 1e3) / 1e12) if prof_ms > 0 else None
     if args.precision == "fp64":
         roof = {

@@ -236,7 +236,10 @@ int bta_matvec(bta_ctx_t ctx, int which, const double* x_dev, double* y_dev);
  * each group's 2 x batch matrices going through the same launches; in
  * mixed precision the solve takes two refinement steps with an FP64
  * residual.  Afterwards slot j holds the matrices and factors of theta
- * (last group start + j).
+ * (last group start + j).  From the second full group on, a full group is
+ * replayed from a CUDA graph captured on the context's stream (the thetas
+ * are first copied into a context buffer), so the stream must not be
+ * capturing already; BTA_GRAPH=0 in the environment turns this off.
  */
 int fobj_eval(bta_ctx_t ctx, bta_model_t model, const double* thetas_dev, int n_theta,
               double* f_out_dev, double* mu_out_dev);
@@ -259,9 +262,10 @@ long long bta_launch_count(void);
 
 /* bta_profile -- when enable != 0, record CUDA events around the two
  * b x b x b Schur-update GEMM launches of every factorisation step of this
- * context (counters reset).  bta_profile_read synchronises those events and
- * returns their summed duration (ms), the number of timed launches and their
- * nominal flops (b^3 each).  Measurement aid; no effect on results. */
+ * context.  bta_profile_read synchronises those events and returns their
+ * summed duration (ms), the number of timed launches and their nominal flops
+ * (b^3 per matrix each).  When fobj_eval replays its CUDA graph, the events
+ * are those of the last replay.  Measurement aid; no effect on results. */
 int bta_profile(bta_ctx_t ctx, int enable);
 int bta_profile_read(bta_ctx_t ctx, double* ms_total, long long* launches, double* flops_total);
 

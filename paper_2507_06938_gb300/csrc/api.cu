@@ -12,6 +12,7 @@ static thread_local cudaError_t g_last_cuda = cudaSuccess;
 static std::atomic<long long> g_launches{0};
 
 void bta_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void bta_note_launches(long long delta) { g_launches.fetch_add(delta, std::memory_order_relaxed); }
 
 extern "C" long long bta_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
@@ -101,6 +102,9 @@ extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch,
     if ((rc = dalloc(&c->ld, nm)) != BTA_OK) return fail(rc);
     if ((rc = dalloc(&c->dots, 3 * (size_t)nm)) != BTA_OK) return fail(rc);
     if ((rc = dalloc(&c->params, (size_t)batch * BTA_PSTRIDE)) != BTA_OK) return fail(rc);
+    if ((rc = dalloc(&c->theta_buf, (size_t)batch * BTA_PSTRIDE)) != BTA_OK) return fail(rc);
+    if ((rc = dalloc(&c->f_buf, (size_t)batch)) != BTA_OK) return fail(rc);
+    if (const char* e = std::getenv("BTA_GRAPH")) c->use_graph = std::atoi(e);
     if (cudaMemset(c->params, 0, (size_t)batch * BTA_PSTRIDE * sizeof(double)) != cudaSuccess)
         return fail(BTA_ERR_CUDA);
     if (cudaMalloc((void**)&c->status, 4 * sizeof(long long)) != cudaSuccess) return fail(BTA_ERR_OOM);
@@ -145,7 +149,8 @@ extern "C" int bta_destroy(bta_ctx_t c) {
     store_free(c->Q);
     store_free(c->L);
     store_free(c->S);
-    double* bufs[] = {c->Linv, c->work, c->vec, c->red, c->ld, c->dots, c->params};
+    if (c->fobj_graph) cudaGraphExecDestroy(c->fobj_graph);
+    double* bufs[] = {c->Linv, c->work, c->vec, c->red, c->ld, c->dots, c->params, c->theta_buf, c->f_buf};
     for (double* p : bufs)
         if (p) cudaFree(p);
     if (c->exec.ws) cudaFree(c->exec.ws);
@@ -209,6 +214,16 @@ extern "C" int bta_block_ptr(bta_ctx_t c, int which, int store, int kind, int i,
     }
 }
 
+// Record a timing event; inside a stream capture as an external event-record
+// node of the graph (a plain record there would only order the capture).
+int prof_record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    BTA_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusActive) BTA_CUDA_TRY(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+    else BTA_CUDA_TRY(cudaEventRecord(e, s));
+    return BTA_OK;
+}
+
 int prof_begin(bta_ctx_t ctx, cudaStream_t s, double flops, cudaEvent_t* stop_out) {
     *stop_out = nullptr;
     if (!ctx->prof) return BTA_OK;
@@ -222,14 +237,23 @@ int prof_begin(bta_ctx_t ctx, cudaStream_t s, double flops, cudaEvent_t* stop_ou
     cudaEvent_t start = ctx->prof_ev[ctx->prof_used], stop = ctx->prof_ev[ctx->prof_used + 1];
     ctx->prof_used += 2;
     ctx->prof_flops += flops;
-    BTA_CUDA_TRY(cudaEventRecord(start, s));
+    BTA_TRY(prof_record(start, s));
     *stop_out = stop;
     return BTA_OK;
 }
 
 extern "C" int bta_profile(bta_ctx_t c, int enable) {
     if (!c) return BTA_ERR_ARG;
-    c->prof = enable ? 1 : 0;
+    enable = enable ? 1 : 0;
+    if (enable == c->prof) return BTA_OK;
+    // a captured f_obj graph has the event records of the old setting baked in
+    if (c->fobj_graph) {
+        cudaStreamSynchronize(c->stream);
+        cudaGraphExecDestroy(c->fobj_graph);
+        c->fobj_graph = nullptr;
+        c->graph_calls = 1;
+    }
+    c->prof = enable;
     c->prof_used = 0;
     c->prof_flops = 0.0;
     return BTA_OK;

@@ -30,6 +30,7 @@ int bta_cuda_fail(cudaError_t e);
 // Every kernel launch of the library is followed by BTA_LAUNCH_CHECK(): it
 // counts the launch (bta_launch_count) and turns a launch error into a code.
 void bta_note_launch();
+void bta_note_launches(long long delta);   // graph replays and captures
 #define BTA_LAUNCH_CHECK()                                   \
     do {                                                     \
         bta_note_launch();                                   \
@@ -122,6 +123,15 @@ struct bta_ctx_s {
     int leaf;                // leaf size of the recursive diagonal factorisation
     long long last_info = -1;
     int last_matrix = -1;
+    // CUDA graph of one full f_obj group (batch thetas), replayed with the
+    // thetas staged in theta_buf and the values written to f_buf
+    cudaGraphExec_t fobj_graph = nullptr;
+    const void* graph_model = nullptr;
+    int graph_calls = 0;     // full groups evaluated so far (the first runs uncaptured)
+    long long graph_kernels = 0;   // kernel nodes of the captured graph
+    int use_graph = 1;
+    double* theta_buf = nullptr;   // batch x dim_theta (dim <= BTA_PSTRIDE)
+    double* f_buf = nullptr;       // batch
     // optional event timing of the b x b x b Schur-update GEMM launches
     int prof = 0;
     std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
@@ -138,6 +148,7 @@ inline int public_index(const bta_ctx_s* c, int m) { return 2 * (m % c->batch) +
 
 // Record an event pair around the next launch on stream s when profiling.
 int prof_begin(bta_ctx_t ctx, cudaStream_t s, double flops, cudaEvent_t* stop_out);
+int prof_record(cudaEvent_t e, cudaStream_t s);
 
 // ---------------------------------------------------------------- FP64 dense kernels (dense64.cu)
 int gemm64(cudaStream_t s, const Gemm64& g);

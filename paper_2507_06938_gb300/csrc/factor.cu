@@ -59,7 +59,7 @@ int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
             cudaEvent_t stop;
             BTA_TRY(prof_begin(ctx, s, (double)cnt * b * b * b, &stop));
             BTA_TRY(gemm_exec(ex, s, g));
-            if (stop) BTA_CUDA_TRY(cudaEventRecord(stop, s));
+            if (stop) BTA_TRY(prof_record(stop, s));
             // D_{i+1} = Q.D_{i+1} - L_{i+1,i} L_{i+1,i}^T   (lower)
             g = Gemm64{};
             g.M = b; g.N = b; g.K = b;
@@ -70,7 +70,7 @@ int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
             g.batch = cnt; g.sA = L.sB; g.sB = L.sB; g.sCi = Q.sD; g.sC = L.sD;
             BTA_TRY(prof_begin(ctx, s, (double)cnt * b * b * b, &stop));
             BTA_TRY(gemm_exec(ex, s, g));
-            if (stop) BTA_CUDA_TRY(cudaEventRecord(stop, s));
+            if (stop) BTA_TRY(prof_record(stop, s));
         }
         if (a > 0) {
             double* Lri = LR + i * ab;

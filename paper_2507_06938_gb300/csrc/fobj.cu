@@ -58,55 +58,117 @@ __global__ void fobj_final_kernel(const double* theta, const double* theta0, int
 
 }  // namespace
 
+// One group of cnt thetas (at `theta`, cnt x dim) -> f (cnt values); mu of
+// the group stays in the VEC_MU rows of the Q_c matrices.
+static int fobj_group(bta_ctx_t ctx, bta_model_t m, const double* theta, int cnt, double* f, cudaStream_t s) {
+    const int B = ctx->batch;
+    const long long N = ctx->N, nb = (long long)ctx->n * ctx->b;
+    BTA_TRY(theta_to_params_impl(m, theta, cnt, ctx->params, s));
+    if (cnt == B) {
+        // all Q_p and Q_c of the batch in one pass
+        BTA_TRY(assemble_impl(ctx, m, ctx->params, 0, 2 * B, s));
+        BTA_TRY(factor_impl(ctx, 0, 2 * B, s));
+        BTA_TRY(logdet_impl(ctx, 0, 2 * B, ctx->ld, s));
+    } else {
+        for (int kind = 0; kind < 2; ++kind) {
+            BTA_TRY(assemble_impl(ctx, m, ctx->params, kind * B, cnt, s));
+            BTA_TRY(factor_impl(ctx, kind * B, cnt, s));
+            BTA_TRY(logdet_impl(ctx, kind * B, cnt, ctx->ld + kind * B, s));
+        }
+    }
+    double* rhs = vec_row(ctx, VEC_RHS, B);
+    double* mu = vec_row(ctx, VEC_MU, B);
+    {
+        int blocks = (int)std::min<long long>((N + 255) / 256, 152 * 8 / cnt + 1);
+        fobj_rhs_kernel<<<dim3(blocks, cnt), 256, 0, s>>>(m->aty, ctx->params, nb, ctx->b, m->ns,
+                                                          m->nr > 0 ? m->nr : 1, N, rhs);
+        BTA_LAUNCH_CHECK();
+    }
+    BTA_TRY(solve_impl(ctx, B, cnt, rhs, mu, s));
+    // iterative refinement with an FP64 residual on the assembled blocks
+    for (int it = 0; it < ctx->refine; ++it) {
+        double* res = vec_row(ctx, VEC_RES, B);
+        double* corr = vec_row(ctx, VEC_CORR, B);
+        BTA_TRY(matvec_impl(ctx, B, cnt, mu, res, s));
+        BTA_TRY(axpby64(s, cnt * N, 1.0, rhs, -1.0, res, res));
+        BTA_TRY(solve_impl(ctx, B, cnt, res, corr, s));
+        BTA_TRY(axpby64(s, cnt * N, 1.0, mu, 1.0, corr, mu));
+    }
+    BTA_TRY(dot_batch64(s, rhs, mu, N, cnt, ctx->red + (long long)B * ctx->red_chunks, ctx->red_chunks,
+                        ctx->dots + 3 * B, 3));
+    fobj_final_kernel<<<cnt, 1, 0, s>>>(theta, m->theta0, m->dim_theta, ctx->params, m->var_stats, m->nv,
+                                        (double)m->m, ctx->ld, ctx->ld + B, ctx->dots + 3 * B, f);
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}
+
+// Full groups replay a CUDA graph of fobj_group (captured on the second full
+// group, so that every one-time set-up has happened outside the capture).  The
+// graph is captured and launched on the context's private non-blocking stream,
+// ordered after and before the caller's stream by events (the caller's stream
+// may be the legacy default stream, which cannot be captured).
+static int fobj_full_group_graph(bta_ctx_t ctx, bta_model_t m, cudaStream_t user) {
+    cudaStream_t s = ctx->aux;
+    BTA_CUDA_TRY(cudaEventRecord(ctx->ev_fork, user));
+    BTA_CUDA_TRY(cudaStreamWaitEvent(s, ctx->ev_fork, 0));
+    if (ctx->fobj_graph && ctx->graph_model != (const void*)m) {
+        cudaGraphExecDestroy(ctx->fobj_graph);
+        ctx->fobj_graph = nullptr;
+    }
+    if (!ctx->fobj_graph) {
+        cudaGraph_t g = nullptr;
+        // timing events (if profiling) then describe this graph's launches only
+        ctx->prof_used = 0;
+        ctx->prof_flops = 0.0;
+        const long long l0 = bta_launch_count();
+        BTA_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const int rc = fobj_group(ctx, m, ctx->theta_buf, ctx->batch, ctx->f_buf, s);
+        const cudaError_t ce = cudaStreamEndCapture(s, &g);
+        // captured launches run when the graph does, not now
+        ctx->graph_kernels = bta_launch_count() - l0;
+        bta_note_launches(-ctx->graph_kernels);
+        if (rc != BTA_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        BTA_CUDA_TRY(ce);
+        const cudaError_t ie = cudaGraphInstantiate(&ctx->fobj_graph, g, 0);
+        cudaGraphDestroy(g);
+        BTA_CUDA_TRY(ie);
+        ctx->graph_model = m;
+    }
+    BTA_CUDA_TRY(cudaGraphLaunch(ctx->fobj_graph, s));
+    bta_note_launches(ctx->graph_kernels);
+    BTA_CUDA_TRY(cudaEventRecord(ctx->ev_join, s));
+    BTA_CUDA_TRY(cudaStreamWaitEvent(user, ctx->ev_join, 0));
+    return BTA_OK;
+}
+
 extern "C" int fobj_eval(bta_ctx_t ctx, bta_model_t m, const double* thetas_dev, int n_theta, double* f_out_dev,
                          double* mu_out_dev) {
     if (!ctx || !m || !thetas_dev || !f_out_dev || n_theta < 1) return BTA_ERR_ARG;
-    if (m->n != ctx->n || m->b != ctx->b || m->a != ctx->a || m->nv > BTA_MAX_NV) return BTA_ERR_ARG;
+    if (m->n != ctx->n || m->b != ctx->b || m->a != ctx->a || m->nv > BTA_MAX_NV ||
+        m->dim_theta > BTA_PSTRIDE)
+        return BTA_ERR_ARG;
     cudaStream_t s = ctx->stream;
     const int B = ctx->batch;
-    const long long N = ctx->N, nb = (long long)ctx->n * ctx->b;
+    const long long N = ctx->N;
     for (int r0 = 0; r0 < n_theta; r0 += B) {
         const int cnt = std::min(B, n_theta - r0);
         const double* theta = thetas_dev + (long long)r0 * m->dim_theta;
-        BTA_TRY(theta_to_params_impl(m, theta, cnt, ctx->params, s));
-        if (cnt == B) {
-            // all Q_p and Q_c of the batch in one pass
-            BTA_TRY(assemble_impl(ctx, m, ctx->params, 0, 2 * B, s));
-            BTA_TRY(factor_impl(ctx, 0, 2 * B, s));
-            BTA_TRY(logdet_impl(ctx, 0, 2 * B, ctx->ld, s));
-        } else {
-            for (int kind = 0; kind < 2; ++kind) {
-                BTA_TRY(assemble_impl(ctx, m, ctx->params, kind * B, cnt, s));
-                BTA_TRY(factor_impl(ctx, kind * B, cnt, s));
-                BTA_TRY(logdet_impl(ctx, kind * B, cnt, ctx->ld + kind * B, s));
-            }
-        }
-        double* rhs = vec_row(ctx, VEC_RHS, B);
-        double* mu = vec_row(ctx, VEC_MU, B);
-        {
-            int blocks = (int)std::min<long long>((N + 255) / 256, 152 * 8 / cnt + 1);
-            fobj_rhs_kernel<<<dim3(blocks, cnt), 256, 0, s>>>(m->aty, ctx->params, nb, ctx->b, m->ns,
-                                                              m->nr > 0 ? m->nr : 1, N, rhs);
-            BTA_LAUNCH_CHECK();
-        }
-        BTA_TRY(solve_impl(ctx, B, cnt, rhs, mu, s));
-        // iterative refinement with an FP64 residual on the assembled blocks
-        for (int it = 0; it < ctx->refine; ++it) {
-            double* res = vec_row(ctx, VEC_RES, B);
-            double* corr = vec_row(ctx, VEC_CORR, B);
-            BTA_TRY(matvec_impl(ctx, B, cnt, mu, res, s));
-            BTA_TRY(axpby64(s, cnt * N, 1.0, rhs, -1.0, res, res));
-            BTA_TRY(solve_impl(ctx, B, cnt, res, corr, s));
-            BTA_TRY(axpby64(s, cnt * N, 1.0, mu, 1.0, corr, mu));
-        }
-        BTA_TRY(dot_batch64(s, rhs, mu, N, cnt, ctx->red + (long long)B * ctx->red_chunks, ctx->red_chunks,
-                            ctx->dots + 3 * B, 3));
-        fobj_final_kernel<<<cnt, 1, 0, s>>>(theta, m->theta0, m->dim_theta, ctx->params, m->var_stats, m->nv,
-                                            (double)m->m, ctx->ld, ctx->ld + B, ctx->dots + 3 * B, f_out_dev + r0);
-        BTA_LAUNCH_CHECK();
-        if (mu_out_dev)
-            BTA_CUDA_TRY(cudaMemcpyAsync(mu_out_dev + (long long)r0 * N, mu, cnt * N * sizeof(double),
+        if (cnt == B && ctx->use_graph && ctx->graph_calls++ > 0) {
+            BTA_CUDA_TRY(cudaMemcpyAsync(ctx->theta_buf, theta, (size_t)B * m->dim_theta * sizeof(double),
                                          cudaMemcpyDeviceToDevice, s));
+            BTA_TRY(fobj_full_group_graph(ctx, m, s));
+            BTA_CUDA_TRY(cudaMemcpyAsync(f_out_dev + r0, ctx->f_buf, (size_t)B * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, s));
+            for (int mm = 0; mm < 2 * B; ++mm) ctx->factored[mm] = 1;
+        } else {
+            BTA_TRY(fobj_group(ctx, m, theta, cnt, f_out_dev + r0, s));
+        }
+        if (mu_out_dev)
+            BTA_CUDA_TRY(cudaMemcpyAsync(mu_out_dev + (long long)r0 * N, vec_row(ctx, VEC_MU, B),
+                                         cnt * N * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
     return BTA_OK;
 }

@@ -79,3 +79,25 @@ def test_batched_error_names_the_matrix():
     assert e.value.code == bta.BTA_ERR_NOT_PD
     assert e.value.info == 2 * p.b + 3
     assert e.value.matrix == 2 * 2 + bta.BTA_QC
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_matches_direct(precision, monkeypatch):
+    """From the second full group on, fobj_eval replays a captured CUDA graph;
+    its values must equal those of the direct launches, for new thetas too."""
+    import torch
+    monkeypatch.setenv("BTA_OZ_MIN", "64")
+    p = problem("t_uni_mid")
+    run = GpuRun(p, precision=precision, batch=3)
+    rng = np.random.default_rng(21)
+    tol = 1e-9 if precision == 0 else 1e-7
+    for call in range(4):
+        thetas = p.theta0 + 0.05 * rng.standard_normal((3, p.theta0.shape[0]))
+        f = torch.zeros(3, dtype=torch.float64, device="cuda")
+        mu = torch.zeros((3, p.N), dtype=torch.float64, device="cuda")
+        run.ctx.fobj_eval(run.model, dev(thetas), f, mu)
+        run.ctx.sync()
+        for j in range(3):
+            terms = ofobj.f_obj_terms(p, thetas[j])
+            assert abs(f[j].item() - terms["f"]) <= tol * abs(terms["f"]), (call, j)
+            assert rel_max(mu[j].cpu().numpy(), terms["mu"]) < 1e-8, (call, j)
