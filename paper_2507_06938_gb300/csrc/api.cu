@@ -113,8 +113,10 @@ extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch,
     if (precision == BTA_MIXED) {
         if (cudaMalloc((void**)&c->oz_err, sizeof(int)) != cudaSuccess) return fail(BTA_ERR_OOM);
         if (cudaMemset(c->oz_err, 0, sizeof(int)) != cudaSuccess) return fail(BTA_ERR_CUDA);
-        int min_dim = 256;
+        int min_dim = 128;
         if (const char* e = std::getenv("BTA_OZ_MIN")) min_dim = std::atoi(e);
+        c->exec.df_leaf = 64;
+        if (const char* e = std::getenv("BTA_DF_LEAF")) c->exec.df_leaf = std::atoi(e);
         const size_t wsb = (size_t)nm * ozaki_workspace_bytes(b, b, b);
         if (cudaMalloc(&c->exec.ws, wsb) != cudaSuccess) {
             c->exec.ws = nullptr;

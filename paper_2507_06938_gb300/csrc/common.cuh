@@ -80,6 +80,7 @@ struct GemmExec {
     size_t ws_bytes;
     int* err;          // device error flag of the tensor-core kernel
     int min_dim;       // smallest M, N (and K) sent to the tensor-core path
+    int df_leaf = 0;   // > 0: diagonal leaves of this order in double-float (leaf_df32.cu)
 };
 
 // ---------------------------------------------------------------- BTA storage
@@ -162,6 +163,10 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
                long long row0, long long* status, double* W, int leaf, const GemmExec* ex = nullptr,
                int batch = 1, long long sA = 0, long long sX = 0, long long sW = 0, int m_first = 0,
                int nbatch = 1);
+// Double-float Cholesky + inverse of `batch` blocks of order n <= 128 (leaf_df32.cu).
+int chol_inv_df32_launch(cudaStream_t s, double* A, long long lda, long long sA, double* X, long long ldx,
+                         long long sX, int n, long long row0, long long* status, int batch, int m_first,
+                         int nbatch);
 int copy_mat64(cudaStream_t s, const double* src, long long lds, double* dst, long long ldd,
                int rows, int cols, int lower_only, int batch = 1, long long ss = 0, long long sd = 0);
 // C = beta Cin (C = 0 if beta == 0); only entries m >= n when lower

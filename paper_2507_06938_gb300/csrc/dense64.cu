@@ -442,8 +442,15 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
                long long* status, double* W, int leaf, const GemmExec* ex, int batch, long long sA,
                long long sX, long long sW, int m_first, int nbatch) {
     if (n <= 0 || batch <= 0) return BTA_OK;
-    leaf = std::max(8, std::min(leaf, LEAF_MAX));
-    if (n <= leaf) return leaf_launch(s, A, lda, sA, X, ldx, sX, n, row0, status, batch, m_first, nbatch);
+    if (ex && ex->df_leaf > 0) {
+        // mixed precision: double-float leaves on the FP32 pipe
+        leaf = std::min(ex->df_leaf, 128);
+        if (n <= leaf)
+            return chol_inv_df32_launch(s, A, lda, sA, X, ldx, sX, n, row0, status, batch, m_first, nbatch);
+    } else {
+        leaf = std::max(8, std::min(leaf, LEAF_MAX));
+        if (n <= leaf) return leaf_launch(s, A, lda, sA, X, ldx, sX, n, row0, status, batch, m_first, nbatch);
+    }
     const int half = (n + 1) / 2;
     int n1 = ((half + leaf - 1) / leaf) * leaf;
     if (n1 >= n) n1 = leaf;

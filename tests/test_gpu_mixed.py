@@ -83,3 +83,31 @@ def test_mixed_fobj(name, monkeypatch):
     tol = 1e-8 * (abs(terms["logdet_p"]) + abs(terms["logdet_c"]))
     assert abs(f.item() - terms["f"]) <= tol
     assert rel_max(mu.cpu().numpy(), terms["mu"]) < 1e-9
+
+
+@pytest.mark.parametrize("b", [37, 100, 128])
+def test_double_float_leaf(b):
+    """Mixed precision factors diagonal blocks of order <= 128 in double-float
+    (two FP32 words, about 48 bits): L and L^{-1} must match the FP64
+    Cholesky to 1e-11 relative; a non-positive pivot is reported."""
+    import torch
+    from paper_2507_06938_gb300 import bta
+    rng = np.random.default_rng(b)
+    M = rng.standard_normal((b, b))
+    S = M @ M.T / b + 0.5 * np.eye(b)
+    ctx = bta.BtaContext(1, b, 0, bta.BTA_MIXED)
+    ctx.block(bta.BTA_QP, bta.BTA_STORE_Q, bta.BTA_BLK_D, 0).copy_(torch.as_tensor(S, device="cuda"))
+    ctx.factor(bta.BTA_QP)
+    ctx.sync()
+    L = np.tril(ctx.block(bta.BTA_QP, bta.BTA_STORE_L, bta.BTA_BLK_D, 0).cpu().numpy())
+    X = ctx.block(bta.BTA_QP, bta.BTA_STORE_LINV, bta.BTA_BLK_D, 0).cpu().numpy()
+    Lref = np.linalg.cholesky(S)
+    assert rel_max(L, Lref) < 1e-11
+    assert rel_max(X, np.linalg.inv(Lref)) < 1e-11
+    S[b // 2, b // 2] = -1.0
+    ctx.block(bta.BTA_QP, bta.BTA_STORE_Q, bta.BTA_BLK_D, 0).copy_(torch.as_tensor(S, device="cuda"))
+    ctx.factor(bta.BTA_QP)
+    with pytest.raises(bta.BtaError) as e:
+        ctx.sync()
+    assert e.value.code == bta.BTA_ERR_NOT_PD
+    assert e.value.info <= b // 2
