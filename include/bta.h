@@ -244,6 +244,20 @@ int bta_matvec(bta_ctx_t ctx, int which, const double* x_dev, double* y_dev);
 int fobj_eval(bta_ctx_t ctx, bta_model_t model, const double* thetas_dev, int n_theta,
               double* f_out_dev, double* mu_out_dev);
 
+/*
+ * bta_fobj_grad -- f_obj and its gradient with respect to theta for n_theta
+ * hyperparameter vectors (device, n_theta x dim(theta)), by the adjoint form
+ * of Eq. 8 for a Gaussian likelihood instead of the central differences of
+ * Eq. 10 (b = A^T D y, mu = Q_c^{-1} b, Sigma = Q^{-1}):
+ *   df/dtheta_k = d log p(theta) + 1/2 tr(Sigma_p dQ_p) - 1/2 tr(Sigma_c dQ_c)
+ *                 - 1/2 y^T dD y + db^T mu - 1/2 mu^T dQ_c mu + 1/2 tr(D^{-1} dD).
+ * Runs fobj_eval, the selected inversion of every Q_p and Q_c of a group,
+ * and the trace kernels; the traces need Sigma only on the BTA pattern.
+ * f_out_dev receives n_theta values, grad_out_dev n_theta x dim(theta).
+ */
+int bta_fobj_grad(bta_ctx_t ctx, bta_model_t model, const double* thetas_dev, int n_theta, double* f_out_dev,
+                  double* grad_out_dev);
+
 /* bta_sync -- wait for the context's stream; return the first error the
  * device recorded since the last bta_sync (and clear it), else BTA_OK. */
 int bta_sync(bta_ctx_t ctx);

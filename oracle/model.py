@@ -57,7 +57,9 @@ class Params:
 def theta_to_params(theta: np.ndarray, nv: int) -> Params:
     """Hyperparameters (log range_s, log range_t, log sigma, log tau_eps per
     variable, then lambda) to model parameters."""
-    theta = np.asarray(theta, dtype=np.float64)
+    theta = np.asarray(theta)
+    if not np.iscomplexobj(theta):          # complex theta: complex-step derivatives
+        theta = theta.astype(np.float64)
     per = theta[: 4 * nv].reshape(nv, 4)
     range_s = np.exp(per[:, 0])
     range_t = np.exp(per[:, 1])
@@ -85,7 +87,7 @@ def params_from_vector(vec: np.ndarray, nv: int) -> Params:
 def mixing_inverse(lam: np.ndarray, nv: int) -> np.ndarray:
     """M^{-1}: unit lower triangular, -lambda below the diagonal, sub-diagonal
     by sub-diagonal (offset 1 first, top to bottom)."""
-    Minv = np.eye(nv)
+    Minv = np.eye(nv, dtype=np.result_type(lam, np.float64))
     k = 0
     for off in range(1, nv):
         for v in range(off, nv):

@@ -68,6 +68,7 @@ def lib():
         "bta_factor_batch": (ip, [vp, ip]),
         "bta_selinv_batch": (ip, [vp, ip]),
         "bta_last_error_matrix": (ip, [vp, C.POINTER(ip)]),
+        "bta_fobj_grad": (ip, [vp, vp, vp, ip, vp, vp]),
         "bta_destroy": (ip, [vp]),
         "bta_assemble": (ip, [vp, vp, vp, ip]),
         "bta_theta_to_params": (ip, [vp, vp, vp, vp]),
@@ -105,7 +106,7 @@ def exported_symbols():
             "bta_strerror", "bta_flops_factor", "bta_flops_selinv", "bta_selinv_diag",
             "bta_launch_count", "bta_profile", "bta_profile_read", "bta_chol_inv_noalloc",
             "bta_create_batched", "bta_batch_size", "bta_factor_batch", "bta_selinv_batch",
-            "bta_last_error_matrix"]
+            "bta_last_error_matrix", "bta_fobj_grad"]
 
 
 def _check(code: int, where: str):
@@ -253,6 +254,11 @@ class BtaContext:
         _check(lib().bta_profile_read(self.handle, C.byref(ms), C.byref(n), C.byref(fl)), "bta_profile_read")
         return ms.value, n.value, fl.value
 
+    def fobj_grad(self, model: BtaModel, thetas, f_out, grad_out):
+        n_theta = int(thetas.shape[0]) if thetas.dim() == 2 else 1
+        _check(lib().bta_fobj_grad(self.handle, model.handle, _ptr(thetas), n_theta, _ptr(f_out), _ptr(grad_out)),
+               "bta_fobj_grad")
+
     def sync(self):
         code = lib().bta_sync(self.handle)
         if code != BTA_OK:
@@ -328,6 +334,10 @@ def bta_matvec(ctx: BtaContext, which: int, x, y):
 
 def fobj_eval(ctx: BtaContext, model: BtaModel, thetas, f_out, mu_out=None):
     ctx.fobj_eval(model, thetas, f_out, mu_out)
+
+
+def bta_fobj_grad(ctx: BtaContext, model: BtaModel, thetas, f_out, grad_out):
+    ctx.fobj_grad(model, thetas, f_out, grad_out)
 
 
 def bta_sync(ctx: BtaContext):

@@ -152,7 +152,8 @@ extern "C" int bta_destroy(bta_ctx_t c) {
     store_free(c->L);
     store_free(c->S);
     if (c->fobj_graph) cudaGraphExecDestroy(c->fobj_graph);
-    double* bufs[] = {c->Linv, c->work, c->vec, c->red, c->ld, c->dots, c->params, c->theta_buf, c->f_buf};
+    double* bufs[] = {c->Linv, c->work, c->vec, c->red, c->ld, c->dots, c->params, c->theta_buf, c->f_buf,
+                      c->adj};
     for (double* p : bufs)
         if (p) cudaFree(p);
     if (c->exec.ws) cudaFree(c->exec.ws);

@@ -18,30 +18,11 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "model_coef.cuh"
 
 namespace {
 
 constexpr int ASM_THREADS = 256;
-
-// M^{-1} entry [row][colv] from lambda: unit lower triangular, -lambda below
-// the diagonal ordered sub-diagonal by sub-diagonal.
-__device__ __forceinline__ double minv_entry(const double* lam, int nv, int row, int colv) {
-    if (row == colv) return 1.0;
-    if (row < colv) return 0.0;
-    int off = row - colv;
-    int k = 0;
-    for (int o = 1; o < off; ++o) k += nv - o;
-    k += colv;  // position within sub-diagonal `off` is the column index
-    return -lam[k];
-}
-
-__device__ __forceinline__ double ar1_entry(double rho, int nt, int ti, int tj) {
-    if (nt == 1) return 1.0;
-    double inv = 1.0 / (1.0 - rho * rho);
-    if (ti == tj) return ((ti == 0 || ti == nt - 1) ? 1.0 : 1.0 + rho * rho) * inv;
-    if (ti - tj == 1 || tj - ti == 1) return -rho * inv;
-    return 0.0;
-}
 
 struct AsmArgs {
     int n, b, a, ns, nv, nr, nt, nnz;

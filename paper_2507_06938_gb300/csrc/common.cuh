@@ -133,6 +133,7 @@ struct bta_ctx_s {
     int use_graph = 1;
     double* theta_buf = nullptr;   // batch x dim_theta (dim <= BTA_PSTRIDE)
     double* f_buf = nullptr;       // batch
+    double* adj = nullptr;         // adjoint trace records (3 x batch)
     // optional event timing of the b x b x b Schur-update GEMM launches
     int prof = 0;
     std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)

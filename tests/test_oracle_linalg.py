@@ -113,3 +113,33 @@ def test_fd_gradient_matches_second_order_accuracy():
     g1 = fobj.fd_gradient(p, p.theta0, h=2e-3, tier="dense")
     g2 = fobj.fd_gradient(p, p.theta0, h=1e-3, tier="dense")
     assert np.max(np.abs(g1 - g2)) < 1e-3 * max(1.0, np.max(np.abs(g2)))
+
+
+@pytest.mark.parametrize("name", ["t_uni", "t_coreg2", "t_coreg3"])
+def test_adjoint_gradient_matches_finite_differences(name):
+    """The analytic (adjoint) gradient against central differences of f_obj
+    (Eq. 10, h = 1e-4: truncation error ~h^2)."""
+    p = synth.problem_from_config(name)
+    theta = p.theta0 + 0.1 * np.random.default_rng(3).standard_normal(p.theta0.shape)
+    g = fobj.grad_adjoint(p, theta)
+    gfd = fobj.fd_gradient(p, theta, h=1e-4, tier="dense")
+    scale = np.maximum(np.abs(g), 1e-3 * np.max(np.abs(g)))
+    assert np.max(np.abs(g - gfd) / scale) < 1e-5
+
+
+def test_logdet_derivative_closed_forms():
+    """1/2 tr(Q_p^{-1} dQ_p) is 1/2 d log|Q_p|: for the univariate prior,
+    d/d log sigma = -(ns nt + nr) and d/d log range_t = ns (nt-1) rho^2 r / (1-rho^2)
+    with r = 1/range_t (log|Q_t| = -(nt-1) log(1-rho^2), rho = exp(-r))."""
+    p = synth.problem_from_config("t_uni")
+    theta = p.theta0.copy()
+    theta[1] = math.log(2.5)
+    fd = model.fem_data(p)
+    prm = model.theta_to_params(theta, 1)
+    Sp = dense.inverse(model.build(p, prm, fd).Qp)
+    dQs, _, _, _ = fobj.model_derivatives(p, theta, 2, fd)
+    assert abs(0.5 * np.sum(Sp * dQs.toarray()) + (p.ns * p.nt + p.nr)) < 1e-8 * p.N
+    dQt, _, _, _ = fobj.model_derivatives(p, theta, 1, fd)
+    rho, r = prm.rho[0], 1.0 / 2.5
+    expect = p.ns * (p.nt - 1) * rho * rho * r / (1 - rho * rho)
+    assert abs(0.5 * np.sum(Sp * dQt.toarray()) - expect) < 1e-8 * abs(expect)
