@@ -1,13 +1,14 @@
 #!/usr/bin/env python
 """Throughput of the BTA hot path of one f_obj(theta) evaluation on GB300.
 
-One step = one BFGS gradient stencil of the univariate AR(1) x SPDE model at
-working size (32 x 32 grid mesh: ns = 1024, nt = 64, nb = 4 fixed effects,
-m = 65,536 observations, N = 65,540): f_obj(theta) at the 2 dim(theta) + 1 = 9
-central-difference points (Eq. 10), each with assembly, factorisation and
-log-determinant of Q_p and Q_c, the conditional-mean solve and the objective,
-plus the selected inversion of every Q_c.  All 18 BTA matrices of a step go
-through the same kernel launches.  Each step uses a different theta.
+One step = one batch of 2 dim(theta) + 1 = 9 theta points (the stencil of
+Eq. 10) of the univariate AR(1) x SPDE model at working size (32 x 32 grid
+mesh: ns = 1024, nt = 64, nb = 4 fixed effects, m = 65,536 observations,
+N = 65,540), each with the whole hot path: assembly, factorisation and
+log-determinant of Q_p and Q_c, the conditional-mean solve, f_obj, the
+selected inversion of Q_p and Q_c and the adjoint gradient of f_obj.  All 18
+BTA matrices of a step go through the same kernel launches.  Each step uses a
+different stencil centre.
 
 value  = f_obj evaluations / s with inputs resident in HBM (device-timed)
 e2e    = the same through the C ABI with the thetas copied host->device and
@@ -34,8 +35,9 @@ sys.path.insert(0, ROOT)
 METRIC = "f_obj evals/s and BTA Cholesky+selinv TFLOP/s: mixed vs FP64 on one GB300"
 UNIT = "f_obj evals/s"
 WORKLOAD = ("univariate AR(1) x SPDE Matern, 32x32 grid mesh ns=1024, nt=64, nb=4 fixed effects, "
-            "m=65536 observations, N=65540; per step: the 2 dim(theta)+1 = 9 central-difference theta points, "
-            "each assemble+factor+log-det of Q_p and Q_c, conditional-mean solve, f_obj, selected inversion of Q_c")
+            "m=65536 observations, N=65540; per step: 9 theta points (2 dim(theta)+1 stencil), each "
+            "assemble+factor+log-det of Q_p and Q_c, conditional-mean solve, f_obj, selected inversion of "
+            "Q_p and Q_c, adjoint gradient")
 CONFIG_NAME = "c2"
 # FP64 peak of the GB300: the nominal FP64 rate (no FP64 figure is measured by
 # the driver); a DFMA throughput probe on this machine read 1.20 TFLOP/s at 1995 MHz.
@@ -157,13 +159,14 @@ def cpu_threads():
 
 
 def oracle_step(problem, theta, fd):
-    """One step of the workload on the CPU oracle (tier B): f_obj and selinv(Q_c)."""
+    """One theta point of the workload on the CPU oracle (tier B): f_obj and the
+    selected inversion of Q_p and Q_c (the inputs of the adjoint gradient)."""
     from oracle import bta as obta
     from oracle import fobj as ofobj
     terms = ofobj.f_obj_terms(problem, theta, tier="bta", fd=fd)
     built = terms["built"]
-    L = obta.factor(obta.blocks_from_sparse(built.Qc, problem.nt, problem.b, problem.a))
-    obta.selinv(L)
+    for Q in (built.Qp, built.Qc):
+        obta.selinv(obta.factor(obta.blocks_from_sparse(Q, problem.nt, problem.b, problem.a)))
     return terms["f"]
 
 
@@ -209,7 +212,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "name": args.config},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                         "sample": "one theta point (f_obj + selinv of Q_c) of each step's 9-point stencil, "
+                         "sample": "one theta point (f_obj + selinv of Q_p and Q_c) of each step's 9 points, "
                                    "numpy/scipy FP64 block recurrences"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -248,12 +251,12 @@ def run_ours(args):
                          for t in thetas_for(p, nsteps, rank)])          # steps x B x dim
     thetas_d = torch.tensor(thetas_h, dtype=torch.float64, device="cuda")
     f_d = torch.zeros((nsteps, B), dtype=torch.float64, device="cuda")
+    g_d = torch.zeros((nsteps, B, p.theta0.shape[0]), dtype=torch.float64, device="cuda")
     mu_d = torch.zeros((B, p.N), dtype=torch.float64, device="cuda")
     var_d = torch.zeros((B, p.N), dtype=torch.float64, device="cuda")
 
     def step(j, theta_dev, f_out):
-        ctx.fobj_eval(model, theta_dev, f_out, mu_d)
-        ctx.selinv_batch(bta.BTA_QC)
+        ctx.fobj_grad(model, theta_dev, f_out, g_d[j])
 
     def barrier_sync():
         torch.cuda.synchronize()
@@ -288,7 +291,7 @@ def run_ours(args):
         # ---- end-to-end through the C ABI with host buffers
         th_pin = torch.tensor(thetas_h, dtype=torch.float64).pin_memory()
         f_pin = torch.zeros((args.steps, B), dtype=torch.float64).pin_memory()
-        mu_pin = torch.zeros((B, p.N), dtype=torch.float64).pin_memory()
+        g_pin = torch.zeros((args.steps, B, p.theta0.shape[0]), dtype=torch.float64).pin_memory()
         var_pin = torch.zeros((B, p.N), dtype=torch.float64).pin_memory()
         theta_stage = torch.zeros((B, p.theta0.shape[0]), dtype=torch.float64, device="cuda")
         g0 = torch.cuda.Event(enable_timing=True)
@@ -296,12 +299,11 @@ def run_ours(args):
         g0.record(stream)
         for j in range(args.steps):
             theta_stage.copy_(th_pin[args.warmup + j], non_blocking=True)
-            ctx.fobj_eval(model, theta_stage, f_d[j], mu_d)
-            ctx.selinv_batch(bta.BTA_QC)
+            ctx.fobj_grad(model, theta_stage, f_d[j], g_d[j])
             for k in range(B):
                 ctx.selinv_diag(2 * k + bta.BTA_QC, var_d[k])
             f_pin[j].copy_(f_d[j], non_blocking=True)
-            mu_pin.copy_(mu_d, non_blocking=True)
+            g_pin[j].copy_(g_d[j], non_blocking=True)
             var_pin.copy_(var_d, non_blocking=True)
         g1.record(stream)
         g1.synchronize()
@@ -315,7 +317,7 @@ def run_ours(args):
     total_evals = args.steps * world * B
     value = total_evals / (ms / 1e3)
     e2e_value = total_evals / (ms_e2e / 1e3)
-    flops_eval = 2 * bta.bta_flops_factor(p.nt, p.b, p.a) + bta.bta_flops_selinv(p.nt, p.b, p.a)
+    flops_eval = 2 * bta.bta_flops_factor(p.nt, p.b, p.a) + 2 * bta.bta_flops_selinv(p.nt, p.b, p.a)
     tflops = flops_eval * total_evals / (ms / 1e3) / 1e12
 
     if rank != 0:
@@ -355,10 +357,10 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "name": args.config, "precision": args.precision, "theta_points": B,
                    "l2": "inputs larger than L2 (BTA blocks ~1.07 GB per matrix)",
                    "parallelism": f"replicas x{world} (independent theta points per GPU)"},
-        "tflops": tflops, "tflops_unit": "nominal (2 F_fact + F_selinv) per step / step time",
+        "tflops": tflops, "tflops_unit": "nominal (2 F_fact + 2 F_selinv) per f_obj evaluation / time",
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B * p.theta0.shape[0] * 8),
-                "d2h_bytes_per_step": int(B * (8 + 2 * p.N * 8))},
+                "d2h_bytes_per_step": int(B * (8 + p.theta0.shape[0] * 8 + p.N * 8))},
         "batch": B,
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
@@ -371,7 +373,7 @@ def run_ours(args):
         oracle_step(p, th, fd)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                                "sample": "one theta point of the stencil (f_obj + selinv of Q_c) on the FP64 "
+                                "sample": "one theta point (f_obj + selinv of Q_p and Q_c) on the FP64 "
                                           "numpy/scipy block recurrences"}
     print(json.dumps(line))
     if dist is not None:
