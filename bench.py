@@ -60,10 +60,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--config", default=CONFIG_NAME)
     ap.add_argument("--batch", type=int, default=0, help="theta points per step (default 2 dim(theta) + 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP64 comparison run of the mixed-precision bench")
     return ap.parse_args()
 
 
@@ -219,8 +221,133 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_ours(args):
+def _roofline(precision, prof_ms, prof_n, prof_flops):
+    """Roofline record of the dominant kernel from the profiling events of the
+    last timed step (the graph replays the same launches every step)."""
+    achieved = (prof_flops / (prof_ms / 1e3) / 1e12) if prof_ms > 0 else None
+    if precision == "fp64":
+        return {
+            "bound": "alu", "kernel": "gemm64_kernel (FP64 DFMA Schur-update GEMMs L_{i+1,i}=B_i L_ii^-T and "
+                                      "D_{i+1}-=L L^T, batched over the step's matrices)",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+            "traffic": traffic_record("gemm64_bxbxb"),
+            "launches_timed": prof_n, "flops_per_launch": (prof_flops / prof_n) if prof_n else None,
+            "peak_source": "nominal GB300 FP64 rate (no FP64 entry in the measured peaks)",
+        }
+    # executed bf16 tensor flops: 15 digit-pair products per FP64-equivalent flop
+    tensor = 15.0 * achieved if achieved else None
+    peak = BF16_PEAK_TFLOPS
+    return {
+        "bound": "tensor", "kernel": "ozaki_gemm (digit split + tcgen05 bf16 15-pair products) for the "
+                                    "Schur-update GEMMs, batched over the step's matrices",
+        "achieved": tensor, "peak": peak, "unit": "TFLOP/s", "frac": (tensor / peak) if tensor else None,
+        "achieved_fp64_equivalent": achieved,
+        "traffic": traffic_record("ozaki_bxbxb"),
+        "launches_timed": prof_n, "flops_per_launch": (prof_flops / prof_n) if prof_n else None,
+        "peak_source": "measured bf16 dense (burst) of this pool, of measured",
+    }
+
+
+def measure(args, precision_name, warmup, steps, with_e2e, dist, rank, world, local):
+    """Time `steps` batched f_obj+gradient+selinv steps of one precision after
+    `warmup` untimed ones; returns the measurements of this rank."""
     import numpy as np
+    import torch
+    from paper_2507_06938_gb300 import bta
+    import synth
+
+    p = synth.problem_from_config(args.config)
+    precision = bta.BTA_FP64 if precision_name == "fp64" else bta.BTA_MIXED
+    B = args.batch or (2 * p.theta0.shape[0] + 1)
+    stream = torch.cuda.Stream()
+    model = bta.BtaModel(p)
+    ctx = bta.BtaContext(p.nt, p.b, p.a, precision, stream, B)
+    nsteps = warmup + steps
+    thetas_h = np.stack([t[:B] if t.shape[0] >= B else np.resize(t, (B, t.shape[1]))
+                         for t in thetas_for(p, nsteps, rank)])          # steps x B x dim
+    thetas_d = torch.tensor(thetas_h, dtype=torch.float64, device="cuda")
+    f_d = torch.zeros((nsteps, B), dtype=torch.float64, device="cuda")
+    g_d = torch.zeros((nsteps, B, p.theta0.shape[0]), dtype=torch.float64, device="cuda")
+    var_d = torch.zeros((B, p.N), dtype=torch.float64, device="cuda")
+
+    def step(j, theta_dev, f_out):
+        ctx.fobj_grad(model, theta_dev, f_out, g_d[j])
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    out = {"problem": p, "B": B, "thetas_h": thetas_h}
+    with torch.cuda.stream(stream):
+        # the dominant GEMM launches carry timing events; the f_obj graph that
+        # the timed steps replay is captured with them during the warm-up
+        ctx.profile(True)
+        for j in range(warmup):
+            step(j, thetas_d[j], f_d[j])
+        ctx.sync()
+        barrier_sync()
+        # ---- device-resident timed region
+        launches0 = bta.bta_launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            for j in range(steps):
+                step(warmup + j, thetas_d[warmup + j], f_d[warmup + j])
+            e1.record(stream)
+            e1.synchronize()
+        ctx.sync()
+        out["launches"] = bta.bta_launch_count() - launches0
+        out["prof"] = ctx.profile_read()
+        ctx.profile(False)
+        out["ms"] = e0.elapsed_time(e1)
+        out["clocks"] = clk.summary()
+        barrier_sync()
+        out["ms_e2e"] = None
+        if with_e2e:
+            # ---- end-to-end through the C ABI with host buffers
+            th_pin = torch.tensor(thetas_h, dtype=torch.float64).pin_memory()
+            f_pin = torch.zeros((steps, B), dtype=torch.float64).pin_memory()
+            g_pin = torch.zeros((steps, B, p.theta0.shape[0]), dtype=torch.float64).pin_memory()
+            var_pin = torch.zeros((B, p.N), dtype=torch.float64).pin_memory()
+            theta_stage = torch.zeros((B, p.theta0.shape[0]), dtype=torch.float64, device="cuda")
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for j in range(steps):
+                theta_stage.copy_(th_pin[warmup + j], non_blocking=True)
+                ctx.fobj_grad(model, theta_stage, f_d[j], g_d[j])
+                for k in range(B):
+                    ctx.selinv_diag(2 * k + bta.BTA_QC, var_d[k])
+                f_pin[j].copy_(f_d[j], non_blocking=True)
+                g_pin[j].copy_(g_d[j], non_blocking=True)
+                var_pin.copy_(var_d, non_blocking=True)
+            g1.record(stream)
+            g1.synchronize()
+            ctx.sync()
+            out["ms_e2e"] = g0.elapsed_time(g1)
+    ctx.close()
+    model.close()
+    del thetas_d, f_d, g_d, var_d
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    t_local = torch.tensor([out["ms"], out["ms_e2e"] or 0.0], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    out["ms"], out["ms_e2e"] = float(t_local[0]), float(t_local[1])
+    total_evals = steps * world * B
+    out["value"] = total_evals / (out["ms"] / 1e3)
+    out["e2e_value"] = total_evals / (out["ms_e2e"] / 1e3) if with_e2e else None
+    flops_eval = 2 * bta.bta_flops_factor(p.nt, p.b, p.a) + 2 * bta.bta_flops_selinv(p.nt, p.b, p.a)
+    out["tflops"] = flops_eval * total_evals / (out["ms"] / 1e3) / 1e12
+    out["roofline"] = _roofline(precision_name, *out["prof"])
+    return out
+
+
+def run_ours(args):
     import torch
 
     rank, world, local = dist_env()
@@ -237,138 +364,43 @@ def run_ours(args):
         _build.build()
     if dist is not None:
         dist.barrier()
-    from paper_2507_06938_gb300 import bta
-    import synth
 
-    p = synth.problem_from_config(args.config)
-    precision = bta.BTA_FP64 if args.precision == "fp64" else bta.BTA_MIXED
-    B = args.batch or (2 * p.theta0.shape[0] + 1)
-    stream = torch.cuda.Stream()
-    model = bta.BtaModel(p)
-    ctx = bta.BtaContext(p.nt, p.b, p.a, precision, stream, B)
-    nsteps = args.warmup + args.steps
-    thetas_h = np.stack([t[:B] if t.shape[0] >= B else np.resize(t, (B, t.shape[1]))
-                         for t in thetas_for(p, nsteps, rank)])          # steps x B x dim
-    thetas_d = torch.tensor(thetas_h, dtype=torch.float64, device="cuda")
-    f_d = torch.zeros((nsteps, B), dtype=torch.float64, device="cuda")
-    g_d = torch.zeros((nsteps, B, p.theta0.shape[0]), dtype=torch.float64, device="cuda")
-    mu_d = torch.zeros((B, p.N), dtype=torch.float64, device="cuda")
-    var_d = torch.zeros((B, p.N), dtype=torch.float64, device="cuda")
-
-    def step(j, theta_dev, f_out):
-        ctx.fobj_grad(model, theta_dev, f_out, g_d[j])
-
-    def barrier_sync():
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    with torch.cuda.stream(stream):
-        # the dominant GEMM launches carry timing events; the f_obj graph that
-        # the timed steps replay is captured with them during the warm-up
-        ctx.profile(True)
-        for j in range(args.warmup):
-            step(j, thetas_d[j], f_d[j])
-        ctx.sync()
-        barrier_sync()
-        # ---- device-resident timed region
-        launches0 = bta.bta_launch_count()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as clk:
-            e0.record(stream)
-            for j in range(args.steps):
-                step(args.warmup + j, thetas_d[args.warmup + j], f_d[args.warmup + j])
-            e1.record(stream)
-            e1.synchronize()
-        ctx.sync()
-        launches = bta.bta_launch_count() - launches0
-        prof_ms, prof_n, prof_flops = ctx.profile_read()
-        ctx.profile(False)
-        ms = e0.elapsed_time(e1)
-        barrier_sync()
-        # ---- end-to-end through the C ABI with host buffers
-        th_pin = torch.tensor(thetas_h, dtype=torch.float64).pin_memory()
-        f_pin = torch.zeros((args.steps, B), dtype=torch.float64).pin_memory()
-        g_pin = torch.zeros((args.steps, B, p.theta0.shape[0]), dtype=torch.float64).pin_memory()
-        var_pin = torch.zeros((B, p.N), dtype=torch.float64).pin_memory()
-        theta_stage = torch.zeros((B, p.theta0.shape[0]), dtype=torch.float64, device="cuda")
-        g0 = torch.cuda.Event(enable_timing=True)
-        g1 = torch.cuda.Event(enable_timing=True)
-        g0.record(stream)
-        for j in range(args.steps):
-            theta_stage.copy_(th_pin[args.warmup + j], non_blocking=True)
-            ctx.fobj_grad(model, theta_stage, f_d[j], g_d[j])
-            for k in range(B):
-                ctx.selinv_diag(2 * k + bta.BTA_QC, var_d[k])
-            f_pin[j].copy_(f_d[j], non_blocking=True)
-            g_pin[j].copy_(g_d[j], non_blocking=True)
-            var_pin.copy_(var_d, non_blocking=True)
-        g1.record(stream)
-        g1.synchronize()
-        ctx.sync()
-        ms_e2e = g0.elapsed_time(g1)
-
-    t_local = torch.tensor([ms, ms_e2e], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms, ms_e2e = float(t_local[0]), float(t_local[1])
-    total_evals = args.steps * world * B
-    value = total_evals / (ms / 1e3)
-    e2e_value = total_evals / (ms_e2e / 1e3)
-    flops_eval = 2 * bta.bta_flops_factor(p.nt, p.b, p.a) + 2 * bta.bta_flops_selinv(p.nt, p.b, p.a)
-    tflops = flops_eval * total_evals / (ms / 1e3) / 1e12
+    r = measure(args, args.precision, args.warmup, args.steps, True, dist, rank, world, local)
+    cmp = None
+    if args.precision == "mixed" and not args.no_compare:
+        # the FP64 path on the same workload, shorter (one FP64 step takes seconds)
+        cmp = measure(args, "fp64", 1, 1, False, dist, rank, world, local)
+    p, B = r["problem"], r["B"]
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    # events of the last timed step (the graph replays the same launches every step)
-    achieved = (prof_flops / (prof_ms / 1e3) / 1e12) if prof_ms > 0 else None
-    if args.precision == "fp64":
-        roof = {
-            "bound": "alu", "kernel": "gemm64_kernel (FP64 DFMA Schur-update GEMMs L_{i+1,i}=B_i L_ii^-T and "
-                                      "D_{i+1}-=L L^T, batched over the step's matrices)",
-            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-            "traffic": traffic_record("gemm64_bxbxb"),
-            "launches_timed": prof_n, "flops_per_launch": (prof_flops / prof_n) if prof_n else None,
-            "peak_source": "nominal GB300 FP64 rate (no FP64 entry in the measured peaks)",
-        }
-    else:
-        # executed bf16 tensor flops: 15 digit-pair products per FP64-equivalent flop
-        tensor = 15.0 * achieved if achieved else None
-        peak = BF16_PEAK_TFLOPS
-        roof = {
-            "bound": "tensor", "kernel": "ozaki_gemm (digit split + tcgen05 bf16 15-pair products) for the "
-                                        "Schur-update GEMMs, batched over the step's matrices",
-            "achieved": tensor, "peak": peak, "unit": "TFLOP/s", "frac": (tensor / peak) if tensor else None,
-            "achieved_fp64_equivalent": achieved,
-            "traffic": traffic_record("ozaki_bxbxb"),
-            "launches_timed": prof_n, "flops_per_launch": (prof_flops / prof_n) if prof_n else None,
-            "peak_source": "measured bf16 dense (burst) of this pool, of measured",
-        }
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "mixed",
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "mixed (f64 with bf16-digit tensor-core products)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "name": args.config, "precision": args.precision, "theta_points": B,
                    "l2": "inputs larger than L2 (BTA blocks ~1.07 GB per matrix)",
                    "parallelism": f"replicas x{world} (independent theta points per GPU)"},
-        "tflops": tflops, "tflops_unit": "nominal (2 F_fact + 2 F_selinv) per f_obj evaluation / time",
-        "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B * p.theta0.shape[0] * 8),
+        "tflops": r["tflops"], "tflops_unit": "nominal (2 F_fact + 2 F_selinv) per f_obj evaluation / time",
+        "roofline": r["roofline"],
+        "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": int(B * p.theta0.shape[0] * 8),
                 "d2h_bytes_per_step": int(B * (8 + p.theta0.shape[0] * 8 + p.N * 8))},
         "batch": B,
-        "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "gpu_launches": int(r["launches"]),
+        "clocks": r["clocks"],
     }
+    if cmp is not None:
+        line["fp64"] = {"value": cmp["value"], "unit": UNIT, "ms_per_step": cmp["ms"], "steps": 1, "warmup": 1,
+                        "tflops": cmp["tflops"], "roofline": cmp["roofline"], "gpu_launches": int(cmp["launches"]),
+                        "clocks": cmp["clocks"], "mixed_over_fp64": r["value"] / cmp["value"]}
     if world == 1 and not args.no_cpu_baseline:
         from oracle import model as omodel
         fd = omodel.fem_data(p)
-        th = thetas_h[args.warmup][0]
+        th = r["thetas_h"][args.warmup][0]
         t0 = time.perf_counter()
         oracle_step(p, th, fd)
         dt = time.perf_counter() - t0

@@ -182,10 +182,13 @@ class BtaModel:
         self.n, self.b, self.a, self.dim_theta = n.value, b.value, a.value, dt.value
         self.N = self.n * self.b + self.a
 
-    def __del__(self):
+    def close(self):
+        """Release the device copy of the model now (also done on collection)."""
         if getattr(self, "handle", None) and _lib is not None:
             _lib.bta_model_destroy(self.handle)
             self.handle = None
+
+    __del__ = close
 
 
 # ----------------------------------------------------------------------------- context
@@ -204,10 +207,13 @@ class BtaContext:
         self.n, self.b, self.a, self.batch = n, b, a, batch
         self.N = n * b + a
 
-    def __del__(self):
+    def close(self):
+        """Release the context's device storage now (also done on collection)."""
         if getattr(self, "handle", None) and _lib is not None:
             _lib.bta_destroy(self.handle)
             self.handle = None
+
+    __del__ = close
 
     # -- the C ABI, one method per entry point
     def assemble(self, model: BtaModel, params, which: int):

@@ -35,11 +35,11 @@ __device__ __forceinline__ double load_opB(const Gemm64& p, const double* B, int
     return p.tb ? B[nn + (long long)k * p.ldb] : B[k + (long long)nn * p.ldb];
 }
 
-template <int MI, int NJ>
+template <int MI, int NJ, int BKT = BK>
 __global__ void __launch_bounds__(GT) gemm64_kernel(Gemm64 p, int ksplit) {
     constexpr int TBM = 16 * MI, TBN = 16 * NJ;
-    __shared__ double As[BK][TBM + 1];
-    __shared__ double Bs[BK][TBN + 1];
+    __shared__ double As[BKT][TBM + 1];
+    __shared__ double Bs[BKT][TBN + 1];
     const int m0 = blockIdx.x * TBM, n0 = blockIdx.y * TBN;
     if (p.lowerC && m0 + TBM - 1 < n0) return;
     const int z = blockIdx.z / ksplit, split = blockIdx.z % ksplit;
@@ -52,13 +52,13 @@ __global__ void __launch_bounds__(GT) gemm64_kernel(Gemm64 p, int ksplit) {
     if (p.shA == 2) kb = max(kb, m0);
     if (p.shB == 1) kb = max(kb, n0);
     if (p.shB == 2) ke = min(ke, n0 + TBN);
-    kb = (kb / BK) * BK;
+    kb = (kb / BKT) * BKT;
     if (ksplit > 1) {
-        // split [kb, ke) into ksplit chunks of whole BK tiles
-        const int tiles = (ke - kb + BK - 1) / BK;
+        // split [kb, ke) into ksplit chunks of whole BKT tiles
+        const int tiles = (ke - kb + BKT - 1) / BKT;
         const int per = (tiles + ksplit - 1) / ksplit;
-        const int s0 = kb + split * per * BK;
-        const int s1 = min(ke, s0 + per * BK);
+        const int s0 = kb + split * per * BKT;
+        const int s1 = min(ke, s0 + per * BKT);
         kb = s0;
         ke = s1;
         if (kb >= ke) return;
@@ -70,21 +70,21 @@ __global__ void __launch_bounds__(GT) gemm64_kernel(Gemm64 p, int ksplit) {
 #pragma unroll
         for (int j = 0; j < NJ; ++j) acc[i][j] = 0.0;
 
-    for (int k0 = kb; k0 < ke; k0 += BK) {
-        // op(A) tile TBM x BK: lanes along the contiguous stored dimension
-        for (int e = tid; e < TBM * BK; e += GT) {
+    for (int k0 = kb; k0 < ke; k0 += BKT) {
+        // op(A) tile TBM x BKT: lanes along the contiguous stored dimension
+        for (int e = tid; e < TBM * BKT; e += GT) {
             int mm, kk;
-            if (!p.ta) { mm = e % TBM; kk = e / TBM; } else { kk = e % BK; mm = e / BK; }
+            if (!p.ta) { mm = e % TBM; kk = e / TBM; } else { kk = e % BKT; mm = e / BKT; }
             As[kk][mm] = load_opA(p, A, m0 + mm, k0 + kk, ke);
         }
-        for (int e = tid; e < TBN * BK; e += GT) {
+        for (int e = tid; e < TBN * BKT; e += GT) {
             int nn, kk;
-            if (!p.tb) { kk = e % BK; nn = e / BK; } else { nn = e % TBN; kk = e / TBN; }
+            if (!p.tb) { kk = e % BKT; nn = e / BKT; } else { nn = e % TBN; kk = e / TBN; }
             Bs[kk][nn] = load_opB(p, B, k0 + kk, n0 + nn, ke);
         }
         __syncthreads();
 #pragma unroll
-        for (int kk = 0; kk < BK; ++kk) {
+        for (int kk = 0; kk < BKT; ++kk) {
             double a[MI], b[NJ];
 #pragma unroll
             for (int i = 0; i < MI; ++i) a[i] = As[kk][tx + 16 * i];
@@ -114,6 +114,87 @@ __global__ void __launch_bounds__(GT) gemm64_kernel(Gemm64 p, int ksplit) {
                 if (p.beta != 0.0) v += p.beta * Cin[mm + (long long)nn * p.ldci];
                 *c = v;
             }
+        }
+    }
+}
+
+// Thin GEMM for op(A) with at most 16 rows (the arrow products
+// L_{t,i} = R X^T, R -= L_t L_B^T, F = L_t X, Sigma_t G of a BTA matrix with a
+// narrow arrowhead).  A 16-row tile of the kernel above would spend 3/4 of
+// its DFMAs on padding rows when M = 4.  Here a CTA owns 64 columns; warp w
+// works on columns n0 + 32 (w & 1) + lane and rows R g .. R g + R - 1 of row
+// group g = w / 2, so a row group beyond M is a whole idle warp and every
+// DFMA issued is a useful one.  The op(A) chunk is read from shared memory as
+// a broadcast, the op(B) chunk is staged coalesced for either stride order.
+constexpr int TH_TN = 64, TH_BK = 32;
+
+template <int R>
+__global__ void __launch_bounds__(GT) gemm64_thin_kernel(Gemm64 p, int ksplit) {
+    constexpr int TM = 4 * R;
+    __shared__ double As[TH_BK][TM];
+    __shared__ double Bs[TH_BK][TH_TN + 1];
+    const int n0 = blockIdx.x * TH_TN;
+    const int z = blockIdx.y / ksplit, split = blockIdx.y % ksplit;
+    const double* A = p.A + z * p.sA;
+    const double* B = p.B + z * p.sB;
+    const double* Cin = p.Cin ? p.Cin + z * p.sCi : nullptr;
+    double* C = p.C + z * p.sC;
+    int kb = 0, ke = p.K;
+    if (p.shA == 1) ke = min(ke, p.M);
+    if (p.shB == 1) kb = max(kb, n0);
+    if (p.shB == 2) ke = min(ke, n0 + TH_TN);
+    kb = (kb / TH_BK) * TH_BK;
+    if (ksplit > 1) {
+        const int tiles = (ke - kb + TH_BK - 1) / TH_BK;
+        const int per = (tiles + ksplit - 1) / ksplit;
+        const int s0 = kb + split * per * TH_BK;
+        const int s1 = min(ke, s0 + per * TH_BK);
+        kb = s0;
+        ke = s1;
+        if (kb >= ke) return;
+    }
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = warp >> 1, col = (warp & 1) * 32 + lane;
+    const bool active = grp * R < p.M;        // warp-uniform
+    double acc[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) acc[i] = 0.0;
+    for (int k0 = kb; k0 < ke; k0 += TH_BK) {
+        for (int e = tid; e < TM * TH_BK; e += GT) {
+            int mm, kk;
+            if (!p.ta) { mm = e % TM; kk = e / TM; } else { kk = e % TH_BK; mm = e / TH_BK; }
+            As[kk][mm] = load_opA(p, A, mm, k0 + kk, ke);
+        }
+        for (int e = tid; e < TH_TN * TH_BK; e += GT) {
+            int nn, kk;
+            if (!p.tb) { kk = e % TH_BK; nn = e / TH_BK; } else { nn = e % TH_TN; kk = e / TH_TN; }
+            Bs[kk][nn] = load_opB(p, B, k0 + kk, n0 + nn, ke);
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll 8
+            for (int kk = 0; kk < TH_BK; ++kk) {
+                const double bv = Bs[kk][col];
+#pragma unroll
+                for (int i = 0; i < R; ++i) acc[i] = fma(As[kk][grp * R + i], bv, acc[i]);
+            }
+        }
+        __syncthreads();
+    }
+    const int nn = n0 + col;
+    if (!active || nn >= p.N) return;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int mm = grp * R + i;
+        if (mm >= p.M) continue;
+        if (p.lowerC && mm < nn) continue;
+        double* c = C + mm + (long long)nn * p.ldc;
+        if (ksplit > 1) {
+            atomicAdd(c, p.alpha * acc[i]);
+        } else {
+            double v = p.alpha * acc[i];
+            if (p.beta != 0.0) v += p.beta * Cin[mm + (long long)nn * p.ldci];
+            *c = v;
         }
     }
 }
@@ -370,8 +451,41 @@ __global__ void dot_finish_kernel(const double* partial, int chunks, double* out
 }  // namespace
 
 // ==================================================================== host launchers
+static int gemm64_thin(cudaStream_t s, const Gemm64& g) {
+    const int gn = (g.N + TH_TN - 1) / TH_TN;
+    const long long ctas = (long long)gn * g.batch;
+    const int kchunks = std::max(1, (g.K + TH_BK - 1) / TH_BK);
+    // about four CTAs per SM; each split keeps at least two K chunks
+    const long long want = 4LL * 152;
+    int ksplit = (int)std::min<long long>(std::max(1, kchunks / 2), std::max<long long>(1, (want + ctas - 1) / ctas));
+    if ((long long)g.batch * ksplit > 65535) ksplit = std::max(1, 65535 / g.batch);
+    if (ksplit > 1) {
+        const bool inplace = (g.Cin == g.C && g.ldci == g.ldc && g.beta == 1.0 && g.sCi == g.sC);
+        if (!inplace) BTA_TRY(scale_into64(s, g.M, g.N, g.Cin, g.ldci, g.beta, g.C, g.ldc, g.lowerC, g.batch, g.sCi, g.sC));
+    }
+    dim3 grid(gn, g.batch * ksplit);
+    const int R = (g.M + 3) / 4;
+    if (R == 1) gemm64_thin_kernel<1><<<grid, GT, 0, s>>>(g, ksplit);
+    else if (R == 2) gemm64_thin_kernel<2><<<grid, GT, 0, s>>>(g, ksplit);
+    else if (R == 3) gemm64_thin_kernel<3><<<grid, GT, 0, s>>>(g, ksplit);
+    else gemm64_thin_kernel<4><<<grid, GT, 0, s>>>(g, ksplit);
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}
+
 int gemm64(cudaStream_t s, const Gemm64& g) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return BTA_OK;
+    if (g.M <= 16 && g.N >= TH_TN) return gemm64_thin(s, g);
+    if (g.K <= 8 && g.M > 32 && g.N > 32) {
+        // rank-a updates of b x b blocks (Sigma -= Sigma_t^T F): one K tile of
+        // the 64 x 64 kernel sized to K, no padding DFMAs, no split
+        const int gm = (g.M + 63) / 64, gn = (g.N + 63) / 64;
+        dim3 grid(gm, gn, g.batch);
+        if (g.K <= 4) gemm64_kernel<4, 4, 4><<<grid, GT, 0, s>>>(g, 1);
+        else gemm64_kernel<4, 4, 8><<<grid, GT, 0, s>>>(g, 1);
+        BTA_LAUNCH_CHECK();
+        return BTA_OK;
+    }
     // The FP64 pipe of one SM is slow (2 DFMA per clock), so every product is
     // spread over about two CTAs per SM: pick the largest micro-tile that
     // still reaches that with a K split of whole 16-wide slices, else the

@@ -17,7 +17,7 @@
 //
 // Kernel structure (one 128 x 128 output tile per CTA, 320 threads):
 //   warp 0      TMA producer: digit tiles 128 x 64 (128-byte swizzle) of A and
-//               B into a 4-stage shared-memory ring
+//               B into a 6-stage shared-memory ring
 //   warp 1      allocates 256 TMEM columns (two 128-column FP32 accumulators)
 //               and issues tcgen05.mma (M = 128, N = 128, K = 16) from one thread
 //   warps 2..9  drain each finished accumulator (tcgen05.ld) into double-float
@@ -566,11 +566,13 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     return BTA_OK;
 }
 
-// GEMM executor of the mixed path: products whose three dimensions are all at
-// least min_dim go to the tensor cores, the rest (arrow, tip, small panels of
-// the recursive diagonal factorisation) stay on the FP64 pipe.
+// GEMM executor of the mixed path: products whose output is at least
+// min_dim x min_dim go to the tensor cores (a short K, as in the rank-a
+// updates of the selected inversion, is padded to one 64-wide K block), the
+// rest (arrow, tip, small panels of the recursive diagonal factorisation)
+// stay on the FP64 pipe.
 int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
-    if (g.M >= ex->min_dim && g.N >= ex->min_dim && g.K >= ex->min_dim &&
+    if (g.M >= ex->min_dim && g.N >= ex->min_dim && g.K >= 1 &&
         (size_t)g.batch * ozaki_workspace_bytes(g.M, g.N, g.K) <= ex->ws_bytes)
         return ozaki_gemm(s, g, ex->ws, ex->err);
     return gemm64(s, g);

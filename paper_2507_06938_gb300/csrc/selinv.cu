@@ -9,9 +9,9 @@
 //   Sigma_{i+1,i} = -Sigma_{i+1,i+1} G_i - Sigma_{t,i+1}^T F_i
 //   Sigma_{t,i}   = -Sigma_{t,i+1} G_i - Sigma_tt F_i
 //   Sigma_ii      = L_ii^{-T} L_ii^{-1} - Sigma_{i+1,i}^T G_i - Sigma_{t,i}^T F_i
-// for i = n-1 down to 0 (terms with index n are absent).  The b x b products
-// go through the context's GEMM executor (tensor cores in mixed precision);
-// the arrow and tip products stay FP64.  Sigma_ii is computed on its lower
+// for i = n-1 down to 0 (terms with index n are absent).  The products with a
+// b x b output go through the context's GEMM executor (tensor cores in mixed
+// precision); the arrow and tip products stay FP64.  Sigma_ii is computed on its lower
 // triangle and then mirrored.
 
 #include <algorithm>
@@ -85,7 +85,7 @@ int selinv_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
                 g.Cin = SBi; g.ldci = b; g.beta = 1.0;
                 g.C = SBi; g.ldc = b; g.alpha = -1.0;
                 g.batch = cnt; g.sA = S.sR; g.sB = sW; g.sCi = S.sB; g.sC = S.sB;
-                BTA_TRY(gemm64(s, g));
+                BTA_TRY(gemm_exec(ex, s, g));
                 // Sigma_{t,i} = -Sigma_{t,i+1} G - Sigma_tt F
                 g = Gemm64{};
                 g.M = a; g.N = b; g.K = b;
@@ -139,7 +139,7 @@ int selinv_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
             g.Cin = SDi; g.ldci = b; g.beta = 1.0;
             g.C = SDi; g.ldc = b; g.alpha = -1.0; g.lowerC = 1;
             g.batch = cnt; g.sA = S.sR; g.sB = sW; g.sCi = S.sD; g.sC = S.sD;
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm_exec(ex, s, g));
         }
         BTA_TRY(symmetrize_lower64(s, SDi, b, b, cnt, S.sD));
     }
