@@ -1,31 +1,40 @@
 // Split-precision FP64 GEMM on the tcgen05 tensor cores (mixed path of the
-// BTA Schur updates).
+// BTA Schur updates and selected inversion).
 //
 // C += alpha * op(A) op(B) with FP64 A, B, C.  Every row i of op(A) is written
-// as 2^{e_i} sum_{p<S} d_p 2^{-7(p+1)} with integer digits |d_p| <= 128 (S = 5
-// slices, 35 bits below the row's largest binary exponent, rounded), and every
-// column j of op(B) the same way with exponent f_j.  A digit is exact in bf16, a digit product is below
-// 2^14, so a sum of up to 1024 products is an integer below 2^24: the FP32
-// accumulator of tcgen05.mma kind::f16 holds it exactly.  The product is
-//   (op(A) op(B))_ij ~ 2^{e_i + f_j - 14} sum_{p+q<S} 2^{-7(p+q)} acc_pq(i,j)
-// (pairs with p + q >= S fall below the digits' own precision).  Each pair's
-// exact FP32 accumulator is drained from tensor memory and summed in
-// double-float (two FP32 words, error-free TwoSum) on the CUDA cores; FP64 is
-// used once per output element.  The FP64 pipe of GB300 delivers ~1.2
-// TFLOP/s, the bf16 tensor pipe ~1.9 PFLOP/s: 15 bf16 products per FP64
-// product still leave a large margin.
+// as 2^{e_i} sum_{p<S} d_p 2^{-7(p+1)} with integer digits (S = 5 slices,
+// 35 bits below the row's largest binary exponent, rounded; |d_0| <= 128,
+// |d_p| <= 64 for p >= 1), every column j of op(B) the same way with
+// exponent f_j.  A digit is exact in bf16.  Grouping the digit products by
+// level s = p + q,
+//   (op(A) op(B))_ij ~ 2^{e_i + f_j - 14} sum_{s<S} 2^{-7s} L_s(i,j),
+//   L_s = sum_k sum_{p+q=s} d_p(i,k) d_q(k,j)
+// (levels s >= S fall below the digits' own precision).  Per k a level sum
+// is an integer of magnitude below 2^15 (at most 2^14 for s = 0), so over a
+// chunk of 512 values of k it stays below 2^24: the FP32 accumulator of
+// tcgen05.mma kind::f16 holds every partial sum exactly.  Each level has its
+// own accumulator in tensor memory; after every chunk the five accumulators
+// are drained (tcgen05.ld), scaled by 2^{-7s} and summed in double-float (two
+// FP32 words, error-free TwoSum) on the CUDA cores.  The result goes into C
+// with one FP64 addition per element; the power-of-two scaling and the
+// FP32 -> FP64 widening are done on the bit patterns, because the FP64 pipe
+// of GB300 (~1.2 TFLOP/s) is the scarce unit and the bf16 tensor pipe
+// (~1.9 PFLOP/s) the plentiful one.
 //
-// Kernel structure (one 128 x 128 output tile per CTA, 320 threads):
-//   warp 0      TMA producer: digit tiles 128 x 64 (128-byte swizzle) of A and
-//               B into a 6-stage shared-memory ring
-//   warp 1      allocates 256 TMEM columns (two 128-column FP32 accumulators)
-//               and issues tcgen05.mma (M = 128, N = 128, K = 16) from one thread
-//   warps 2..9  drain each finished accumulator (tcgen05.ld) into double-float
-//               registers, then write alpha * result into C
-// grid.z splits the 15 pairs into groups (more CTAs for small outputs); the
-// groups add into C atomically.  Every wait on an mbarrier is bounded in
-// time; on expiry the kernel records an error, stops issuing, drains what it
-// issued and frees its tensor memory.
+// Kernel (persistent, one CTA of 320 threads per SM, 128 x 96 output tiles):
+//   warp 0      TMA producer: for every 32-wide K block all five digit slices
+//               of the A tile (128 x 32) and of the B tile (96 x 32), 64-byte
+//               swizzle, into a 3-stage shared-memory ring (70 KB a stage), so
+//               that each digit is read from L2 once per tile
+//   warp 1      allocates 512 TMEM columns (five 96-column accumulators) and
+//               issues tcgen05.mma (M = 128, N = 96, K = 16) for the 15 digit
+//               pairs of each K block from one thread
+//   warps 2..9  drain the level accumulators after each chunk, then update C
+//               while the next tile's products run
+// Work units are (matrix, tile, K part); a K split (atomic adds into C) only
+// appears when the tiles alone cannot fill the GPU.  Every wait on an
+// mbarrier is bounded in time; on expiry the kernel records an error, stops
+// issuing, drains what it issued and frees its tensor memory.
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -38,37 +47,80 @@
 
 namespace oz {
 
-constexpr int S = 5;
-constexpr int NPAIRS = S * (S + 1) / 2;
-constexpr int TM = 128, TN = 128, TK = 64;
-constexpr int STAGES = 6;
-constexpr int KB_PER_CHUNK = 1024 / TK;   // exactness bound of one FP32 accumulation
+constexpr int S = 5;                      // digit slices = accumulated levels
+constexpr int TM = 128, TN = 96, TK = 32; // output tile; K block (64-byte rows)
+constexpr int STAGES = 3;
+constexpr int KB_PER_CHUNK = 512 / TK;    // exactness bound of one FP32 level accumulation
 constexpr int THREADS = 320;
-constexpr uint32_t TMEM_COLS = 256;
-constexpr uint32_t STAGE_BYTES = (TM + TN) * TK * 2;
+constexpr uint32_t TMEM_COLS = 512;       // S * TN = 480 used
+constexpr uint32_t A_SLICE_BYTES = TM * TK * 2;                       // 8 KB
+constexpr uint32_t B_SLICE_BYTES = TN * TK * 2;                       // 6 KB
+constexpr uint32_t STAGE_BYTES = S * (A_SLICE_BYTES + B_SLICE_BYTES); // 70 KB
 constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + STAGES * STAGE_BYTES + 256;
 constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;   // about 2 s
+constexpr int PAD_M = TM, PAD_N = TN, PAD_K = 64;        // digit array padding (PAD_K: split tile)
+constexpr int MAX_MT = 128;               // row tiles per matrix (M <= 16384)
 
-__constant__ int c_pair_p[NPAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4};
-__constant__ int c_pair_q[NPAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0};
+static_assert(SMEM_BYTES <= 232448, "shared memory of one CTA");
+static_assert(S * TN <= (int)TMEM_COLS, "level accumulators must fit in tensor memory");
 
 struct Args {
     int M, N;            // output extent
-    int groups;          // pair groups per matrix (blockIdx.z = matrix * groups + group)
     long long sC;        // matrix stride of C
-    int Mp, Np;          // padded rows per digit slice (multiples of 128)
-    int kblocks;         // padded K / 64
-    const int* expA;     // Mp exponents of the rows of op(A)
-    const int* expB;     // Np exponents of the columns of op(B)
+    int Mp, Np;          // padded rows per digit slice
+    int kblocks;         // padded K / TK
+    int gm, gn;          // row and column tiles per matrix
+    int tiles;           // tiles per matrix (lower-output tiles only when lowerC)
+    int ksplit;          // K parts per tile (atomic adds into C when > 1)
+    int units;           // matrices * tiles * ksplit
+    const int* expA;     // Mp exponents of the rows of op(A), per matrix
+    const int* expB;     // Np exponents of the columns of op(B), per matrix
     double* C;
     long long ldc;
     double alpha;
-    int pairs_per_group;
-    int atomic;          // several pair groups add into C
     int lowerC;          // only entries m >= n (tiles strictly above skipped)
     int shA, shB;        // triangular shapes of op(A), op(B): K blocks outside them are zero, skipped
     int* err;            // set to 1 on a wait time-out
+    int mcum[MAX_MT + 1];// lowerC: tiles of row tiles 0..m-1
 };
+
+struct Unit {
+    int inst, m0, n0;
+    int kbl;             // first K block of the tile
+    int c0, c1;          // chunk range [c0, c1) of this unit (chunks of KB_PER_CHUNK blocks from kbl)
+    int kbh;             // end of the tile's K blocks
+};
+
+// Decode work unit u; returns false when the unit has no K blocks.
+__device__ __forceinline__ bool decode_unit(const Args& a, int u, Unit& w) {
+    const int kpart = u % a.ksplit;
+    u /= a.ksplit;
+    const int tile = u % a.tiles;
+    w.inst = u / a.tiles;
+    int mt, nt;
+    if (a.lowerC) {
+        mt = 0;
+        while (mt + 1 < a.gm && a.mcum[mt + 1] <= tile) ++mt;
+        nt = tile - a.mcum[mt];
+    } else {
+        mt = tile / a.gn;
+        nt = tile % a.gn;
+    }
+    w.m0 = mt * TM;
+    w.n0 = nt * TN;
+    int kbl = 0, kbh = a.kblocks;
+    if (a.shA == 1) kbh = min(kbh, (w.m0 + TM + TK - 1) / TK);   // op(A) lower: k <= m
+    if (a.shA == 2) kbl = max(kbl, w.m0 / TK);                    // op(A) upper: k >= m
+    if (a.shB == 1) kbl = max(kbl, w.n0 / TK);                    // op(B) lower: k >= n
+    if (a.shB == 2) kbh = min(kbh, (w.n0 + TN + TK - 1) / TK);    // op(B) upper: k <= n
+    w.kbl = kbl;
+    w.kbh = kbh;
+    const int nch = max(0, (kbh - kbl + KB_PER_CHUNK - 1) / KB_PER_CHUNK);
+    const int per = (nch + a.ksplit - 1) / a.ksplit;
+    w.c0 = min(nch, kpart * per);
+    w.c1 = min(nch, w.c0 + per);
+    return w.c1 > w.c0;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -123,19 +175,20 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major tile whose 8-row groups of
-// 128-byte rows (64 bf16) are 1024 bytes apart, 128-byte swizzle.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+// Shared-memory matrix descriptor: K-major tile whose rows are 64 bytes
+// (32 bf16) long, 8-row groups 512 bytes apart, 64-byte swizzle (the layout a
+// TMA copy with CU_TENSOR_MAP_SWIZZLE_64B writes).
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
     d |= (uint64_t)(16 >> 4) << 16;      // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset: next 8-row group
+    d |= (uint64_t)(512 >> 4) << 32;     // stride byte offset: next 8-row group
     d |= (uint64_t)1 << 46;              // descriptor version
-    d |= (uint64_t)2 << 61;              // 128-byte swizzle
+    d |= (uint64_t)4 << 61;              // 64-byte swizzle
     return d;
 }
 
-// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = 128.
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = 96.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                            ((uint32_t)(TM >> 4) << 24);
 
@@ -153,17 +206,24 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld_16cols(uint32_t taddr, uint32_t* r) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Ties 16 registers written by an asynchronous tcgen05.ld to a point after
+// tcgen05.wait::ld: uses of r cannot be scheduled above this statement.
+__device__ __forceinline__ void reg_fence16(uint32_t* r) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]));
 }
 
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -178,43 +238,42 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
     lo = __fadd_rn(lo, e);
 }
 
+
+// f 2^e as a double, built from the bit pattern of the FP32 value f (zero or
+// normal; the accumulated values here never reach the subnormal range).
+__device__ __forceinline__ double f2d_scaled(float f, int e) {
+    const uint32_t u = __float_as_uint(f);
+    const int ef = (int)((u >> 23) & 0xFF);
+    if (ef == 0) return 0.0;
+    const int ed = ef - 127 + 1023 + e;
+    if (ed <= 0 || ed >= 2047) return ldexp((double)f, e);   // outside the normal range: exact slow path
+    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)ed << 52) |
+                                    ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
-    ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Args a) {
+    ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const __grid_constant__ Args a) {
     extern __shared__ uint8_t smem_raw[];
-    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
-    if (a.lowerC && m0 + TM - 1 < n0) return;   // uniform for the CTA
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
     uint64_t* accfull = empty + STAGES;
-    uint64_t* accempty = accfull + 2;
-    uint64_t* drain = accempty + 2;
+    uint64_t* accempty = accfull + 1;
+    uint64_t* drain = accempty + 1;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int inst = blockIdx.z / a.groups;
-    const int pb = (blockIdx.z % a.groups) * a.pairs_per_group;
-    const int pe = min(NPAIRS, pb + a.pairs_per_group);
-    // K blocks that can hold non-zero digits for this tile
-    int kbl = 0, kbh = a.kblocks;
-    if (a.shA == 1) kbh = min(kbh, (m0 + TM + TK - 1) / TK);   // op(A) lower: k <= m
-    if (a.shA == 2) kbl = max(kbl, m0 / TK);                    // op(A) upper: k >= m
-    if (a.shB == 1) kbl = max(kbl, n0 / TK);                    // op(B) lower: k >= n
-    if (a.shB == 2) kbh = min(kbh, (n0 + TN + TK - 1) / TK);    // op(B) upper: k <= n
-    const int kspan = max(0, kbh - kbl);
-    const int nchunks = (kspan + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
-    const int units = (pe - pb) * nchunks;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&accfull[b], 1);
-            mbar_init(&accempty[b], 8);
-        }
+        mbar_init(accfull, 1);
+        mbar_init(accempty, 8);
         mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -234,19 +293,25 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) {
             // ------------------------------------------------------------ TMA producer
             int it = 0;
-            for (int u = 0; u < units && !*abort_flag; ++u) {
-                const int pair = pb + u / nchunks, chunk = u % nchunks;
-                const int p = c_pair_p[pair], q = c_pair_q[pair];
-                const int kb0 = kbl + chunk * KB_PER_CHUNK, kb1 = min(kbh, kb0 + KB_PER_CHUNK);
+            for (int u = blockIdx.x; u < a.units && !*abort_flag; u += gridDim.x) {
+                Unit w;
+                if (!decode_unit(a, u, w)) continue;
+                const int kb0 = w.kbl + w.c0 * KB_PER_CHUNK;
+                const int kb1 = min(w.kbh, w.kbl + w.c1 * KB_PER_CHUNK);
                 for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int st = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
                     if (!mbar_wait(&empty[st], ph ^ 1, abort_flag, a.err)) break;
                     uint8_t* sA = smem + st * STAGE_BYTES;
-                    uint8_t* sB = sA + TM * TK * 2;
+                    uint8_t* sB = sA + S * A_SLICE_BYTES;
                     mbar_expect_tx(&full[st], STAGE_BYTES);
-                    tma_load_2d(smem_u32(sA), &tmA, &full[st], kb * TK, (inst * S + p) * a.Mp + m0);
-                    tma_load_2d(smem_u32(sB), &tmB, &full[st], kb * TK, (inst * S + q) * a.Np + n0);
+#pragma unroll
+                    for (int p = 0; p < S; ++p) {
+                        tma_load_2d(smem_u32(sA + p * A_SLICE_BYTES), &tmA, &full[st], kb * TK,
+                                    (w.inst * S + p) * a.Mp + w.m0);
+                        tma_load_2d(smem_u32(sB + p * B_SLICE_BYTES), &tmB, &full[st], kb * TK,
+                                    (w.inst * S + p) * a.Np + w.n0);
+                    }
                 }
             }
             if (*abort_flag) {
@@ -263,35 +328,50 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ------------------------------------------------------------ MMA issuer
-            int it = 0;
-            for (int u = 0; u < units && !*abort_flag; ++u) {
-                const int chunk = u % nchunks;
-                const int kb0 = kbl + chunk * KB_PER_CHUNK, kb1 = min(kbh, kb0 + KB_PER_CHUNK);
-                const int buf = u & 1;
-                const uint32_t aph = (u >> 1) & 1;
-                if (!mbar_wait(&accempty[buf], aph ^ 1, abort_flag, a.err)) break;
-                fence_after_sync();
-                const uint32_t d_tmem = tmem_base + buf * TN;
-                bool ok = true;
-                for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                    const int st = it % STAGES;
-                    const uint32_t ph = (it / STAGES) & 1;
-                    if (!mbar_wait(&full[st], ph, abort_flag, a.err)) {
+            int it = 0, chunk_it = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; ok && u < a.units && !*abort_flag; u += gridDim.x) {
+                Unit w;
+                if (!decode_unit(a, u, w)) continue;
+                for (int c = w.c0; ok && c < w.c1; ++c, ++chunk_it) {
+                    const int kb0 = w.kbl + c * KB_PER_CHUNK, kb1 = min(w.kbh, kb0 + KB_PER_CHUNK);
+                    if (!mbar_wait(accempty, (chunk_it & 1) ^ 1, abort_flag, a.err)) {
                         ok = false;
                         break;
                     }
                     fence_after_sync();
-                    const uint32_t sA = smem_u32(smem + st * STAGE_BYTES);
-                    const uint32_t sB = sA + TM * TK * 2;
+                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int st = it % STAGES;
+                        const uint32_t ph = (it / STAGES) & 1;
+                        if (!mbar_wait(&full[st], ph, abort_flag, a.err)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after_sync();
+                        const uint32_t sA = smem_u32(smem + st * STAGE_BYTES);
+                        const uint32_t sB = sA + S * A_SLICE_BYTES;
+                        const uint64_t dA = smem_desc_sw64(sA), dB = smem_desc_sw64(sB);
 #pragma unroll
-                    for (int k = 0; k < TK / 16; ++k) {
-                        umma_bf16(d_tmem, smem_desc_sw128(sA + k * 32), smem_desc_sw128(sB + k * 32),
-                                  (kb > kb0 || k > 0) ? 1u : 0u);
+                        for (int lv = 0; lv < S; ++lv) {
+                            const uint32_t d_tmem = tmem_base + lv * TN;
+#pragma unroll
+                            for (int p = 0; p <= lv; ++p) {
+                                const int q = lv - p;
+#pragma unroll
+                                for (int k = 0; k < TK / 16; ++k) {
+                                    // descriptor start addresses are in 16-byte units
+                                    const uint64_t offA = (uint64_t)((p * A_SLICE_BYTES + k * 32) >> 4);
+                                    const uint64_t offB = (uint64_t)((q * B_SLICE_BYTES + k * 32) >> 4);
+                                    const bool first = (kb == kb0) && p == 0 && k == 0;
+                                    umma_bf16(d_tmem, dA + offA, dB + offB, first ? 0u : 1u);
+                                }
+                            }
+                        }
+                        umma_commit(&empty[st]);
                     }
-                    umma_commit(&empty[st]);
+                    if (!ok) break;
+                    umma_commit(accfull);
                 }
-                if (!ok) break;
-                umma_commit(&accfull[buf]);
             }
             // all MMAs issued by this thread have completed once `drain` fires
             umma_commit(drain);
@@ -301,51 +381,75 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else {
         // ---------------------------------------------------------------- epilogue
-        const int ew = warp - 2;              // 0..7
-        const int quarter = warp % 4;         // TMEM lanes 32*quarter .. +31
-        const int colbase = (ew / 4) * 64;    // 64 of the 128 columns
+        const int quarter = warp % 4;          // TMEM lanes 32*quarter .. +31 (warps 2..9)
+        const int colbase = ((warp - 2) / 4) * (TN / 2);   // 48 of the 96 columns
         const int row = quarter * 32 + lane;
-        float hi[64], lo[64];
-#pragma unroll
-        for (int j = 0; j < 64; ++j) {
-            hi[j] = 0.f;
-            lo[j] = 0.f;
-        }
+        const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+        float hi[TN / 2], lo[TN / 2];
+        int chunk_it = 0;
         bool ok = true;
-        for (int u = 0; u < units; ++u) {
-            const int pair = pb + u / nchunks;
-            const int buf = u & 1;
-            const uint32_t aph = (u >> 1) & 1;
-            if (!mbar_wait(&accfull[buf], aph, abort_flag, a.err)) {
-                ok = false;
-                break;
+        for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
+            Unit w;
+            if (!decode_unit(a, u, w)) continue;
+#pragma unroll
+            for (int j = 0; j < TN / 2; ++j) {
+                hi[j] = 0.f;
+                lo[j] = 0.f;
             }
-            fence_after_sync();
-            const float scale = ldexpf(1.0f, -7 * (c_pair_p[pair] + c_pair_q[pair]));
+            for (int c = w.c0; c < w.c1; ++c, ++chunk_it) {
+                if (!mbar_wait(accfull, chunk_it & 1, abort_flag, a.err)) {
+                    ok = false;
+                    break;
+                }
+                fence_after_sync();
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                uint32_t r[32];
-                tmem_ld_32cols(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * TN + colbase + h * 32, r);
+                for (int lv = 0; lv < S; ++lv) {
+                    uint32_t r[TN / 2];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) df_add(hi[h * 32 + j], lo[h * 32 + j], __uint_as_float(r[j]) * scale);
+                    for (int h = 0; h < TN / 32; ++h)
+                        tmem_ld_16cols(tmem_base + lane_addr + lv * TN + colbase + h * 16, r + h * 16);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int h = 0; h < TN / 32; ++h) reg_fence16(r + h * 16);
+                    const float scale = __uint_as_float((uint32_t)(127 - 7 * lv) << 23);   // 2^{-7 lv}
+#pragma unroll
+                    for (int j = 0; j < TN / 2; ++j) df_add(hi[j], lo[j], __uint_as_float(r[j]) * scale);
+                }
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(accempty);
             }
-            fence_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&accempty[buf]);
-        }
-        const int i = m0 + row;
-        if (ok && i < a.M) {
-            const int ea = a.expA[(long long)inst * a.Mp + i];
-            const int* expB = a.expB + (long long)inst * a.Np;
-            double* Cm = a.C + inst * a.sC;
+            if (!ok) break;
+            // C update from registers (tensor memory is already free for the next unit)
+            const int i = w.m0 + row;
+            if (i < a.M) {
+                const int ea = a.expA[(long long)w.inst * a.Mp + i] - 14;
+                const int* expB = a.expB + (long long)w.inst * a.Np;
+                double* Cm = a.C + w.inst * a.sC;
+                const bool atomic = a.ksplit > 1;
+                const bool neg = a.alpha == -1.0, unit_alpha = neg || a.alpha == 1.0;
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                const int nn = n0 + colbase + j;
-                if (nn >= a.N || (a.lowerC && i < nn)) continue;
-                const double v = ((double)hi[j] + (double)lo[j]) * ldexp(a.alpha, ea + expB[nn] - 14);
-                double* c = Cm + i + (long long)nn * a.ldc;
-                if (a.atomic) atomicAdd(c, v);
-                else *c += v;
+                for (int j0 = 0; j0 < TN / 2; j0 += 8) {
+                    double cv[8];
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int nn = w.n0 + colbase + j0 + jj;
+                        const bool valid = nn < a.N && !(a.lowerC && i < nn);
+                        cv[jj] = (valid && !atomic) ? Cm[i + (long long)nn * a.ldc] : 0.0;
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int nn = w.n0 + colbase + j0 + jj;
+                        if (nn >= a.N || (a.lowerC && i < nn)) continue;
+                        const int e = ea + expB[nn];
+                        double v = f2d_scaled(hi[j0 + jj], e) + f2d_scaled(lo[j0 + jj], e);
+                        if (!unit_alpha) v *= a.alpha;
+                        else if (neg) v = -v;
+                        double* c = Cm + i + (long long)nn * a.ldc;
+                        if (atomic) atomicAdd(c, v);
+                        else *c = cv[jj] + v;
+                    }
+                }
             }
         }
     }
@@ -478,37 +582,57 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int kp) {
+// 2D map over `rows` digit rows of kp bf16 each; box = TK x box_rows, 64-byte swizzle.
+int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int kp, int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return BTA_ERR_CUDA;
     cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-    cuuint32_t box[2] = {TK, 128};
+    cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? BTA_OK : BTA_ERR_CUDA;
 }
+
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 148;
+    }
+    return n;
+}
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 }  // namespace oz
 
 // Workspace needed by ozaki_gemm for one M x N x K product (bytes; a batch of
 // products needs batch times this).
 size_t ozaki_workspace_bytes(int M, int N, int K) {
-    const size_t Mp = ((size_t)M + 127) / 128 * 128, Np = ((size_t)N + 127) / 128 * 128;
-    const size_t Kp = ((size_t)K + oz::TK - 1) / oz::TK * oz::TK;
+    const size_t Mp = (size_t)oz::round_up(M, oz::PAD_M), Np = (size_t)oz::round_up(N, oz::PAD_N);
+    const size_t Kp = (size_t)std::max(oz::PAD_K, oz::round_up(K, oz::PAD_K));
     return oz::S * (Mp + Np) * Kp * 2 + (Mp + Np) * sizeof(int) + 4 * 256;
 }
 
+// Largest M the tensor-core path accepts (row tiles per matrix).
+int ozaki_max_rows() { return oz::MAX_MT * oz::TM; }
+
 // C = beta Cin + alpha op(A) op(B) through the digit-split tensor-core path.
-// ws: device workspace of ozaki_workspace_bytes(M, N, K); err: device int.
+// ws: device workspace of batch * ozaki_workspace_bytes(M, N, K); err: device int.
 int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     using namespace oz;
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return BTA_OK;
+    if (g.M > MAX_MT * TM) return BTA_ERR_ARG;
     const int nb = g.batch;
-    const int Mp = (g.M + 127) / 128 * 128, Np = (g.N + 127) / 128 * 128;
-    const int Kp = std::max(TK, (g.K + TK - 1) / TK * TK);
+    const int Mp = round_up(g.M, PAD_M), Np = round_up(g.N, PAD_N);
+    const int Kp = std::max(PAD_K, round_up(g.K, PAD_K));
     uint8_t* w = static_cast<uint8_t*>(ws);
     __nv_bfloat16* digA = reinterpret_cast<__nv_bfloat16*>(w);
     __nv_bfloat16* digB = digA + (size_t)nb * S * Mp * Kp;
@@ -531,26 +655,33 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
                                                                                Np, Kp, expB, digB, g.sB);
     BTA_LAUNCH_CHECK();
     CUtensorMap mA, mB;
-    BTA_TRY(make_map(&mA, digA, nb * S * Mp, Kp));
-    BTA_TRY(make_map(&mB, digB, nb * S * Np, Kp));
+    BTA_TRY(make_map(&mA, digA, nb * S * Mp, Kp, TM));
+    BTA_TRY(make_map(&mB, digB, nb * S * Np, Kp, TN));
     // C = beta Cin first (the tensor-core kernel adds into C)
     const bool inplace = (g.Cin == g.C && g.ldci == g.ldc && g.beta == 1.0 && g.sCi == g.sC);
     if (!inplace) BTA_TRY(scale_into64(s, g.M, g.N, g.Cin, g.ldci, g.beta, g.C, g.ldc, g.lowerC, nb, g.sCi, g.sC));
-    const int gm = Mp / TM, gn = Np / TN;
-    long long tiles = (long long)gm * gn;
-    if (g.lowerC) tiles = (tiles + gm) / 2;
-    tiles *= nb;
-    int groups = 1;
-    while (groups < 5 && tiles * groups < 152) ++groups;
-    const int per = (NPAIRS + groups - 1) / groups;
-    groups = (NPAIRS + per - 1) / per;
-    Args a;
-    a.M = g.M; a.N = g.N; a.groups = groups; a.sC = g.sC;
+    Args a{};
+    a.M = g.M; a.N = g.N; a.sC = g.sC;
     a.Mp = Mp; a.Np = Np; a.kblocks = Kp / TK;
+    a.gm = Mp / TM; a.gn = Np / TN;
+    if (g.lowerC) {
+        a.mcum[0] = 0;
+        for (int m = 0; m < a.gm; ++m)
+            a.mcum[m + 1] = a.mcum[m] + std::min(a.gn, (m * TM + TM - 1) / TN + 1);
+        a.tiles = a.mcum[a.gm];
+    } else {
+        a.tiles = a.gm * a.gn;
+    }
+    const long long base = (long long)nb * a.tiles;
+    const int sms = num_sms();
+    const int nchunks = (a.kblocks + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
+    long long ksplit = 1;
+    if (base < sms) ksplit = std::min<long long>(nchunks, (sms + base - 1) / base);
+    if (base * ksplit > 0x7FFFFFFFLL) return BTA_ERR_ARG;
+    a.ksplit = (int)ksplit;
+    a.units = (int)(base * ksplit);
     a.expA = expA; a.expB = expB;
     a.C = g.C; a.ldc = g.ldc; a.alpha = g.alpha;
-    a.pairs_per_group = per;
-    a.atomic = groups > 1;
     a.lowerC = g.lowerC;
     a.shA = g.shA;
     a.shB = g.shB;
@@ -561,7 +692,8 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
                                           (int)SMEM_BYTES));
         attr = true;
     }
-    ozaki_gemm_kernel<<<dim3(gm, gn, nb * groups), THREADS, SMEM_BYTES, s>>>(mA, mB, a);
+    const int grid = (int)std::min<long long>(a.units, sms);
+    ozaki_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(mA, mB, a);
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }
@@ -572,7 +704,7 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
 // rest (arrow, tip, small panels of the recursive diagonal factorisation)
 // stay on the FP64 pipe.
 int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
-    if (g.M >= ex->min_dim && g.N >= ex->min_dim && g.K >= 1 &&
+    if (g.M >= ex->min_dim && g.N >= ex->min_dim && g.K >= 1 && g.M <= ozaki_max_rows() &&
         (size_t)g.batch * ozaki_workspace_bytes(g.M, g.N, g.K) <= ex->ws_bytes)
         return ozaki_gemm(s, g, ex->ws, ex->err);
     return gemm64(s, g);
