@@ -51,7 +51,9 @@ constexpr int S = 5;                      // digit slices = accumulated levels
 constexpr int TM = 128, TN = 96, TK = 32; // output tile; K block (64-byte rows)
 constexpr int STAGES = 3;
 constexpr int KB_PER_CHUNK = 512 / TK;    // exactness bound of one FP32 level accumulation
-constexpr int THREADS = 320;
+constexpr int EPI_WARPS = 16;            // 4 per TMEM lane quarter
+constexpr int EPI_COLS = TN / (EPI_WARPS / 4);   // 24 columns per epilogue thread
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;       // S * TN = 480 used
 constexpr uint32_t A_SLICE_BYTES = TM * TK * 2;                       // 8 KB
 constexpr uint32_t B_SLICE_BYTES = TN * TK * 2;                       // 6 KB
@@ -81,6 +83,10 @@ struct Args {
     int lowerC;          // only entries m >= n (tiles strictly above skipped)
     int shA, shB;        // triangular shapes of op(A), op(B): K blocks outside them are zero, skipped
     int* err;            // set to 1 on a wait time-out
+    const double* Cin;   // C = beta Cin + alpha op(A) op(B) when ksplit == 1 and Cin != C
+    long long ldci, sCi;
+    double beta;
+    int inplace;         // Cin is C with beta = 1 (or the K split pre-initialised C)
     int mcum[MAX_MT + 1];// lowerC: tiles of row tiles 0..m-1
 };
 
@@ -120,6 +126,22 @@ __device__ __forceinline__ bool decode_unit(const Args& a, int u, Unit& w) {
     w.c0 = min(nch, kpart * per);
     w.c1 = min(nch, w.c0 + per);
     return w.c1 > w.c0;
+}
+
+// Prefetch the C (or Cin) tile of unit w into L2 ahead of the epilogue's
+// read-modify-write: one bulk prefetch per column of the tile.
+__device__ __forceinline__ void prefetch_c_tile(const double* base, long long ld, const Unit& w, int M, int N) {
+    const int rows = min(TM, M - w.m0);
+    const int ncols = min(TN, N - w.n0);
+    for (int j = 0; j < ncols; ++j) {
+        const double* col = base + w.m0 + (long long)(w.n0 + j) * ld;
+        uintptr_t lo = reinterpret_cast<uintptr_t>(col);
+        const uintptr_t hi = reinterpret_cast<uintptr_t>(col + rows);
+        lo = (lo + 15) & ~uintptr_t(15);
+        const uintptr_t bytes = (hi - lo) & ~uintptr_t(15);
+        if (hi > lo && bytes >= 16)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)bytes) : "memory");
+    }
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -206,25 +228,18 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld_16cols(uint32_t taddr, uint32_t* r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+__device__ __forceinline__ void tmem_ld_8cols(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void reg_fence8(uint32_t* r) {
+    asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]));
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Ties 16 registers written by an asynchronous tcgen05.ld to a point after
-// tcgen05.wait::ld: uses of r cannot be scheduled above this statement.
-__device__ __forceinline__ void reg_fence16(uint32_t* r) {
-    asm volatile(""
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15]));
-}
 
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -273,7 +288,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(&empty[s], 1);
         }
         mbar_init(accfull, 1);
-        mbar_init(accempty, 8);
+        mbar_init(accempty, EPI_WARPS);
         mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -298,10 +313,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (!decode_unit(a, u, w)) continue;
                 const int kb0 = w.kbl + w.c0 * KB_PER_CHUNK;
                 const int kb1 = min(w.kbh, w.kbl + w.c1 * KB_PER_CHUNK);
+                const int kb_last = w.kbl + (w.c1 - 1) * KB_PER_CHUNK;
                 for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int st = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
                     if (!mbar_wait(&empty[st], ph ^ 1, abort_flag, a.err)) break;
+                    if (kb == kb_last && a.ksplit == 1) {
+                        if (a.inplace)
+                            prefetch_c_tile(a.C + w.inst * a.sC, a.ldc, w, a.M, a.N);
+                        else if (a.Cin != nullptr && a.beta != 0.0)
+                            prefetch_c_tile(a.Cin + w.inst * a.sCi, a.ldci, w, a.M, a.N);
+                    }
                     uint8_t* sA = smem + st * STAGE_BYTES;
                     uint8_t* sB = sA + S * A_SLICE_BYTES;
                     mbar_expect_tx(&full[st], STAGE_BYTES);
@@ -381,18 +403,19 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else {
         // ---------------------------------------------------------------- epilogue
-        const int quarter = warp % 4;          // TMEM lanes 32*quarter .. +31 (warps 2..9)
-        const int colbase = ((warp - 2) / 4) * (TN / 2);   // 48 of the 96 columns
+        const int quarter = warp % 4;          // TMEM lanes 32*quarter .. +31
+        const int colbase = ((warp - 2) / 4) * EPI_COLS;
         const int row = quarter * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-        float hi[TN / 2], lo[TN / 2];
+        float hi[EPI_COLS], lo[EPI_COLS];
         int chunk_it = 0;
         bool ok = true;
         for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
             Unit w;
-            if (!decode_unit(a, u, w)) continue;
+            // a unit without K blocks still writes beta Cin when there is no K split
+            if (!decode_unit(a, u, w) && (a.ksplit > 1 || a.inplace)) continue;
 #pragma unroll
-            for (int j = 0; j < TN / 2; ++j) {
+            for (int j = 0; j < EPI_COLS; ++j) {
                 hi[j] = 0.f;
                 lo[j] = 0.f;
             }
@@ -404,16 +427,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                 fence_after_sync();
 #pragma unroll
                 for (int lv = 0; lv < S; ++lv) {
-                    uint32_t r[TN / 2];
-#pragma unroll
-                    for (int h = 0; h < TN / 32; ++h)
-                        tmem_ld_16cols(tmem_base + lane_addr + lv * TN + colbase + h * 16, r + h * 16);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int h = 0; h < TN / 32; ++h) reg_fence16(r + h * 16);
                     const float scale = __uint_as_float((uint32_t)(127 - 7 * lv) << 23);   // 2^{-7 lv}
 #pragma unroll
-                    for (int j = 0; j < TN / 2; ++j) df_add(hi[j], lo[j], __uint_as_float(r[j]) * scale);
+                    for (int h = 0; h < EPI_COLS / 8; ++h) {
+                        uint32_t r[8];
+                        tmem_ld_8cols(tmem_base + lane_addr + lv * TN + colbase + h * 8, r);
+                        tmem_wait_ld();
+                        reg_fence8(r);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) df_add(hi[h * 8 + j], lo[h * 8 + j], __uint_as_float(r[j]) * scale);
+                    }
                 }
                 fence_before_sync();
                 __syncwarp();
@@ -426,16 +449,19 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int ea = a.expA[(long long)w.inst * a.Mp + i] - 14;
                 const int* expB = a.expB + (long long)w.inst * a.Np;
                 double* Cm = a.C + w.inst * a.sC;
+                const double* Ci = a.inplace ? Cm : a.Cin + w.inst * a.sCi;
+                const long long ldi = a.inplace ? a.ldc : a.ldci;
+                const double beta = a.inplace ? 1.0 : a.beta;
                 const bool atomic = a.ksplit > 1;
                 const bool neg = a.alpha == -1.0, unit_alpha = neg || a.alpha == 1.0;
 #pragma unroll
-                for (int j0 = 0; j0 < TN / 2; j0 += 8) {
+                for (int j0 = 0; j0 < EPI_COLS; j0 += 8) {
                     double cv[8];
 #pragma unroll
                     for (int jj = 0; jj < 8; ++jj) {
                         const int nn = w.n0 + colbase + j0 + jj;
                         const bool valid = nn < a.N && !(a.lowerC && i < nn);
-                        cv[jj] = (valid && !atomic) ? Cm[i + (long long)nn * a.ldc] : 0.0;
+                        cv[jj] = (valid && !atomic && beta != 0.0) ? Ci[i + (long long)nn * ldi] : 0.0;
                     }
 #pragma unroll
                     for (int jj = 0; jj < 8; ++jj) {
@@ -446,8 +472,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                         if (!unit_alpha) v *= a.alpha;
                         else if (neg) v = -v;
                         double* c = Cm + i + (long long)nn * a.ldc;
-                        if (atomic) atomicAdd(c, v);
-                        else *c = cv[jj] + v;
+                        if (atomic) {
+                            atomicAdd(c, v);
+                        } else {
+                            const double base = (beta == 1.0 || beta == 0.0) ? cv[jj] : beta * cv[jj];
+                            *c = base + v;
+                        }
                     }
                 }
             }
@@ -657,9 +687,7 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     CUtensorMap mA, mB;
     BTA_TRY(make_map(&mA, digA, nb * S * Mp, Kp, TM));
     BTA_TRY(make_map(&mB, digB, nb * S * Np, Kp, TN));
-    // C = beta Cin first (the tensor-core kernel adds into C)
     const bool inplace = (g.Cin == g.C && g.ldci == g.ldc && g.beta == 1.0 && g.sCi == g.sC);
-    if (!inplace) BTA_TRY(scale_into64(s, g.M, g.N, g.Cin, g.ldci, g.beta, g.C, g.ldc, g.lowerC, nb, g.sCi, g.sC));
     Args a{};
     a.M = g.M; a.N = g.N; a.sC = g.sC;
     a.Mp = Mp; a.Np = Np; a.kblocks = Kp / TK;
@@ -680,6 +708,15 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     if (base * ksplit > 0x7FFFFFFFLL) return BTA_ERR_ARG;
     a.ksplit = (int)ksplit;
     a.units = (int)(base * ksplit);
+    // with a K split the parts add into C, which must hold beta Cin first;
+    // otherwise the epilogue reads beta Cin itself
+    if (ksplit > 1 && !inplace)
+        BTA_TRY(scale_into64(s, g.M, g.N, g.Cin, g.ldci, g.beta, g.C, g.ldc, g.lowerC, nb, g.sCi, g.sC));
+    a.inplace = (inplace || ksplit > 1) ? 1 : 0;
+    a.Cin = g.Cin;
+    a.ldci = g.ldci;
+    a.sCi = g.sCi;
+    a.beta = g.Cin ? g.beta : 0.0;
     a.expA = expA; a.expB = expB;
     a.C = g.C; a.ldc = g.ldc; a.alpha = g.alpha;
     a.lowerC = g.lowerC;
