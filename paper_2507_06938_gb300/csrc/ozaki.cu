@@ -9,19 +9,24 @@
 // level s = p + q,
 //   (op(A) op(B))_ij ~ 2^{e_i + f_j - 14} sum_{s<S} 2^{-7s} L_s(i,j),
 //   L_s = sum_k sum_{p+q=s} d_p(i,k) d_q(k,j)
-// (levels s >= S fall below the digits' own precision).  Per k a level sum
-// is an integer of magnitude below 2^15 (at most 2^14 for s = 0), so over a
-// chunk of 512 values of k it stays below 2^24: the FP32 accumulator of
-// tcgen05.mma kind::f16 holds every partial sum exactly.  Each level has its
-// own accumulator in tensor memory; after every chunk the five accumulators
-// are drained (tcgen05.ld), scaled by 2^{-7s} and summed in double-float (two
-// FP32 words, error-free TwoSum) on the CUDA cores.  The result goes into C
+// (levels s >= S fall below the digits' own precision).  Per k the level
+// sums are integers bounded by 2^14 (s = 0, 1), 20480 (s = 2), 24576 (s = 3)
+// and 28672 (s = 4).  Each level has its own FP32 accumulator in tensor
+// memory (tcgen05.mma kind::f16):
+//   levels 0 and 1 stay below 2^24, hence exact, over 1024 values of k;
+//   level 2 is exact over 512 values of k and is drained that often;
+//   levels 3 and 4 run over 1024 values of k past 2^24, where each of at
+//   most 320 accumulation steps rounds by at most 2 units: 2^-37 and 2^-44 of
+//   the output scale |A_i||B_j|K, below the 2^-35 truncation of the digits.
+// A drain reads an accumulator (tcgen05.ld), scales it by 2^{-7s} and adds it
+// into a double-float sum (two FP32 words, error-free TwoSum) on the CUDA
+// cores.  The result goes into C
 // with one FP64 addition per element; the power-of-two scaling and the
 // FP32 -> FP64 widening are done on the bit patterns, because the FP64 pipe
 // of GB300 (~1.2 TFLOP/s) is the scarce unit and the bf16 tensor pipe
 // (~1.9 PFLOP/s) the plentiful one.
 //
-// Kernel (persistent, one CTA of 320 threads per SM, 128 x 96 output tiles):
+// Kernel (persistent, one CTA of 576 threads per SM, 128 x 96 output tiles):
 //   warp 0      TMA producer: for every 32-wide K block all five digit slices
 //               of the A tile (128 x 32) and of the B tile (96 x 32), 64-byte
 //               swizzle, into a 3-stage shared-memory ring (70 KB a stage), so
@@ -29,8 +34,9 @@
 //   warp 1      allocates 512 TMEM columns (five 96-column accumulators) and
 //               issues tcgen05.mma (M = 128, N = 96, K = 16) for the 15 digit
 //               pairs of each K block from one thread
-//   warps 2..9  drain the level accumulators after each chunk, then update C
-//               while the next tile's products run
+//   warps 2..17 drain level 2 after every 512-long K chunk and the other
+//               levels after every second chunk, then update C while the
+//               next tile's products run
 // Work units are (matrix, tile, K part); a K split (atomic adds into C) only
 // appears when the tiles alone cannot fill the GPU.  Every wait on an
 // mbarrier is bounded in time; on expiry the kernel records an error, stops
@@ -50,7 +56,7 @@ namespace oz {
 constexpr int S = 5;                      // digit slices = accumulated levels
 constexpr int TM = 128, TN = 96, TK = 32; // output tile; K block (64-byte rows)
 constexpr int STAGES = 3;
-constexpr int KB_PER_CHUNK = 512 / TK;    // exactness bound of one FP32 level accumulation
+constexpr int KB_PER_CHUNK = 512 / TK;    // exactness bound of the level-2 accumulation
 constexpr int EPI_WARPS = 16;            // 4 per TMEM lane quarter
 constexpr int EPI_COLS = TN / (EPI_WARPS / 4);   // 24 columns per epilogue thread
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
@@ -267,6 +273,22 @@ __device__ __forceinline__ double f2d_scaled(float f, int e) {
     return __longlong_as_double((long long)bits);
 }
 
+// Adds 2^{-7 lv} times this thread's EPI_COLS accumulator columns of one
+// level (tensor memory address taddr: lane quarter, level, column group) into
+// the double-float sums hi + lo.
+__device__ __forceinline__ void drain_level(uint32_t taddr, int lv, float* hi, float* lo) {
+    const float scale = __uint_as_float((uint32_t)(127 - 7 * lv) << 23);   // 2^{-7 lv}
+#pragma unroll
+    for (int h = 0; h < EPI_COLS / 8; ++h) {
+        uint32_t r[8];
+        tmem_ld_8cols(taddr + h * 8, r);
+        tmem_wait_ld();
+        reg_fence8(r);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) df_add(hi[h * 8 + j], lo[h * 8 + j], __uint_as_float(r[j]) * scale);
+    }
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const __grid_constant__ Args a) {
@@ -274,9 +296,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* accfull = empty + STAGES;
-    uint64_t* accempty = accfull + 1;
-    uint64_t* drain = accempty + 1;
+    // accumulator hand-off: group A = levels 0, 1, 3, 4 (drained every second
+    // chunk), group B = level 2 (drained every chunk)
+    uint64_t* fullA = empty + STAGES;
+    uint64_t* emptyA = fullA + 1;
+    uint64_t* fullB = emptyA + 1;
+    uint64_t* emptyB = fullB + 1;
+    uint64_t* drain = emptyB + 1;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -287,8 +313,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accfull, 1);
-        mbar_init(accempty, EPI_WARPS);
+        mbar_init(fullA, 1);
+        mbar_init(emptyA, EPI_WARPS);
+        mbar_init(fullB, 1);
+        mbar_init(emptyB, EPI_WARPS);
         mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -350,18 +378,22 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ------------------------------------------------------------ MMA issuer
-            int it = 0, chunk_it = 0;
+            int it = 0, nA = 0, nB = 0;
             bool ok = true;
             for (int u = blockIdx.x; ok && u < a.units && !*abort_flag; u += gridDim.x) {
                 Unit w;
                 if (!decode_unit(a, u, w)) continue;
-                for (int c = w.c0; ok && c < w.c1; ++c, ++chunk_it) {
+                for (int c = w.c0; ok && c < w.c1; ++c) {
                     const int kb0 = w.kbl + c * KB_PER_CHUNK, kb1 = min(w.kbh, kb0 + KB_PER_CHUNK);
-                    if (!mbar_wait(accempty, (chunk_it & 1) ^ 1, abort_flag, a.err)) {
-                        ok = false;
-                        break;
+                    const bool resetA = ((c - w.c0) & 1) == 0;
+                    const bool drainA = ((c - w.c0) & 1) == 1 || c == w.c1 - 1;
+                    if (resetA) {
+                        if (!mbar_wait(emptyA, (nA & 1) ^ 1, abort_flag, a.err)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after_sync();
                     }
-                    fence_after_sync();
                     for (int kb = kb0; kb < kb1; ++kb, ++it) {
                         const int st = it % STAGES;
                         const uint32_t ph = (it / STAGES) & 1;
@@ -376,6 +408,14 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                         for (int lv = 0; lv < S; ++lv) {
                             const uint32_t d_tmem = tmem_base + lv * TN;
+                            if (lv == 2 && kb == kb0) {
+                                // level 2 restarts every chunk: its previous sums must be drained
+                                if (!mbar_wait(emptyB, (nB & 1) ^ 1, abort_flag, a.err)) {
+                                    ok = false;
+                                    break;
+                                }
+                                fence_after_sync();
+                            }
 #pragma unroll
                             for (int p = 0; p <= lv; ++p) {
                                 const int q = lv - p;
@@ -384,15 +424,21 @@ __global__ void __launch_bounds__(THREADS, 1)
                                     // descriptor start addresses are in 16-byte units
                                     const uint64_t offA = (uint64_t)((p * A_SLICE_BYTES + k * 32) >> 4);
                                     const uint64_t offB = (uint64_t)((q * B_SLICE_BYTES + k * 32) >> 4);
-                                    const bool first = (kb == kb0) && p == 0 && k == 0;
+                                    const bool first = (kb == kb0) && p == 0 && k == 0 && (lv == 2 || resetA);
                                     umma_bf16(d_tmem, dA + offA, dB + offB, first ? 0u : 1u);
                                 }
                             }
                         }
+                        if (!ok) break;
                         umma_commit(&empty[st]);
                     }
                     if (!ok) break;
-                    umma_commit(accfull);
+                    umma_commit(fullB);
+                    ++nB;
+                    if (drainA) {
+                        umma_commit(fullA);
+                        ++nA;
+                    }
                 }
             }
             // all MMAs issued by this thread have completed once `drain` fires
@@ -408,7 +454,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int row = quarter * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
         float hi[EPI_COLS], lo[EPI_COLS];
-        int chunk_it = 0;
+        int nA = 0, nB = 0;
         bool ok = true;
         for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
             Unit w;
@@ -419,28 +465,33 @@ __global__ void __launch_bounds__(THREADS, 1)
                 hi[j] = 0.f;
                 lo[j] = 0.f;
             }
-            for (int c = w.c0; c < w.c1; ++c, ++chunk_it) {
-                if (!mbar_wait(accfull, chunk_it & 1, abort_flag, a.err)) {
+            for (int c = w.c0; c < w.c1; ++c) {
+                const bool drainA = ((c - w.c0) & 1) == 1 || c == w.c1 - 1;
+                if (!mbar_wait(fullB, nB & 1, abort_flag, a.err)) {
                     ok = false;
                     break;
                 }
                 fence_after_sync();
-#pragma unroll
-                for (int lv = 0; lv < S; ++lv) {
-                    const float scale = __uint_as_float((uint32_t)(127 - 7 * lv) << 23);   // 2^{-7 lv}
-#pragma unroll
-                    for (int h = 0; h < EPI_COLS / 8; ++h) {
-                        uint32_t r[8];
-                        tmem_ld_8cols(tmem_base + lane_addr + lv * TN + colbase + h * 8, r);
-                        tmem_wait_ld();
-                        reg_fence8(r);
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) df_add(hi[h * 8 + j], lo[h * 8 + j], __uint_as_float(r[j]) * scale);
-                    }
-                }
+                drain_level(tmem_base + lane_addr + 2 * TN + colbase, 2, hi, lo);
                 fence_before_sync();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(accempty);
+                if (lane == 0) mbar_arrive(emptyB);
+                ++nB;
+                if (drainA) {
+                    if (!mbar_wait(fullA, nA & 1, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after_sync();
+                    drain_level(tmem_base + lane_addr + 0 * TN + colbase, 0, hi, lo);
+                    drain_level(tmem_base + lane_addr + 1 * TN + colbase, 1, hi, lo);
+                    drain_level(tmem_base + lane_addr + 3 * TN + colbase, 3, hi, lo);
+                    drain_level(tmem_base + lane_addr + 4 * TN + colbase, 4, hi, lo);
+                    fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(emptyA);
+                    ++nA;
+                }
             }
             if (!ok) break;
             // C update from registers (tensor memory is already free for the next unit)
