@@ -7,14 +7,22 @@
 // matrix factors an n x n block (n <= 128) entirely in shared memory with
 // values held as unevaluated sums hi + lo of two FP32 numbers (about 48
 // significand bits, well above the 36 bits of the tensor-core products of
-// the mixed path), using only the FP32 pipe:
+// the mixed path), using only the FP32 and integer pipes:
 //   error-free sum (Knuth's TwoSum) and product (FMA-based TwoProduct),
-//   1/sqrt by one Newton-Raphson step in double-float from an FP32 seed.
-// Phase 1: right-looking Cholesky, one barrier per pivot; column k is scaled
-//   to L in place one iteration later (nothing reads it then).  L is written
-//   to global memory (FP64).
-// Phase 2: in-place inversion X = L^{-1} column by column from the right:
-//   X(i, j) = -(1/L_jj) sum_{k=j+1..i} X(i, k) L(k, j),  X(j, j) = 1/L_jj.
+//   1/sqrt by one Newton-Raphson step in double-float from an FP32 seed,
+//   FP64 <-> double-float conversion on the bit patterns (one FP64 addition
+//   per stored element).
+// Both phases are right-looking with one barrier per step, so a step costs
+// one short chain of dependent operations per thread:
+// Phase 1: Cholesky.  Step k subtracts (a_ik / a_kk) a_jk from a_ij for
+//   k < j <= i; the thread that finishes a_{k+1,k+1} computes the next
+//   1/sqrt pivot at once; column k is scaled to L one step later (nobody
+//   reads it then).
+// Phase 2: X = L^{-1} by forward substitution on the identity.  B starts as
+//   the identity; step i makes row i of X final (X(i, j) = B(i, j) / L_ii)
+//   and subtracts L(r, i) X(i, j) from B(r, j) for r > i, j <= i.  The strict
+//   lower triangle of B / X lives transposed in the strict upper triangle of
+//   the shared-memory matrix, whose lower triangle holds L.
 // A non-positive pivot records BTA_ERR_NOT_PD (global row, matrix) in the
 // status word and poisons the results with NaN.
 
@@ -26,18 +34,51 @@ namespace {
 
 constexpr int DF_MAX = 128;
 constexpr int DF_LD = DF_MAX + 1;
-constexpr int DF_THREADS = 1024;
+constexpr int DF_THREADS = 512;
 
 struct df {
     float hi, lo;
 };
 
-__device__ __forceinline__ df df_make(double x) {
-    const float h = __double2float_rn(x);
-    return {h, __double2float_rn(x - (double)h)};
+// x as hi + lo: hi keeps the top 24 significand bits (truncated), lo the
+// rest rounded to 24 bits (relative error below 2^-47 of x).  Integer work
+// except one conversion of the low bits; FP32-range exponents only (others
+// take the library conversion).
+__device__ __forceinline__ df df_from_double(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    const int E = e - 1023;
+    if (e == 0) return {0.f, 0.f};
+    if (E < -74 || E > 127) {   // the low word's scale 2^(E-52) must be a normal FP32 (or x not finite)
+        const float h = __double2float_rn(x);
+        return {h, __double2float_rn(x - (double)h)};
+    }
+    const unsigned int sgn = (unsigned int)(b >> 63) << 31;
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    const float hi = __uint_as_float(sgn | ((unsigned int)(E + 127) << 23) | (unsigned int)(m >> 29));
+    const unsigned int rest = (unsigned int)(m & ((1u << 29) - 1));
+    float lo = 0.f;
+    if (rest) {
+        // rest * 2^(E - 52): the low 29 bits, rounded to FP32
+        lo = __uint2float_rn(rest) * __uint_as_float((unsigned int)(E - 52 + 127) << 23);
+        lo = __uint_as_float(__float_as_uint(lo) | sgn);
+    }
+    return {hi, lo};
 }
 
-__device__ __forceinline__ double df_double(df a) { return (double)a.hi + (double)a.lo; }
+// FP32 value as a double from its bit pattern (zero or normal).
+__device__ __forceinline__ double f_to_double(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int ef = (u >> 23) & 0xFF;
+    if (ef == 0) return 0.0;
+    if (ef == 0xFF) return (double)f;
+    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                    ((unsigned long long)(ef - 127 + 1023) << 52) |
+                                    ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return f_to_double(a.hi) + f_to_double(a.lo); }
 
 // a + b, both double-float
 __device__ __forceinline__ df df_add(df a, df b) {
@@ -61,6 +102,9 @@ __device__ __forceinline__ df df_mul(df a, df b) {
     return {h, __fsub_rn(e, __fsub_rn(h, p))};
 }
 
+// c - a * b, all double-float
+__device__ __forceinline__ df df_fnms(df c, df a, df b) { return df_add(c, df_neg(df_mul(a, b))); }
+
 // 1/sqrt(x) for x > 0: FP32 estimate y0, then y = y0 + y0 (1 - x y0^2) / 2
 // with the residual 1 - x y0^2 formed in double-float; NaN unless x > 0.
 __device__ __forceinline__ df df_rsqrt(df x) {
@@ -79,18 +123,17 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
                                                                    long long row0, long long* status, int m_first,
                                                                    int nbatch) {
     extern __shared__ float smf[];
-    float* Sh = smf;                      // column-major, ld DF_LD
+    // M[r][c] at (c * DF_LD + r): lower triangle = A, then L; strict upper = B / X transposed
+    float* Sh = smf;
     float* Sl = smf + DF_LD * DF_MAX;
-    float* yh = smf + 2 * DF_LD * DF_MAX; // 1/L_kk (double-float)
+    float* yh = smf + 2 * DF_LD * DF_MAX;   // 1/L_kk (double-float)
     float* yl = yh + DF_MAX + 1;
-    float* ph = yl + DF_MAX + 1;          // phase-2 partial sums (nq x rows_per)
-    float* pl = ph + DF_THREADS;
     A += blockIdx.x * sA;
     X += blockIdx.x * sX;
     const int tid = threadIdx.x;
     for (int e = tid; e < n * n; e += DF_THREADS) {
         const int i = e % n, j = e / n;
-        const df v = (i >= j) ? df_make(A[i + (long long)j * lda]) : df{0.f, 0.f};
+        const df v = (i >= j) ? df_from_double(A[i + (long long)j * lda]) : df{0.f, 0.f};
         Sh[j * DF_LD + i] = v.hi;
         Sl[j * DF_LD + i] = v.lo;
     }
@@ -120,8 +163,8 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
                 const df y2 = df_mul(y, y);
                 const df sik = df_mul(df{Sh[k * DF_LD + row], Sl[k * DF_LD + row]}, y2);
                 for (int j = k + 1 + q; j <= row; j += nq) {
-                    const df skj = df{Sh[k * DF_LD + j], Sl[k * DF_LD + j]};
-                    const df v = df_add(df{Sh[j * DF_LD + row], Sl[j * DF_LD + row]}, df_neg(df_mul(sik, skj)));
+                    const df v = df_fnms(df{Sh[j * DF_LD + row], Sl[j * DF_LD + row]}, sik,
+                                         df{Sh[k * DF_LD + j], Sl[k * DF_LD + j]});
                     Sh[j * DF_LD + row] = v.hi;
                     Sl[j * DF_LD + row] = v.lo;
                     if (j == k + 1 && row == k + 1) {   // the next pivot is final
@@ -143,48 +186,43 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
     __syncthreads();
     for (int e = tid; e < n * n; e += DF_THREADS) {
         const int i = e % n, j = e / n;
-        A[i + (long long)j * lda] = (i >= j) ? df_double(df{Sh[j * DF_LD + i], Sl[j * DF_LD + i]}) : 0.0;
+        A[i + (long long)j * lda] = (i >= j) ? df_to_double(df{Sh[j * DF_LD + i], Sl[j * DF_LD + i]}) : 0.0;
     }
     // ---------------------------------------------------------------- phase 2
-    // Column j: every row i > j is a dot product over k in (j, i] of X(i, k)
-    // (columns > j, already inverted) and L(k, j) (column j, still L), split
-    // over the nq threads of the row; partial sums meet in shared memory.
-    for (int j = n - 1; j >= 0; --j) {
+    // B(r, j) (r > j) at M[j][r]; zero from the load (the strict upper
+    // triangle of the input is never read).  Step i: X(i, j) = B(i, j) y_i is
+    // final for j < i (written by the last update of row i), X(i, i) = y_i.
+    for (int i = 0; i < n - 1; ++i) {
         __syncthreads();
-        if (row > j && row < n) {
-            df acc{0.f, 0.f};
-            for (int k = j + 1 + q; k <= row; k += nq)
-                acc = df_add(acc, df_mul(df{Sh[k * DF_LD + row], Sl[k * DF_LD + row]},
-                                         df{Sh[j * DF_LD + k], Sl[j * DF_LD + k]}));
-            ph[q * rows_per + row] = acc.hi;
-            pl[q * rows_per + row] = acc.lo;
-        }
-        __syncthreads();
-        if (q == 0 && row >= j && row < n) {
-            if (row == j) {
-                Sh[j * DF_LD + j] = yh[j];
-                Sl[j * DF_LD + j] = yl[j];
-            } else {
-                df sum{ph[row], pl[row]};
-                for (int qq = 1; qq < nq; ++qq) sum = df_add(sum, df{ph[qq * rows_per + row], pl[qq * rows_per + row]});
-                const df xij = df_neg(df_mul(sum, df{yh[j], yl[j]}));
-                Sh[j * DF_LD + row] = xij.hi;
-                Sl[j * DF_LD + row] = xij.lo;
+        const int r = row;
+        if (r > i && r < n) {
+            const df lri = df{Sh[i * DF_LD + r], Sl[i * DF_LD + r]};
+            const bool finish = (r == i + 1);
+            const df yr = finish ? df{yh[r], yl[r]} : df{0.f, 0.f};
+            for (int j = q; j <= i; j += nq) {
+                const df xij = (j == i) ? df{yh[i], yl[i]} : df{Sh[i * DF_LD + j], Sl[i * DF_LD + j]};
+                df b = df_fnms(df{Sh[r * DF_LD + j], Sl[r * DF_LD + j]}, lri, xij);
+                if (finish) b = df_mul(b, yr);   // row r is final after this step
+                Sh[r * DF_LD + j] = b.hi;
+                Sl[r * DF_LD + j] = b.lo;
             }
         }
     }
     __syncthreads();
     for (int e = tid; e < n * n; e += DF_THREADS) {
         const int i = e % n, j = e / n;
-        X[i + (long long)j * ldx] = (i >= j) ? df_double(df{Sh[j * DF_LD + i], Sl[j * DF_LD + i]}) : 0.0;
+        double v = 0.0;
+        if (i > j) v = df_to_double(df{Sh[i * DF_LD + j], Sl[i * DF_LD + j]});
+        else if (i == j) v = df_to_double(df{yh[i], yl[i]});
+        X[i + (long long)j * ldx] = v;
     }
 }
 
 }  // namespace
 
 size_t chol_inv_df32_smem_bytes() {
-    // S (hi, lo), y (hi, lo), partial sums (hi, lo)
-    return (2 * (size_t)DF_LD * DF_MAX + 2 * (DF_MAX + 1) + 2 * (size_t)DF_THREADS) * sizeof(float);
+    // M (hi, lo), y (hi, lo)
+    return (2 * (size_t)DF_LD * DF_MAX + 2 * (DF_MAX + 1)) * sizeof(float);
 }
 
 int chol_inv_df32_launch(cudaStream_t s, double* A, long long lda, long long sA, double* X, long long ldx,

@@ -555,35 +555,16 @@ __global__ void __launch_bounds__(THREADS, 1)
 // operations on the FP64 bit pattern are used (the FP64 pipe of GB300 is the
 // slow one).  Output: dig[s][r][k] (bf16, rows padded to Rp, K padded to Kp
 // with zeros) and exp[r] (0 for padding rows).
-constexpr int SPLIT_ROWS = 32, SPLIT_K = 64;
+constexpr int SPLIT_ROWS = 32, SPLIT_K = 64, SPLIT_THREADS = 256;
 
-__global__ void __launch_bounds__(256) row_maxexp_kernel(const double* P, long long sr, long long sk, int R, int K,
-                                                         int shape, int Rp, int* expo, long long sP) {
-    // one warp per row; blockIdx.y = matrix
-    P += blockIdx.y * sP;
-    expo += (long long)blockIdx.y * Rp;
-    const int r = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (r >= Rp) return;
-    // the largest biased exponent field of the row decides e_r
-    unsigned int emax = 0;
-    if (r < R) {
-        int kb = 0, ke = K;
-        if (shape == 1) ke = min(K, r + 1);
-        if (shape == 2) kb = r;
-        for (int k = kb + lane; k < ke; k += 32) {
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(P[r * sr + k * sk]);
-            const unsigned int ef = (unsigned int)((bits >> 52) & 0x7FF);
-            if (ef > emax) emax = ef;
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-    if (lane == 0) {
-        // |x| < 2^(ef - 1023 + 1) for a normal number with exponent field ef;
-        // a NaN or Inf in the row gives a huge exponent, so the product
-        // overflows to a non-finite value instead of passing silently
-        expo[r] = emax == 0 ? 0 : (emax == 0x7FF ? 4096 : (int)emax - 1023 + 1);
-    }
-}
+struct SplitJob {
+    const double* P;
+    long long sr, sk, sP;   // strides of X[r][k] and between matrices
+    int R, K, shape, Rp, Kp;
+    int* expo;              // Rp per matrix
+    __nv_bfloat16* dig;     // S * Rp * Kp per matrix
+    int row_blocks;         // Rp / SPLIT_ROWS
+};
 
 __device__ __forceinline__ long long fixed_point35(double x, int e) {
     // round(x 2^{35 - e}) for |x| < 2^e, by shifting the 53-bit significand
@@ -605,42 +586,94 @@ __device__ __forceinline__ long long fixed_point35(double x, int e) {
     return (bits >> 63) ? -sv : sv;
 }
 
-__global__ void __launch_bounds__(256) split_digits_kernel(const double* P, long long sr, long long sk, int R, int K,
-                                                           int shape, int Rp, int Kp, const int* expo,
-                                                           __nv_bfloat16* dig, long long sP) {
-    // blockIdx.z = matrix: digits of matrix z start at dig + z S Rp Kp.  The
-    // tile (SPLIT_ROWS x SPLIT_K) is staged through shared memory so that both
-    // the FP64 read and the bf16 write are coalesced for either stride order.
-    __shared__ double tile[SPLIT_ROWS][SPLIT_K + 1];
-    P += blockIdx.z * sP;
-    expo += (long long)blockIdx.z * Rp;
-    dig += (long long)blockIdx.z * S * Rp * Kp;
-    const int r0 = blockIdx.y * SPLIT_ROWS, k0 = blockIdx.x * SPLIT_K;
-    for (int e = threadIdx.x; e < SPLIT_ROWS * SPLIT_K; e += 256) {
+// Stages the SPLIT_ROWS x SPLIT_K tile of X at (r0, k0) in shared memory so
+// that the global reads are coalesced for either stride order.
+__device__ __forceinline__ void stage_tile(const SplitJob& J, const double* P, int r0, int k0,
+                                           double (*tile)[SPLIT_K + 1]) {
+    for (int e = threadIdx.x; e < SPLIT_ROWS * SPLIT_K; e += SPLIT_THREADS) {
         int rr, kk;
-        if (sr == 1) { rr = e % SPLIT_ROWS; kk = e / SPLIT_ROWS; } else { kk = e % SPLIT_K; rr = e / SPLIT_K; }
+        if (J.sr == 1) { rr = e % SPLIT_ROWS; kk = e / SPLIT_ROWS; } else { kk = e % SPLIT_K; rr = e / SPLIT_K; }
         const int r = r0 + rr, k = k0 + kk;
         double v = 0.0;
-        if (r < R && k < K && !(shape == 1 && k > r) && !(shape == 2 && k < r)) v = P[r * sr + k * sk];
+        if (r < J.R && k < J.K && !(J.shape == 1 && k > r) && !(J.shape == 2 && k < r)) v = P[r * J.sr + k * J.sk];
         tile[rr][kk] = v;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < SPLIT_ROWS * SPLIT_K; e += 256) {
-        const int kk = e % SPLIT_K, rr = e / SPLIT_K;
-        const int r = r0 + rr, k = k0 + kk;
-        if (r >= Rp || k >= Kp) continue;
-        long long V = (r < R) ? fixed_point35(tile[rr][kk], expo[r]) : 0;
-        int d[S];
+}
+
+// One CTA per (32-row block, matrix) of one or two operands (blockIdx.x runs
+// over the row blocks of job 0, then of job 1; blockIdx.y = matrix).  Pass 1
+// finds the largest exponent field of every row over all of K; pass 2 reads
+// the rows again (from L2) and writes the digits.
+__global__ void __launch_bounds__(SPLIT_THREADS) split_fused_kernel(SplitJob j0, SplitJob j1) {
+    __shared__ double tile[SPLIT_ROWS][SPLIT_K + 1];
+    __shared__ int row_exp[SPLIT_ROWS];
+    int rb = blockIdx.x;
+    const bool second = rb >= j0.row_blocks;
+    const SplitJob& J = second ? j1 : j0;
+    if (second) rb -= j0.row_blocks;
+    const int z = blockIdx.y;
+    const double* P = J.P + z * J.sP;
+    int* expo = J.expo + (long long)z * J.Rp;
+    __nv_bfloat16* dig = J.dig + (long long)z * S * J.Rp * J.Kp;
+    const int r0 = rb * SPLIT_ROWS;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    constexpr int ROWS_PER_WARP = SPLIT_ROWS / (SPLIT_THREADS / 32);
+    unsigned int emax[ROWS_PER_WARP];
 #pragma unroll
-        for (int s = S - 1; s >= 1; --s) {
-            int low = (int)(V & 127);          // V mod 128 in [0, 128)
-            if (low >= 64) low -= 128;         // balanced digit in [-64, 64)
-            d[s] = low;
-            V = (V - low) >> 7;                // exact: V - low is a multiple of 128
+    for (int q = 0; q < ROWS_PER_WARP; ++q) emax[q] = 0;
+    // ---- pass 1: row maxima of the exponent field
+    for (int k0 = 0; k0 < J.K; k0 += SPLIT_K) {
+        stage_tile(J, P, r0, k0, tile);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < ROWS_PER_WARP; ++q) {
+            const int rr = warp * ROWS_PER_WARP + q;
+#pragma unroll
+            for (int h = 0; h < SPLIT_K / 32; ++h) {
+                const unsigned long long bits = (unsigned long long)__double_as_longlong(tile[rr][lane + 32 * h]);
+                const unsigned int ef = (unsigned int)((bits >> 52) & 0x7FF);
+                emax[q] = max(emax[q], ef);
+            }
         }
-        d[0] = (int)V;                         // |d_0| <= 128
+        __syncthreads();
+    }
 #pragma unroll
-        for (int s = 0; s < S; ++s) dig[((size_t)s * Rp + r) * Kp + k] = __int2bfloat16_rn(d[s]);
+    for (int q = 0; q < ROWS_PER_WARP; ++q) {
+        unsigned int m = emax[q];
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            const int rr = warp * ROWS_PER_WARP + q;
+            // |x| < 2^(ef - 1023 + 1) for a normal number with exponent field ef;
+            // a NaN or Inf in the row gives a huge exponent, so the product
+            // overflows to a non-finite value instead of passing silently
+            const int e = m == 0 ? 0 : (m == 0x7FF ? 4096 : (int)m - 1023 + 1);
+            row_exp[rr] = e;
+            if (r0 + rr < J.Rp) expo[r0 + rr] = e;
+        }
+    }
+    __syncthreads();
+    // ---- pass 2: digits
+    for (int k0 = 0; k0 < J.Kp; k0 += SPLIT_K) {
+        stage_tile(J, P, r0, k0, tile);
+        __syncthreads();
+        for (int e = threadIdx.x; e < SPLIT_ROWS * SPLIT_K; e += SPLIT_THREADS) {
+            const int kk = e % SPLIT_K, rr = e / SPLIT_K;
+            const int r = r0 + rr, k = k0 + kk;
+            if (r >= J.Rp || k >= J.Kp) continue;
+            long long V = (r < J.R) ? fixed_point35(tile[rr][kk], row_exp[rr]) : 0;
+            int d[S];
+#pragma unroll
+            for (int sl = S - 1; sl >= 1; --sl) {
+                int low = (int)(V & 127);          // V mod 128 in [0, 128)
+                if (low >= 64) low -= 128;         // balanced digit in [-64, 64)
+                d[sl] = low;
+                V = (V - low) >> 7;                // exact: V - low is a multiple of 128
+            }
+            d[0] = (int)V;                         // |d_0| <= 128
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl) dig[((size_t)sl * J.Rp + r) * J.Kp + k] = __int2bfloat16_rn(d[sl]);
+        }
+        __syncthreads();
     }
 }
 
@@ -725,24 +758,24 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     const long long srB = g.tb ? 1 : g.ldb, skB = g.tb ? g.ldb : 1;
     // shape of op(B)^T: lower op(B) (zero for j > k) is upper in op(B)^T
     const int shBt = g.shB == 1 ? 2 : (g.shB == 2 ? 1 : 0);
-    row_maxexp_kernel<<<dim3((Mp + 7) / 8, nb), 256, 0, s>>>(g.A, srA, skA, g.M, g.K, g.shA, Mp, expA, g.sA);
+    // op(B)^T = op(A) (A B^T or A^T A shapes on one matrix): one split serves both
+    const bool same = g.A == g.B && g.sA == g.sB && g.M == g.N && srA == srB && skA == skB && g.shA == shBt;
+    SplitJob ja{g.A, srA, skA, g.sA, g.M, g.K, g.shA, Mp, Kp, expA, digA, Mp / SPLIT_ROWS};
+    SplitJob jb{g.B, srB, skB, g.sB, g.N, g.K, shBt, Np, Kp, expB, digB, Np / SPLIT_ROWS};
+    split_fused_kernel<<<dim3(ja.row_blocks + (same ? 0 : jb.row_blocks), nb), SPLIT_THREADS, 0, s>>>(ja, jb);
     BTA_LAUNCH_CHECK();
-    row_maxexp_kernel<<<dim3((Np + 7) / 8, nb), 256, 0, s>>>(g.B, srB, skB, g.N, g.K, shBt, Np, expB, g.sB);
-    BTA_LAUNCH_CHECK();
-    split_digits_kernel<<<dim3(Kp / SPLIT_K, Mp / SPLIT_ROWS, nb), 256, 0, s>>>(g.A, srA, skA, g.M, g.K, g.shA,
-                                                                               Mp, Kp, expA, digA, g.sA);
-    BTA_LAUNCH_CHECK();
-    split_digits_kernel<<<dim3(Kp / SPLIT_K, Np / SPLIT_ROWS, nb), 256, 0, s>>>(g.B, srB, skB, g.N, g.K, shBt,
-                                                                               Np, Kp, expB, digB, g.sB);
-    BTA_LAUNCH_CHECK();
+    // digit rows per slice of the B operand as the GEMM kernel reads them
+    const int NpB = same ? Mp : Np;
+    const __nv_bfloat16* digBr = same ? digA : digB;
+    const int* expBr = same ? expA : expB;
     CUtensorMap mA, mB;
     BTA_TRY(make_map(&mA, digA, nb * S * Mp, Kp, TM));
-    BTA_TRY(make_map(&mB, digB, nb * S * Np, Kp, TN));
+    BTA_TRY(make_map(&mB, digBr, nb * S * NpB, Kp, TN));
     const bool inplace = (g.Cin == g.C && g.ldci == g.ldc && g.beta == 1.0 && g.sCi == g.sC);
     Args a{};
     a.M = g.M; a.N = g.N; a.sC = g.sC;
-    a.Mp = Mp; a.Np = Np; a.kblocks = Kp / TK;
-    a.gm = Mp / TM; a.gn = Np / TN;
+    a.Mp = Mp; a.Np = NpB; a.kblocks = Kp / TK;
+    a.gm = Mp / TM; a.gn = (g.N + TN - 1) / TN;
     if (g.lowerC) {
         a.mcum[0] = 0;
         for (int m = 0; m < a.gm; ++m)
@@ -768,7 +801,7 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     a.ldci = g.ldci;
     a.sCi = g.sCi;
     a.beta = g.Cin ? g.beta : 0.0;
-    a.expA = expA; a.expB = expB;
+    a.expA = expA; a.expB = expBr;
     a.C = g.C; a.ldc = g.ldc; a.alpha = g.alpha;
     a.lowerC = g.lowerC;
     a.shA = g.shA;
