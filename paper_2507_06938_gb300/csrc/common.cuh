@@ -192,6 +192,9 @@ size_t ozaki_workspace_bytes(int M, int N, int K);
 // same contract as gemm64 (any batch); ws holds batch x ozaki_workspace_bytes
 int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err);
 int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
+// true when gemm_exec sends g to the split-precision path, whose operands are
+// read completely (digit split) before C is written: C may then alias A or B
+bool gemm_mixed_takes(const GemmExec* ex, const Gemm64& g);
 
 // ---------------------------------------------------------------- drivers on matrices m0 .. m0+count-1
 int factor_impl(bta_ctx_t ctx, int m0, int count, cudaStream_t s);

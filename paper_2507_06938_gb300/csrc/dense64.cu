@@ -584,8 +584,14 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
     g.B = X11; g.ldb = ldx; g.tb = 1; g.shB = 2;
     g.C = W; g.ldc = n2; g.alpha = 1.0; g.beta = 0.0;
     g.batch = batch; g.sA = sA; g.sB = sX; g.sC = sW;
-    BTA_TRY(gemm_exec(ex, s, g));
-    BTA_TRY(copy_mat64(s, W, n2, A21, lda, n2, n1, 0, batch, sW, sA));
+    if (gemm_mixed_takes(ex, g)) {
+        // the split-precision product reads A21 completely before writing: in place
+        g.C = A21; g.ldc = lda; g.sC = sA;
+        BTA_TRY(gemm_exec(ex, s, g));
+    } else {
+        BTA_TRY(gemm_exec(ex, s, g));
+        BTA_TRY(copy_mat64(s, W, n2, A21, lda, n2, n1, 0, batch, sW, sA));
+    }
     // A22 -= L21 L21^T  (lower)
     g = Gemm64{};
     g.M = n2; g.N = n2; g.K = n1;

@@ -12,8 +12,10 @@
 //   1/sqrt by one Newton-Raphson step in double-float from an FP32 seed,
 //   FP64 <-> double-float conversion on the bit patterns (one FP64 addition
 //   per stored element).
-// Both phases are right-looking with one barrier per step, so a step costs
-// one short chain of dependent operations per thread:
+// Both phases are right-looking with one barrier per step, and the updates of
+// a step are dealt to consecutive threads densely (an index table of the
+// lower triangle for phase 1, a rectangle for phase 2), so that warps issue
+// only useful work:
 // Phase 1: Cholesky.  Step k subtracts (a_ik / a_kk) a_jk from a_ij for
 //   k < j <= i; the thread that finishes a_{k+1,k+1} computes the next
 //   1/sqrt pivot at once; column k is scaled to L one step later (nobody
@@ -34,7 +36,7 @@ namespace {
 
 constexpr int DF_MAX = 128;
 constexpr int DF_LD = DF_MAX + 1;
-constexpr int DF_THREADS = 512;
+constexpr int DF_THREADS = 1024;
 
 struct df {
     float hi, lo;
@@ -128,9 +130,15 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
     float* Sl = smf + DF_LD * DF_MAX;
     float* yh = smf + 2 * DF_LD * DF_MAX;   // 1/L_kk (double-float)
     float* yl = yh + DF_MAX + 1;
+    // lower-triangle entries (i, j), i >= j, column by column: the entries with
+    // j > k (the trailing matrix of pivot k) are the suffix from colstart(k+1)
+    unsigned short* tri = reinterpret_cast<unsigned short*>(yl + DF_MAX + 1);
     A += blockIdx.x * sA;
     X += blockIdx.x * sX;
     const int tid = threadIdx.x;
+    auto colstart = [n](int j) { return j * n - j * (j - 1) / 2; };
+    for (int j = tid; j < n; j += DF_THREADS)
+        for (int i = j; i < n; ++i) tri[colstart(j) + i - j] = (unsigned short)((i << 8) | j);
     for (int e = tid; e < n * n; e += DF_THREADS) {
         const int i = e % n, j = e / n;
         const df v = (i >= j) ? df_from_double(A[i + (long long)j * lda]) : df{0.f, 0.f};
@@ -143,10 +151,6 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
         yh[0] = y.hi;
         yl[0] = y.lo;
     }
-    const int rows_per = n <= 32 ? 32 : (n <= 64 ? 64 : DF_MAX);
-    const int row = tid % rows_per;
-    const int q = tid / rows_per;
-    const int nq = DF_THREADS / rows_per;
     // ---------------------------------------------------------------- phase 1
     for (int k = 0; k <= n; ++k) {
         __syncthreads();
@@ -159,28 +163,35 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
                     status[2] = 2 * (mm % nbatch) + mm / nbatch;
                 }
             }
-            if (row > k && row < n) {
-                const df y2 = df_mul(y, y);
-                const df sik = df_mul(df{Sh[k * DF_LD + row], Sl[k * DF_LD + row]}, y2);
-                for (int j = k + 1 + q; j <= row; j += nq) {
-                    const df v = df_fnms(df{Sh[j * DF_LD + row], Sl[j * DF_LD + row]}, sik,
-                                         df{Sh[k * DF_LD + j], Sl[k * DF_LD + j]});
-                    Sh[j * DF_LD + row] = v.hi;
-                    Sl[j * DF_LD + row] = v.lo;
-                    if (j == k + 1 && row == k + 1) {   // the next pivot is final
-                        const df yn = df_rsqrt(v);
-                        yh[k + 1] = yn.hi;
-                        yl[k + 1] = yn.lo;
-                    }
+            const df y2 = df_mul(y, y);
+            const int base = colstart(k + 1);
+            const int count = (n - k - 1) * (n - k) / 2;
+            // the first entry of the suffix is the next pivot (k+1, k+1): thread 0
+            // updates it first and computes its 1/sqrt at once
+            for (int t = tid; t < count; t += DF_THREADS) {
+                const int ij = tri[base + t];
+                const int i = ij >> 8, j = ij & 255;
+                const df aik = df{Sh[k * DF_LD + i], Sl[k * DF_LD + i]};
+                const df ajk = df{Sh[k * DF_LD + j], Sl[k * DF_LD + j]};
+                const df v = df_fnms(df{Sh[j * DF_LD + i], Sl[j * DF_LD + i]}, df_mul(aik, y2), ajk);
+                Sh[j * DF_LD + i] = v.hi;
+                Sl[j * DF_LD + i] = v.lo;
+                if (t == 0) {
+                    const df yn = df_rsqrt(v);
+                    yh[k + 1] = yn.hi;
+                    yl[k + 1] = yn.lo;
                 }
             }
         }
-        if (k > 0 && q == 0 && row >= k - 1 && row < n) {
+        if (k > 0) {
             // column k-1 is complete: scale it to L (nobody reads it in this iteration)
             const int c = k - 1;
-            const df v = df_mul(df{Sh[c * DF_LD + row], Sl[c * DF_LD + row]}, df{yh[c], yl[c]});
-            Sh[c * DF_LD + row] = v.hi;
-            Sl[c * DF_LD + row] = v.lo;
+            const int rowc = c + (DF_THREADS - 1 - tid);   // the last threads, least loaded above
+            if (rowc < n && tid >= DF_THREADS - (n - c)) {
+                const df v = df_mul(df{Sh[c * DF_LD + rowc], Sl[c * DF_LD + rowc]}, df{yh[c], yl[c]});
+                Sh[c * DF_LD + rowc] = v.hi;
+                Sl[c * DF_LD + rowc] = v.lo;
+            }
         }
     }
     __syncthreads();
@@ -190,22 +201,22 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
     }
     // ---------------------------------------------------------------- phase 2
     // B(r, j) (r > j) at M[j][r]; zero from the load (the strict upper
-    // triangle of the input is never read).  Step i: X(i, j) = B(i, j) y_i is
-    // final for j < i (written by the last update of row i), X(i, i) = y_i.
+    // triangle of the input is never read).  Step i updates the (n-1-i) x (i+1)
+    // rectangle r > i, j <= i; X(i, j) = B(i, j) y_i is final for j < i
+    // (written by the last update of row i), X(i, i) = y_i.
     for (int i = 0; i < n - 1; ++i) {
         __syncthreads();
-        const int r = row;
-        if (r > i && r < n) {
+        const int R = n - 1 - i;
+        const int count = R * (i + 1);
+        for (int t = tid; t < count; t += DF_THREADS) {
+            const int j = t / R;
+            const int r = i + 1 + (t - j * R);
             const df lri = df{Sh[i * DF_LD + r], Sl[i * DF_LD + r]};
-            const bool finish = (r == i + 1);
-            const df yr = finish ? df{yh[r], yl[r]} : df{0.f, 0.f};
-            for (int j = q; j <= i; j += nq) {
-                const df xij = (j == i) ? df{yh[i], yl[i]} : df{Sh[i * DF_LD + j], Sl[i * DF_LD + j]};
-                df b = df_fnms(df{Sh[r * DF_LD + j], Sl[r * DF_LD + j]}, lri, xij);
-                if (finish) b = df_mul(b, yr);   // row r is final after this step
-                Sh[r * DF_LD + j] = b.hi;
-                Sl[r * DF_LD + j] = b.lo;
-            }
+            const df xij = (j == i) ? df{yh[i], yl[i]} : df{Sh[i * DF_LD + j], Sl[i * DF_LD + j]};
+            df b = df_fnms(df{Sh[r * DF_LD + j], Sl[r * DF_LD + j]}, lri, xij);
+            if (r == i + 1) b = df_mul(b, df{yh[r], yl[r]});   // row r is final after this step
+            Sh[r * DF_LD + j] = b.hi;
+            Sl[r * DF_LD + j] = b.lo;
         }
     }
     __syncthreads();
@@ -221,8 +232,9 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
 }  // namespace
 
 size_t chol_inv_df32_smem_bytes() {
-    // M (hi, lo), y (hi, lo)
-    return (2 * (size_t)DF_LD * DF_MAX + 2 * (DF_MAX + 1)) * sizeof(float);
+    // M (hi, lo), y (hi, lo), lower-triangle index table
+    return (2 * (size_t)DF_LD * DF_MAX + 2 * (DF_MAX + 1)) * sizeof(float) +
+           (size_t)DF_MAX * (DF_MAX + 1) / 2 * sizeof(unsigned short);
 }
 
 int chol_inv_df32_launch(cudaStream_t s, double* A, long long lda, long long sA, double* X, long long ldx,

@@ -586,6 +586,38 @@ __device__ __forceinline__ long long fixed_point35(double x, int e) {
     return (bits >> 63) ? -sv : sv;
 }
 
+// bf16 bit pattern of a small integer d (|d| <= 256, exact): d as FP32 by
+// the 1.5 * 2^23 offset (exact for |d| < 2^22), then the upper half.
+__device__ __forceinline__ uint32_t small_int_bf16(int d) {
+    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+    return __float_as_uint(f) >> 16;
+}
+
+// The five balanced base-128 digits of V (|V| < 2^35) as bf16 bit patterns,
+// most significant first: digits of |V| with 32-bit operations (the low 28
+// bits hold four digits, the top 7 bits plus the last carry the first), then
+// the sign of V on every digit.
+__device__ __forceinline__ void digits_bf16(long long V, uint32_t* out) {
+    const bool neg = V < 0;
+    const unsigned long long U = (unsigned long long)(neg ? -V : V);
+    unsigned int lo = (unsigned int)(U & 0xFFFFFFFull);
+    const unsigned int top = (unsigned int)(U >> 28);
+    int d[S];
+#pragma unroll
+    for (int sl = S - 1; sl >= 1; --sl) {
+        int r = (int)(lo & 127u);
+        lo >>= 7;
+        if (r >= 64) {          // balanced digit in [-64, 64), carry one into the rest
+            r -= 128;
+            lo += 1;
+        }
+        d[sl] = r;
+    }
+    d[0] = (int)(top + lo);     // lo is the final carry (0 or 1); |d_0| <= 128
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) out[sl] = small_int_bf16(neg ? -d[sl] : d[sl]);
+}
+
 // Stages the SPLIT_ROWS x SPLIT_K tile of X at (r0, k0) in shared memory so
 // that the global reads are coalesced for either stride order.
 __device__ __forceinline__ void stage_tile(const SplitJob& J, const double* P, int r0, int k0,
@@ -652,26 +684,20 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_fused_kernel(SplitJob j0,
         }
     }
     __syncthreads();
-    // ---- pass 2: digits
+    // ---- pass 2: digits, two consecutive k per thread (4-byte stores)
     for (int k0 = 0; k0 < J.Kp; k0 += SPLIT_K) {
         stage_tile(J, P, r0, k0, tile);
         __syncthreads();
-        for (int e = threadIdx.x; e < SPLIT_ROWS * SPLIT_K; e += SPLIT_THREADS) {
-            const int kk = e % SPLIT_K, rr = e / SPLIT_K;
+        for (int e = threadIdx.x; e < SPLIT_ROWS * SPLIT_K / 2; e += SPLIT_THREADS) {
+            const int kk = 2 * (e % (SPLIT_K / 2)), rr = e / (SPLIT_K / 2);
             const int r = r0 + rr, k = k0 + kk;
-            if (r >= J.Rp || k >= J.Kp) continue;
-            long long V = (r < J.R) ? fixed_point35(tile[rr][kk], row_exp[rr]) : 0;
-            int d[S];
+            if (r >= J.Rp || k >= J.Kp) continue;   // Kp is even: k + 1 < Kp as well
+            uint32_t d0[S], d1[S];
+            digits_bf16(r < J.R ? fixed_point35(tile[rr][kk], row_exp[rr]) : 0, d0);
+            digits_bf16(r < J.R ? fixed_point35(tile[rr][kk + 1], row_exp[rr]) : 0, d1);
 #pragma unroll
-            for (int sl = S - 1; sl >= 1; --sl) {
-                int low = (int)(V & 127);          // V mod 128 in [0, 128)
-                if (low >= 64) low -= 128;         // balanced digit in [-64, 64)
-                d[sl] = low;
-                V = (V - low) >> 7;                // exact: V - low is a multiple of 128
-            }
-            d[0] = (int)V;                         // |d_0| <= 128
-#pragma unroll
-            for (int sl = 0; sl < S; ++sl) dig[((size_t)sl * J.Rp + r) * J.Kp + k] = __int2bfloat16_rn(d[sl]);
+            for (int sl = 0; sl < S; ++sl)
+                *reinterpret_cast<uint32_t*>(dig + ((size_t)sl * J.Rp + r) * J.Kp + k) = d0[sl] | (d1[sl] << 16);
         }
         __syncthreads();
     }
@@ -824,9 +850,12 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
 // updates of the selected inversion, is padded to one 64-wide K block), the
 // rest (arrow, tip, small panels of the recursive diagonal factorisation)
 // stay on the FP64 pipe.
+bool gemm_mixed_takes(const GemmExec* ex, const Gemm64& g) {
+    return ex && ex->fn == gemm_mixed_fn && g.M >= ex->min_dim && g.N >= ex->min_dim && g.K >= 1 &&
+           g.M <= ozaki_max_rows() && (size_t)g.batch * ozaki_workspace_bytes(g.M, g.N, g.K) <= ex->ws_bytes;
+}
+
 int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
-    if (g.M >= ex->min_dim && g.N >= ex->min_dim && g.K >= 1 && g.M <= ozaki_max_rows() &&
-        (size_t)g.batch * ozaki_workspace_bytes(g.M, g.N, g.K) <= ex->ws_bytes)
-        return ozaki_gemm(s, g, ex->ws, ex->err);
+    if (gemm_mixed_takes(ex, g)) return ozaki_gemm(s, g, ex->ws, ex->err);
     return gemm64(s, g);
 }
