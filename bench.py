@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--config", default=CONFIG_NAME)
     ap.add_argument("--batch", type=int, default=0, help="theta points per step (default 2 dim(theta) + 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the FP64 comparison run of the mixed-precision bench")
     return ap.parse_args()
@@ -190,6 +191,22 @@ def thetas_for(problem, count, rank):
     return [stencil(problem.theta0 + 0.02 * rng.standard_normal(problem.theta0.shape)) for _ in range(count)]
 
 
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of per-rank timings (the job's time is the slowest
+    rank's); identity without a process group."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_throughput(steps, world, batch, ms):
+    """Evaluations per second of the whole job: every rank evaluates its own
+    `batch` theta points per step (weak scaling), over the slowest rank's time."""
+    return steps * world * batch / (ms / 1e3)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -263,6 +280,7 @@ def measure(args, precision_name, warmup, steps, with_e2e, dist, rank, world, lo
     stream = torch.cuda.Stream()
     model = bta.BtaModel(p)
     ctx = bta.BtaContext(p.nt, p.b, p.a, precision, stream, B)
+    tuned = None if args.no_autotune else ctx.autotune(reps=2)
     nsteps = warmup + steps
     thetas_h = np.stack([t[:B] if t.shape[0] >= B else np.resize(t, (B, t.shape[1]))
                          for t in thetas_for(p, nsteps, rank)])          # steps x B x dim
@@ -280,7 +298,7 @@ def measure(args, precision_name, warmup, steps, with_e2e, dist, rank, world, lo
             dist.barrier()
         torch.cuda.synchronize()
 
-    out = {"problem": p, "B": B, "thetas_h": thetas_h}
+    out = {"problem": p, "B": B, "thetas_h": thetas_h, "tuned": tuned}
     with torch.cuda.stream(stream):
         # the dominant GEMM launches carry timing events; the f_obj graph that
         # the timed steps replay is captured with them during the warm-up
@@ -334,13 +352,10 @@ def measure(args, precision_name, warmup, steps, with_e2e, dist, rank, world, lo
     del thetas_d, f_d, g_d, var_d
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
-    t_local = torch.tensor([out["ms"], out["ms_e2e"] or 0.0], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    out["ms"], out["ms_e2e"] = float(t_local[0]), float(t_local[1])
+    out["ms"], out["ms_e2e"] = max_over_ranks([out["ms"], out["ms_e2e"] or 0.0], dist, "cuda")
     total_evals = steps * world * B
-    out["value"] = total_evals / (out["ms"] / 1e3)
-    out["e2e_value"] = total_evals / (out["ms_e2e"] / 1e3) if with_e2e else None
+    out["value"] = job_throughput(steps, world, B, out["ms"])
+    out["e2e_value"] = job_throughput(steps, world, B, out["ms_e2e"]) if with_e2e else None
     flops_eval = 2 * bta.bta_flops_factor(p.nt, p.b, p.a) + 2 * bta.bta_flops_selinv(p.nt, p.b, p.a)
     out["tflops"] = flops_eval * total_evals / (out["ms"] / 1e3) / 1e12
     out["roofline"] = _roofline(precision_name, *out["prof"])
@@ -390,6 +405,8 @@ def run_ours(args):
         "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": int(B * p.theta0.shape[0] * 8),
                 "d2h_bytes_per_step": int(B * (8 + p.theta0.shape[0] * 8 + p.N * 8))},
         "batch": B,
+        "autotuned": (None if r["tuned"] is None else
+                      dict(zip(("fp64_leaf", "df32_leaf", "tensor_min_dim"), r["tuned"]))),
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
     }

@@ -283,6 +283,21 @@ long long bta_launch_count(void);
 int bta_profile(bta_ctx_t ctx, int enable);
 int bta_profile_read(bta_ctx_t ctx, double* ms_total, long long* launches, double* flops_total);
 
+/* bta_autotune -- choose the launch shapes of the diagonal-block
+ * factorisation (the latency-bound chain of the block Cholesky, Section
+ * III-A) for this context's block order, precision and batch by timing
+ * candidates on the context's own storage: the FP64 leaf order (16, 32, 64),
+ * or in mixed precision the double-float leaf order (32, 64, 128) and the
+ * smallest product dimension sent to the tensor cores (128, 256).  Each
+ * candidate runs once untimed and `reps` (>= 1) times timed.  The chosen
+ * values are written to chosen[0..2] (host: leaf, double-float leaf, tensor
+ * threshold) and used by every later call on the context.  The first
+ * diagonal block of every matrix is overwritten with a synthetic SPD block:
+ * call it before assembling, or assemble again afterwards.  Synchronises the
+ * context's stream.  Errors: BTA_ERR_ARG (null pointers, reps < 1), CUDA
+ * errors. */
+int bta_autotune(bta_ctx_t ctx, int reps, int* chosen);
+
 /*
  * bta_chol_inv_noalloc -- allocation-free Cholesky factor and inverse of one
  * dense symmetric positive definite block.  The paper has no counterpart to

@@ -87,6 +87,7 @@ def lib():
         "bta_profile": (ip, [vp, ip]),
         "bta_profile_read": (ip, [vp, C.POINTER(dp), C.POINTER(C.c_longlong), C.POINTER(dp)]),
         "bta_chol_inv_noalloc": (ip, [vp, ip, ip, vp, ip, vp, vp]),
+        "bta_autotune": (ip, [vp, ip, C.POINTER(C.c_int)]),
         "bta_flops_factor": (dp, [ip, ip, ip]),
         "bta_flops_selinv": (dp, [ip, ip, ip]),
     }
@@ -106,7 +107,7 @@ def exported_symbols():
             "bta_strerror", "bta_flops_factor", "bta_flops_selinv", "bta_selinv_diag",
             "bta_launch_count", "bta_profile", "bta_profile_read", "bta_chol_inv_noalloc",
             "bta_create_batched", "bta_batch_size", "bta_factor_batch", "bta_selinv_batch",
-            "bta_last_error_matrix", "bta_fobj_grad"]
+            "bta_last_error_matrix", "bta_fobj_grad", "bta_autotune"]
 
 
 def _check(code: int, where: str):
@@ -251,6 +252,14 @@ class BtaContext:
 
     def selinv_diag(self, which: int, out):
         _check(lib().bta_selinv_diag(self.handle, which, _ptr(out)), "bta_selinv_diag")
+
+    def autotune(self, reps: int = 2):
+        """bta_autotune: time the diagonal-block launch-shape candidates on this
+        context's storage and keep the fastest; returns (leaf, df_leaf, tensor
+        threshold).  Overwrites the first diagonal block of every matrix."""
+        out = (C.c_int * 3)()
+        _check(lib().bta_autotune(self.handle, int(reps), out), "bta_autotune")
+        return int(out[0]), int(out[1]), int(out[2])
 
     def profile(self, enable: bool):
         _check(lib().bta_profile(self.handle, 1 if enable else 0), "bta_profile")

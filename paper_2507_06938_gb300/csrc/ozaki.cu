@@ -525,9 +525,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                         double* c = Cm + i + (long long)nn * a.ldc;
                         if (atomic) {
                             atomicAdd(c, v);
+                        } else if (beta == 0.0) {
+                            *c = v;
                         } else {
-                            const double base = (beta == 1.0 || beta == 0.0) ? cv[jj] : beta * cv[jj];
-                            *c = base + v;
+                            *c = (beta == 1.0 ? cv[jj] : beta * cv[jj]) + v;
                         }
                     }
                 }

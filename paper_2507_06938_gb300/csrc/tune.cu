@@ -1,0 +1,96 @@
+// Autotuning of the launch shapes of the diagonal-block factorisation, the
+// latency-bound chain of the BTA Cholesky (one batched Cholesky + inverse of
+// a b x b block per time step).  For the context's shape, precision and
+// batch, every candidate setting is timed on the context's own storage and
+// the fastest one is kept:
+//   FP64:   the leaf order of the recursive Cholesky + inverse (16, 32, 64)
+//   mixed:  the double-float leaf order (32, 64, 128) x the smallest product
+//           dimension sent to the tensor cores (128, 256)
+// The timed matrices are synthetic SPD blocks written into the first
+// diagonal block of every matrix of the context (its contents are lost).
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+// A_ij = 2 delta_ij + 1 / ((1 + |i - j|) n): diagonally dominant, SPD.
+__global__ void fill_spd_kernel(double* A, int n, long long lda, long long sA) {
+    A += blockIdx.y * sA;
+    const int j = blockIdx.x;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        A[i + (long long)j * lda] = (i == j ? 2.0 : 0.0) + 1.0 / ((1.0 + abs(i - j)) * n);
+}
+
+}  // namespace
+
+extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
+    if (!ctx || !chosen || reps < 1) return BTA_ERR_ARG;
+    const int b = ctx->b, nm = ctx->nmat;
+    cudaStream_t s = ctx->stream;
+    // the storage is about to be overwritten: nothing stays factored, and a
+    // captured f_obj graph would carry the old launch shapes
+    if (ctx->fobj_graph) {
+        cudaStreamSynchronize(s);
+        cudaGraphExecDestroy(ctx->fobj_graph);
+        ctx->fobj_graph = nullptr;
+        ctx->graph_calls = 1;
+    }
+    std::fill(ctx->factored.begin(), ctx->factored.end(), 0);
+    fill_spd_kernel<<<dim3(b, nm), 256, 0, s>>>(ctx->Q.D, b, b, ctx->Q.sD);
+    BTA_LAUNCH_CHECK();
+
+    struct Cand {
+        int leaf, df_leaf, min_dim;
+    };
+    std::vector<Cand> cands;
+    if (ctx->precision == BTA_MIXED) {
+        for (int dl : {32, 64, 128})
+            for (int md : {128, 256}) cands.push_back({ctx->leaf, dl, md});
+    } else {
+        for (int lf : {16, 32, 64}) cands.push_back({lf, ctx->exec.df_leaf, ctx->exec.min_dim});
+    }
+    cudaEvent_t e0, e1;
+    BTA_CUDA_TRY(cudaEventCreate(&e0));
+    BTA_CUDA_TRY(cudaEventCreate(&e1));
+    auto run = [&](const Cand& c) -> int {
+        ctx->leaf = c.leaf;
+        ctx->exec.df_leaf = c.df_leaf;
+        ctx->exec.min_dim = c.min_dim;
+        BTA_TRY(copy_mat64(s, ctx->Q.D, b, ctx->L.D, b, b, b, 1, nm, ctx->Q.sD, ctx->L.sD));
+        return chol_inv64(s, ctx->L.D, b, ctx->Linv, b, b, 0, ctx->status, ctx->work, c.leaf, &ctx->exec, nm,
+                          ctx->L.sD, ctx->sLinv, ctx->sWork, 0, ctx->batch);
+    };
+    float best = -1.f;
+    Cand pick = cands[0];
+    int rc = BTA_OK;
+    for (const Cand& c : cands) {
+        if ((rc = run(c)) != BTA_OK) break;   // warm-up (first use of each launch shape)
+        if (cudaEventRecord(e0, s) != cudaSuccess) { rc = BTA_ERR_CUDA; break; }
+        for (int r = 0; r < reps && rc == BTA_OK; ++r) rc = run(c);
+        if (rc != BTA_OK) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = BTA_ERR_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best < 0.f || ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->leaf = pick.leaf;
+    ctx->exec.df_leaf = pick.df_leaf;
+    ctx->exec.min_dim = pick.min_dim;
+    if (rc != BTA_OK) return rc;
+    BTA_TRY(bta_sync(ctx));
+    chosen[0] = pick.leaf;
+    chosen[1] = pick.df_leaf;
+    chosen[2] = pick.min_dim;
+    return BTA_OK;
+}

@@ -111,3 +111,29 @@ def test_double_float_leaf(b):
         ctx.sync()
     assert e.value.code == bta.BTA_ERR_NOT_PD
     assert e.value.info <= b // 2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotune_keeps_results_exact(precision):
+    """The autotuner only changes launch shapes: after it runs, f_obj and the
+    conditional mean still match the oracle at the bounds of the precision."""
+    import torch
+    from gpu_util import GpuRun, dev, problem, rel_max
+    from oracle import fobj as ofobj
+    p = problem("t_uni_mid")
+    run = GpuRun(p, precision=precision, batch=2)
+    leaf, df_leaf, tmin = run.ctx.autotune(reps=1)
+    if precision == 0:
+        assert leaf in (16, 32, 64)
+    else:
+        assert df_leaf in (32, 64, 128) and tmin in (128, 256)
+    th = np.stack([p.theta0, p.theta0 + 1e-3])
+    f = torch.zeros(2, dtype=torch.float64, device="cuda")
+    mu = torch.zeros((2, p.N), dtype=torch.float64, device="cuda")
+    run.ctx.fobj_eval(run.model, dev(th), f, mu)
+    run.ctx.sync()
+    for j in range(2):
+        terms = ofobj.f_obj_terms(p, th[j])
+        tol = 1e-9 * abs(terms["f"]) if precision == 0 else 1e-8 * (abs(terms["logdet_p"]) + abs(terms["logdet_c"]))
+        assert abs(f[j].item() - terms["f"]) <= tol
+        assert rel_max(mu[j].cpu().numpy(), terms["mu"]) < 1e-8
