@@ -55,7 +55,7 @@ namespace oz {
 
 constexpr int S = 5;                      // digit slices = accumulated levels
 constexpr int TM = 128, TN = 96, TK = 32; // output tile; K block (64-byte rows)
-constexpr int STAGES = 3;
+constexpr int STAGES = 2;
 constexpr int KB_PER_CHUNK = 512 / TK;    // exactness bound of the level-2 accumulation
 constexpr int EPI_WARPS = 16;            // 4 per TMEM lane quarter
 constexpr int EPI_COLS = TN / (EPI_WARPS / 4);   // 24 columns per epilogue thread
@@ -64,7 +64,9 @@ constexpr uint32_t TMEM_COLS = 512;       // S * TN = 480 used
 constexpr uint32_t A_SLICE_BYTES = TM * TK * 2;                       // 8 KB
 constexpr uint32_t B_SLICE_BYTES = TN * TK * 2;                       // 6 KB
 constexpr uint32_t STAGE_BYTES = S * (A_SLICE_BYTES + B_SLICE_BYTES); // 70 KB
-constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + STAGES * STAGE_BYTES + 256;
+// per epilogue warp, two 32-row x 8-column FP64 buffers for the bulk reduce-add of C
+constexpr uint32_t CBUF_BYTES = 2 * 8 * 32 * 8;
+constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + STAGES * STAGE_BYTES + EPI_WARPS * CBUF_BYTES + 256;
 constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;   // about 2 s
 constexpr int PAD_M = TM, PAD_N = TN, PAD_K = 64;        // digit array padding (PAD_K: split tile)
 constexpr int MAX_MT = 128;               // row tiles per matrix (M <= 16384)
@@ -93,6 +95,7 @@ struct Args {
     long long ldci, sCi;
     double beta;
     int inplace;         // Cin is C with beta = 1 (or the K split pre-initialised C)
+    int bulk;            // in-place accumulation through bulk reduce-add (C, ldc, sC 16-byte aligned)
     int mcum[MAX_MT + 1];// lowerC: tiles of row tiles 0..m-1
 };
 
@@ -294,7 +297,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                       const __grid_constant__ Args a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    double* cbuf = reinterpret_cast<double*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + EPI_WARPS * CBUF_BYTES);
     uint64_t* empty = full + STAGES;
     // accumulator hand-off: group A = levels 0, 1, 3, 4 (drained every second
     // chunk), group B = level 2 (drained every chunk)
@@ -496,7 +500,55 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!ok) break;
             // C update from registers (tensor memory is already free for the next unit)
             const int i = w.m0 + row;
-            if (i < a.M) {
+            const int rows_here = a.M - (w.m0 + quarter * 32);   // rows of this warp inside C
+            if (a.bulk && rows_here > 0 && (rows_here >= 32 || (rows_here & 1) == 0)) {
+                // C += v through the L2: v staged per 8 columns in shared memory,
+                // one bulk reduce-add (FP64) per column of 32 (or fewer, even) rows
+                const int ea = (i < a.M) ? a.expA[(long long)w.inst * a.Mp + i] - 14 : 0;
+                const int* expB = a.expB + (long long)w.inst * a.Np;
+                double* Cw = a.C + w.inst * a.sC + (w.m0 + quarter * 32);
+                const uint32_t bytes = (uint32_t)min(rows_here, 32) * 8u;
+                const bool neg = a.alpha == -1.0, unit_alpha = neg || a.alpha == 1.0;
+                double* wbuf = cbuf + (warp - 2) * (CBUF_BYTES / 8);
+#pragma unroll
+                for (int g = 0; g < EPI_COLS / 8; ++g) {
+                    double* bufg = wbuf + (g & 1) * 256;
+                    if (g >= 2) {
+                        // the bulk reads of the group issued two steps ago must be done
+                        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                        __syncwarp();
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int nn = w.n0 + colbase + g * 8 + jj;
+                        double v = 0.0;
+                        if (i < a.M && nn < a.N && !(a.lowerC && i < nn)) {
+                            const int e = ea + expB[nn];
+                            v = f2d_scaled(hi[g * 8 + jj], e) + f2d_scaled(lo[g * 8 + jj], e);
+                            if (!unit_alpha) v *= a.alpha;
+                            else if (neg) v = -v;
+                        }
+                        bufg[jj * 32 + lane] = v;
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) {
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) {
+                            const int nn = w.n0 + colbase + g * 8 + jj;
+                            if (nn < a.N)
+                                asm volatile(
+                                    "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;" ::"l"(
+                                        Cw + (long long)nn * a.ldc),
+                                    "r"(smem_u32(bufg + jj * 32)), "r"(bytes)
+                                    : "memory");
+                        }
+                        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    }
+                }
+                if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                __syncwarp();
+            } else if (i < a.M) {
                 const int ea = a.expA[(long long)w.inst * a.Mp + i] - 14;
                 const int* expB = a.expB + (long long)w.inst * a.Np;
                 double* Cm = a.C + w.inst * a.sC;
@@ -534,6 +586,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
             }
         }
+        // every bulk reduce-add of this warp has landed before the CTA exits
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        __syncwarp();
     }
     fence_before_sync();
     __syncthreads();
@@ -824,6 +879,12 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     if (ksplit > 1 && !inplace)
         BTA_TRY(scale_into64(s, g.M, g.N, g.Cin, g.ldci, g.beta, g.C, g.ldc, g.lowerC, nb, g.sCi, g.sC));
     a.inplace = (inplace || ksplit > 1) ? 1 : 0;
+    // in-place accumulation without a K split goes through bulk reduce-adds,
+    // which need 16-byte aligned column starts
+    a.bulk = (inplace && ksplit == 1 && (reinterpret_cast<uintptr_t>(g.C) & 15) == 0 && (g.ldc & 1) == 0 &&
+              (g.sC & 1) == 0)
+                 ? 1
+                 : 0;
     a.Cin = g.Cin;
     a.ldci = g.ldci;
     a.sCi = g.sCi;
