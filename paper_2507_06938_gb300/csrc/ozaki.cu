@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 // operations on the FP64 bit pattern are used (the FP64 pipe of GB300 is the
 // slow one).  Output: dig[s][r][k] (bf16, rows padded to Rp, K padded to Kp
 // with zeros) and exp[r] (0 for padding rows).
-constexpr int SPLIT_ROWS = 32, SPLIT_K = 64, SPLIT_THREADS = 256;
+constexpr int SPLIT_ROWS = 16, SPLIT_K = 64, SPLIT_THREADS = 256;
 
 struct SplitJob {
     const double* P;
@@ -674,25 +674,46 @@ __device__ __forceinline__ void digits_bf16(long long V, uint32_t* out) {
     for (int sl = 0; sl < S; ++sl) out[sl] = small_int_bf16(neg ? -d[sl] : d[sl]);
 }
 
-// Stages the SPLIT_ROWS x SPLIT_K tile of X at (r0, k0) in shared memory so
-// that the global reads are coalesced for either stride order.
-__device__ __forceinline__ void stage_tile(const SplitJob& J, const double* P, int r0, int k0,
-                                           double (*tile)[SPLIT_K + 1]) {
-    for (int e = threadIdx.x; e < SPLIT_ROWS * SPLIT_K; e += SPLIT_THREADS) {
+// Each thread moves a fixed set of SPLIT_ROWS x SPLIT_K / SPLIT_THREADS tile
+// entries; lanes run along the contiguous stored dimension so that the
+// global reads are coalesced for either stride order.
+constexpr int SPLIT_PER_THREAD = SPLIT_ROWS * SPLIT_K / SPLIT_THREADS;
+
+__device__ __forceinline__ void tile_coord(const SplitJob& J, int e, int& rr, int& kk) {
+    if (J.sr == 1) { rr = e % SPLIT_ROWS; kk = e / SPLIT_ROWS; } else { kk = e % SPLIT_K; rr = e / SPLIT_K; }
+}
+
+// Loads this thread's entries of the tile at (r0, k0) into registers.
+__device__ __forceinline__ void load_tile(const SplitJob& J, const double* P, int r0, int k0,
+                                          double (&v)[SPLIT_PER_THREAD]) {
+#pragma unroll
+    for (int q = 0; q < SPLIT_PER_THREAD; ++q) {
         int rr, kk;
-        if (J.sr == 1) { rr = e % SPLIT_ROWS; kk = e / SPLIT_ROWS; } else { kk = e % SPLIT_K; rr = e / SPLIT_K; }
+        tile_coord(J, threadIdx.x + q * SPLIT_THREADS, rr, kk);
         const int r = r0 + rr, k = k0 + kk;
-        double v = 0.0;
-        if (r < J.R && k < J.K && !(J.shape == 1 && k > r) && !(J.shape == 2 && k < r)) v = P[r * J.sr + k * J.sk];
-        tile[rr][kk] = v;
+        double x = 0.0;
+        if (r < J.R && k < J.K && !(J.shape == 1 && k > r) && !(J.shape == 2 && k < r)) x = P[r * J.sr + k * J.sk];
+        v[q] = x;
     }
 }
 
-// One CTA per (32-row block, matrix) of one or two operands (blockIdx.x runs
-// over the row blocks of job 0, then of job 1; blockIdx.y = matrix).  Pass 1
-// finds the largest exponent field of every row over all of K; pass 2 reads
-// the rows again (from L2) and writes the digits.
-__global__ void __launch_bounds__(SPLIT_THREADS) split_fused_kernel(SplitJob j0, SplitJob j1) {
+__device__ __forceinline__ void store_tile(const SplitJob& J, const double (&v)[SPLIT_PER_THREAD],
+                                           double (*tile)[SPLIT_K + 1]) {
+#pragma unroll
+    for (int q = 0; q < SPLIT_PER_THREAD; ++q) {
+        int rr, kk;
+        tile_coord(J, threadIdx.x + q * SPLIT_THREADS, rr, kk);
+        tile[rr][kk] = v[q];
+    }
+}
+
+// One CTA per (SPLIT_ROWS-row block, matrix) of one or two operands
+// (blockIdx.x runs over the row blocks of job 0, then of job 1; blockIdx.y =
+// matrix).  Pass 1 finds the largest exponent field of every row over all
+// of K; pass 2 reads the rows again (from L2) and writes the digits.  In both
+// passes the next tile is loaded into registers while the current one is
+// processed from shared memory.
+__global__ void __launch_bounds__(SPLIT_THREADS, 4) split_fused_kernel(SplitJob j0, SplitJob j1) {
     __shared__ double tile[SPLIT_ROWS][SPLIT_K + 1];
     __shared__ int row_exp[SPLIT_ROWS];
     int rb = blockIdx.x;
@@ -709,10 +730,13 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_fused_kernel(SplitJob j0,
     unsigned int emax[ROWS_PER_WARP];
 #pragma unroll
     for (int q = 0; q < ROWS_PER_WARP; ++q) emax[q] = 0;
+    double v[SPLIT_PER_THREAD];
     // ---- pass 1: row maxima of the exponent field
+    load_tile(J, P, r0, 0, v);
     for (int k0 = 0; k0 < J.K; k0 += SPLIT_K) {
-        stage_tile(J, P, r0, k0, tile);
+        store_tile(J, v, tile);
         __syncthreads();
+        if (k0 + SPLIT_K < J.K) load_tile(J, P, r0, k0 + SPLIT_K, v);   // in flight during the max
 #pragma unroll
         for (int q = 0; q < ROWS_PER_WARP; ++q) {
             const int rr = warp * ROWS_PER_WARP + q;
@@ -739,11 +763,13 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_fused_kernel(SplitJob j0,
             if (r0 + rr < J.Rp) expo[r0 + rr] = e;
         }
     }
-    __syncthreads();
     // ---- pass 2: digits, two consecutive k per thread (4-byte stores)
+    load_tile(J, P, r0, 0, v);
     for (int k0 = 0; k0 < J.Kp; k0 += SPLIT_K) {
-        stage_tile(J, P, r0, k0, tile);
+        __syncthreads();   // row_exp written; the previous tile's digits are done
+        store_tile(J, v, tile);
         __syncthreads();
+        if (k0 + SPLIT_K < J.Kp) load_tile(J, P, r0, k0 + SPLIT_K, v);   // in flight during the digits
         for (int e = threadIdx.x; e < SPLIT_ROWS * SPLIT_K / 2; e += SPLIT_THREADS) {
             const int kk = 2 * (e % (SPLIT_K / 2)), rr = e / (SPLIT_K / 2);
             const int r = r0 + rr, k = k0 + kk;
@@ -755,7 +781,6 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_fused_kernel(SplitJob j0,
             for (int sl = 0; sl < S; ++sl)
                 *reinterpret_cast<uint32_t*>(dig + ((size_t)sl * J.Rp + r) * J.Kp + k) = d0[sl] | (d1[sl] << 16);
         }
-        __syncthreads();
     }
 }
 
