@@ -128,6 +128,21 @@ extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch,
         c->exec.min_dim = min_dim;
         c->refine = 2;
     }
+    // side stream of the diagonal-block recursion (products off its critical
+    // path), with a digit workspace of its own in mixed precision
+    c->fork = new CholFork();
+    if (cudaStreamCreateWithFlags(&c->fork->s2, cudaStreamNonBlocking) != cudaSuccess) return fail(BTA_ERR_CUDA);
+    for (int k = 0; k < 2 * CHOL_FORK_DEPTH; ++k)
+        if (cudaEventCreateWithFlags(&c->fork->ev[k], cudaEventDisableTiming) != cudaSuccess)
+            return fail(BTA_ERR_CUDA);
+    c->fork->ex2 = c->exec;
+    if (precision == BTA_MIXED) {
+        c->fork->ex2.ws = nullptr;
+        if (cudaMalloc(&c->fork->ex2.ws, c->exec.ws_bytes) != cudaSuccess) {
+            c->fork->ex2.ws = nullptr;
+            return fail(BTA_ERR_OOM);
+        }
+    }
     if (const char* e = std::getenv("BTA_REFINE")) c->refine = std::atoi(e);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(BTA_ERR_CUDA);
     *out = c;
@@ -148,6 +163,15 @@ extern "C" int bta_destroy(bta_ctx_t c) {
     if (!c) return BTA_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->aux) cudaStreamSynchronize(c->aux);
+    if (c->fork) {
+        if (c->fork->s2) cudaStreamSynchronize(c->fork->s2);
+        for (int q = 0; q < 2 * CHOL_FORK_DEPTH; ++q)
+            if (c->fork->ev[q]) cudaEventDestroy(c->fork->ev[q]);
+        if (c->fork->s2) cudaStreamDestroy(c->fork->s2);
+        if (c->precision == BTA_MIXED && c->fork->ex2.ws) cudaFree(c->fork->ex2.ws);
+        delete c->fork;
+        c->fork = nullptr;
+    }
     store_free(c->Q);
     store_free(c->L);
     store_free(c->S);

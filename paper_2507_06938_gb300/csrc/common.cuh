@@ -83,6 +83,15 @@ struct GemmExec {
     int df_leaf = 0;   // > 0: diagonal leaves of this order in double-float (leaf_df32.cu)
 };
 
+// Side stream, events and executor for the products of the recursive
+// diagonal-block factorisation that lie off its critical path.
+constexpr int CHOL_FORK_DEPTH = 8;
+struct CholFork {
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev[2 * CHOL_FORK_DEPTH] = {};
+    GemmExec ex2{};   // the context's executor with a digit workspace of its own
+};
+
 // ---------------------------------------------------------------- BTA storage
 // `nmat` BTA matrices of one shape, matrix after matrix: the blocks of matrix
 // m start at D + m sD, B + m sB, R + m sR, T + m sT.
@@ -104,6 +113,7 @@ struct bta_ctx_s {
     long long N;
     cudaStream_t stream;
     cudaStream_t aux;        // second stream for a partial batch (Q_p beside Q_c)
+    CholFork* fork = nullptr;  // side stream of the diagonal-block recursion
     cudaEvent_t ev_fork, ev_join;
     BtaStore Q, L, S;
     double* Linv = nullptr;  // per matrix: n b^2, then a^2 (tip)
@@ -160,10 +170,15 @@ int gemm_exec(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
 // scratch W with stride sW).  status receives the first non-positive pivot:
 // row row0 + k of the matrix with storage index m_first + instance, reported
 // by its public index for a context of `nbatch` parameter slots.
+// With `fork`, the product L21 X11 of every recursion node (independent of
+// the factorisation of A22) runs on fork->s2 with its own digit workspace,
+// joined back before X21 is formed; the subtrees then need about n^2/3 of
+// scratch per matrix instead of n^2/4.
+struct CholFork;
 int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ldx, int n,
                long long row0, long long* status, double* W, int leaf, const GemmExec* ex = nullptr,
                int batch = 1, long long sA = 0, long long sX = 0, long long sW = 0, int m_first = 0,
-               int nbatch = 1);
+               int nbatch = 1, const CholFork* fork = nullptr, int depth = 0);
 // Double-float Cholesky + inverse of `batch` blocks of order n <= 128 (leaf_df32.cu).
 int chol_inv_df32_launch(cudaStream_t s, double* A, long long lda, long long sA, double* X, long long ldx,
                          long long sX, int n, long long row0, long long* status, int batch, int m_first,

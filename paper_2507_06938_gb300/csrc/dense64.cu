@@ -554,7 +554,7 @@ static int leaf_launch(cudaStream_t s, double* A, long long lda, long long sA, d
 //                 X21 = -X22 (L21 X11)
 int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ldx, int n, long long row0,
                long long* status, double* W, int leaf, const GemmExec* ex, int batch, long long sA,
-               long long sX, long long sW, int m_first, int nbatch) {
+               long long sX, long long sW, int m_first, int nbatch, const CholFork* fork, int depth) {
     if (n <= 0 || batch <= 0) return BTA_OK;
     if (ex && ex->df_leaf > 0) {
         // mixed precision: double-float leaves on the FP32 pipe
@@ -575,7 +575,12 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
     double* X11 = X;
     double* X21 = X + n1;
     double* X22 = X + n1 + n1 * ldx;
-    BTA_TRY(chol_inv64(s, A11, lda, X11, ldx, n1, row0, status, W, leaf, ex, batch, sA, sX, sW, m_first, nbatch));
+    // W (n2 x n1) belongs to this node while L21 X11 runs beside the subtree
+    // of A22; the subtrees then use the scratch after it
+    const bool forked = fork && fork->s2 && depth < CHOL_FORK_DEPTH;
+    double* Wc = forked ? W + (long long)n2 * n1 : W;
+    BTA_TRY(chol_inv64(s, A11, lda, X11, ldx, n1, row0, status, Wc, leaf, ex, batch, sA, sX, sW, m_first, nbatch,
+                       fork, depth + 1));
     Gemm64 g{};
     // W (n2 x n1) = A21 * X11^T      (op(B) upper)
     g = Gemm64{};
@@ -601,16 +606,27 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
     g.C = A22; g.ldc = lda; g.alpha = -1.0; g.lowerC = 1;
     g.batch = batch; g.sA = sA; g.sB = sA; g.sCi = sA; g.sC = sA;
     BTA_TRY(gemm_exec(ex, s, g));
-    BTA_TRY(chol_inv64(s, A22, lda, X22, ldx, n2, row0 + n1, status, W, leaf, ex, batch, sA, sX, sW, m_first,
-                       nbatch));
-    // W = L21 * X11   (op(B) lower)
+    // W = L21 * X11   (op(B) lower); independent of the factorisation of A22
     g = Gemm64{};
     g.M = n2; g.N = n1; g.K = n1;
     g.A = A21; g.lda = lda;
     g.B = X11; g.ldb = ldx; g.tb = 0; g.shB = 1;
     g.C = W; g.ldc = n2; g.alpha = 1.0; g.beta = 0.0;
     g.batch = batch; g.sA = sA; g.sB = sX; g.sC = sW;
-    BTA_TRY(gemm_exec(ex, s, g));
+    if (forked) {
+        cudaEvent_t ev_fork = fork->ev[2 * depth], ev_join = fork->ev[2 * depth + 1];
+        BTA_CUDA_TRY(cudaEventRecord(ev_fork, s));
+        BTA_CUDA_TRY(cudaStreamWaitEvent(fork->s2, ev_fork, 0));
+        BTA_TRY(gemm_exec(ex && ex->fn ? &fork->ex2 : ex, fork->s2, g));
+        BTA_CUDA_TRY(cudaEventRecord(ev_join, fork->s2));
+        BTA_TRY(chol_inv64(s, A22, lda, X22, ldx, n2, row0 + n1, status, Wc, leaf, ex, batch, sA, sX, sW, m_first,
+                           nbatch, fork, depth + 1));
+        BTA_CUDA_TRY(cudaStreamWaitEvent(s, ev_join, 0));
+    } else {
+        BTA_TRY(chol_inv64(s, A22, lda, X22, ldx, n2, row0 + n1, status, Wc, leaf, ex, batch, sA, sX, sW, m_first,
+                           nbatch));
+        BTA_TRY(gemm_exec(ex, s, g));
+    }
     // X21 = -X22 * W   (op(A) lower)
     g = Gemm64{};
     g.M = n2; g.N = n1; g.K = n2;

@@ -46,7 +46,7 @@ int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
         double* Di = LD + i * bb;
         double* Xi = Linv + i * bb;
         BTA_TRY(chol_inv64(s, Di, b, Xi, b, b, (long long)i * b, status, W, leaf, ex, cnt, L.sD, sX, sW, m0,
-                           ctx->batch));
+                           ctx->batch, ctx->fork));
         Gemm64 g{};
         if (i < n - 1) {
             // L_{i+1,i} = B_i X_i^T

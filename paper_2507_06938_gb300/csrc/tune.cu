@@ -59,9 +59,13 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
         ctx->leaf = c.leaf;
         ctx->exec.df_leaf = c.df_leaf;
         ctx->exec.min_dim = c.min_dim;
+        if (ctx->fork) {
+            ctx->fork->ex2.df_leaf = c.df_leaf;
+            ctx->fork->ex2.min_dim = c.min_dim;
+        }
         BTA_TRY(copy_mat64(s, ctx->Q.D, b, ctx->L.D, b, b, b, 1, nm, ctx->Q.sD, ctx->L.sD));
         return chol_inv64(s, ctx->L.D, b, ctx->Linv, b, b, 0, ctx->status, ctx->work, c.leaf, &ctx->exec, nm,
-                          ctx->L.sD, ctx->sLinv, ctx->sWork, 0, ctx->batch);
+                          ctx->L.sD, ctx->sLinv, ctx->sWork, 0, ctx->batch, ctx->fork);
     };
     float best = -1.f;
     Cand pick = cands[0];
@@ -87,6 +91,10 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
     ctx->leaf = pick.leaf;
     ctx->exec.df_leaf = pick.df_leaf;
     ctx->exec.min_dim = pick.min_dim;
+    if (ctx->fork) {
+        ctx->fork->ex2.df_leaf = pick.df_leaf;
+        ctx->fork->ex2.min_dim = pick.min_dim;
+    }
     if (rc != BTA_OK) return rc;
     BTA_TRY(bta_sync(ctx));
     chosen[0] = pick.leaf;
