@@ -135,6 +135,10 @@ extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch,
     for (int k = 0; k < 2 * CHOL_FORK_DEPTH; ++k)
         if (cudaEventCreateWithFlags(&c->fork->ev[k], cudaEventDisableTiming) != cudaSuccess)
             return fail(BTA_ERR_CUDA);
+    if (cudaStreamCreateWithFlags(&c->fork->s3, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork->ev3_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork->ev3_join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(BTA_ERR_CUDA);
     c->fork->ex2 = c->exec;
     if (precision == BTA_MIXED) {
         c->fork->ex2.ws = nullptr;
@@ -168,6 +172,12 @@ extern "C" int bta_destroy(bta_ctx_t c) {
         for (int q = 0; q < 2 * CHOL_FORK_DEPTH; ++q)
             if (c->fork->ev[q]) cudaEventDestroy(c->fork->ev[q]);
         if (c->fork->s2) cudaStreamDestroy(c->fork->s2);
+        if (c->fork->s3) {
+            cudaStreamSynchronize(c->fork->s3);
+            cudaStreamDestroy(c->fork->s3);
+        }
+        if (c->fork->ev3_fork) cudaEventDestroy(c->fork->ev3_fork);
+        if (c->fork->ev3_join) cudaEventDestroy(c->fork->ev3_join);
         if (c->precision == BTA_MIXED && c->fork->ex2.ws) cudaFree(c->fork->ex2.ws);
         delete c->fork;
         c->fork = nullptr;

@@ -90,6 +90,10 @@ struct CholFork {
     cudaStream_t s2 = nullptr;
     cudaEvent_t ev[2 * CHOL_FORK_DEPTH] = {};
     GemmExec ex2{};   // the context's executor with a digit workspace of its own
+    // third stream for the FP64 arrow products of the block recurrences,
+    // which are off the critical path of the diagonal chain
+    cudaStream_t s3 = nullptr;
+    cudaEvent_t ev3_fork = nullptr, ev3_join = nullptr;
 };
 
 // ---------------------------------------------------------------- BTA storage

@@ -73,6 +73,14 @@ int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
             if (stop) BTA_TRY(prof_record(stop, s));
         }
         if (a > 0) {
+            // the arrow products need X_i and L_{i+1,i} only, and nothing on the
+            // diagonal chain needs them: they run on the third stream
+            cudaStream_t as = s;
+            if (ctx->fork && ctx->fork->s3) {
+                as = ctx->fork->s3;
+                BTA_CUDA_TRY(cudaEventRecord(ctx->fork->ev3_fork, s));
+                BTA_CUDA_TRY(cudaStreamWaitEvent(as, ctx->fork->ev3_fork, 0));
+            }
             double* Lri = LR + i * ab;
             // L_{t,i} = Racc X_i^T
             g = Gemm64{};
@@ -81,7 +89,7 @@ int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
             g.B = Xi; g.ldb = b; g.tb = 1; g.shB = 2;
             g.C = Lri; g.ldc = a; g.alpha = 1.0;
             g.batch = cnt; g.sA = sW; g.sB = sX; g.sC = L.sR;
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm64(as, g));
             if (i < n - 1) {
                 // Racc = R_{i+1} - L_{t,i} L_{i+1,i}^T
                 g = Gemm64{};
@@ -91,7 +99,7 @@ int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
                 g.Cin = QR + (i + 1) * ab; g.ldci = a; g.beta = 1.0;
                 g.C = Racc; g.ldc = a; g.alpha = -1.0;
                 g.batch = cnt; g.sA = L.sR; g.sB = L.sB; g.sCi = Q.sR; g.sC = sW;
-                BTA_TRY(gemm64(s, g));
+                BTA_TRY(gemm64(as, g));
             }
             // T -= L_{t,i} L_{t,i}^T   (lower, FP64)
             g = Gemm64{};
@@ -101,8 +109,13 @@ int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
             g.Cin = LT; g.ldci = a; g.beta = 1.0;
             g.C = LT; g.ldc = a; g.alpha = -1.0; g.lowerC = 1;
             g.batch = cnt; g.sA = L.sR; g.sB = L.sR; g.sCi = L.sT; g.sC = L.sT;
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm64(as, g));
         }
+    }
+    if (a > 0 && ctx->fork && ctx->fork->s3) {
+        // join the arrow stream before the tip is factored
+        BTA_CUDA_TRY(cudaEventRecord(ctx->fork->ev3_join, ctx->fork->s3));
+        BTA_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fork->ev3_join, 0));
     }
     if (a > 0)
         BTA_TRY(chol_inv64(s, LT, a, Linv + (long long)n * bb, a, a, (long long)n * b, status, W, leaf, nullptr, cnt,

@@ -11,7 +11,8 @@
 //   Sigma_ii      = L_ii^{-T} L_ii^{-1} - Sigma_{i+1,i}^T G_i - Sigma_{t,i}^T F_i
 // for i = n-1 down to 0 (terms with index n are absent).  The products with a
 // b x b output go through the context's GEMM executor (tensor cores in mixed
-// precision); the arrow and tip products stay FP64.  Sigma_ii is computed on its lower
+// precision); the arrow and tip products stay FP64 and run on a third stream
+// (F_i one step ahead, Sigma_{t,i} beside the b x b product of its step).  Sigma_ii is computed on its lower
 // triangle and then mirrored.
 
 #include <algorithm>
@@ -32,11 +33,38 @@ int selinv_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
     const double* Linv = ctx->Linv + m0 * ctx->sLinv;
     const long long sX = ctx->sLinv, sW = ctx->sWork;
     double* G = ctx->work + m0 * ctx->sWork;   // b x b
-    double* F = G + bb;                        // a x b
+    double* Fb[2] = {G + bb, G + bb + ab};     // a x b, F_i in Fb[i & 1]
     const double* XT = Linv + n * bb;          // L_tt^{-1}
     const GemmExec* ex = &ctx->exec;
+    // the arrow products (F_i and Sigma_{t,i}) run on the third stream, one
+    // step ahead for F, beside the b x b products of the main stream
+    const bool side = a > 0 && ctx->fork && ctx->fork->s3;
+    cudaStream_t as = side ? ctx->fork->s3 : s;
+    auto fork = [&]() -> int {
+        if (!side) return BTA_OK;
+        BTA_CUDA_TRY(cudaEventRecord(ctx->fork->ev3_fork, s));
+        BTA_CUDA_TRY(cudaStreamWaitEvent(as, ctx->fork->ev3_fork, 0));
+        return BTA_OK;
+    };
+    auto join = [&]() -> int {
+        if (!side) return BTA_OK;
+        BTA_CUDA_TRY(cudaEventRecord(ctx->fork->ev3_join, as));
+        BTA_CUDA_TRY(cudaStreamWaitEvent(s, ctx->fork->ev3_join, 0));
+        return BTA_OK;
+    };
+    // F_i = L_{t,i} X_i
+    auto arrow_F = [&](int i, cudaStream_t st) -> int {
+        Gemm64 g{};
+        g.M = a; g.N = b; g.K = b;
+        g.A = LR + i * ab; g.lda = a;
+        g.B = Linv + i * bb; g.ldb = b; g.shB = 1;
+        g.C = Fb[i & 1]; g.ldc = a; g.alpha = 1.0;
+        g.batch = cnt; g.sA = L.sR; g.sB = sX; g.sC = sW;
+        return gemm64(st, g);
+    };
     Gemm64 g{};
     if (a > 0) {
+        // Sigma_tt = X_T^T X_T
         g = Gemm64{};
         g.M = a; g.N = a; g.K = a;
         g.A = XT; g.lda = a; g.ta = 1; g.shA = 2;
@@ -44,21 +72,14 @@ int selinv_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
         g.C = ST; g.ldc = a; g.alpha = 1.0;
         g.batch = cnt; g.sA = sX; g.sB = sX; g.sC = S.sT;
         BTA_TRY(gemm64(s, g));
+        BTA_TRY(fork());
+        BTA_TRY(arrow_F(n - 1, as));
     }
     for (int i = n - 1; i >= 0; --i) {
         const double* Xi = Linv + i * bb;
         double* SDi = SD + i * bb;
         double* SRi = SR + i * ab;
-        if (a > 0) {
-            // F = L_{t,i} X_i
-            g = Gemm64{};
-            g.M = a; g.N = b; g.K = b;
-            g.A = LR + i * ab; g.lda = a;
-            g.B = Xi; g.ldb = b; g.shB = 1;
-            g.C = F; g.ldc = a; g.alpha = 1.0;
-            g.batch = cnt; g.sA = L.sR; g.sB = sX; g.sC = sW;
-            BTA_TRY(gemm64(s, g));
-        }
+        double* F = Fb[i & 1];
         if (i < n - 1) {
             double* SBi = SB + i * bb;
             // G = L_{i+1,i} X_i
@@ -69,6 +90,26 @@ int selinv_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
             g.C = G; g.ldc = b; g.alpha = 1.0;
             g.batch = cnt; g.sA = L.sB; g.sB = sX; g.sC = sW;
             BTA_TRY(gemm_exec(ex, s, g));
+            if (a > 0) {
+                BTA_TRY(fork());
+                // Sigma_{t,i} = -Sigma_{t,i+1} G - Sigma_tt F      (third stream)
+                g = Gemm64{};
+                g.M = a; g.N = b; g.K = b;
+                g.A = SR + (i + 1) * ab; g.lda = a;
+                g.B = G; g.ldb = b;
+                g.C = SRi; g.ldc = a; g.alpha = -1.0;
+                g.batch = cnt; g.sA = S.sR; g.sB = sW; g.sC = S.sR;
+                BTA_TRY(gemm64(as, g));
+                g = Gemm64{};
+                g.M = a; g.N = b; g.K = a;
+                g.A = ST; g.lda = a;
+                g.B = F; g.ldb = a;
+                g.Cin = SRi; g.ldci = a; g.beta = 1.0;
+                g.C = SRi; g.ldc = a; g.alpha = -1.0;
+                g.batch = cnt; g.sA = S.sT; g.sB = sW; g.sCi = S.sR; g.sC = S.sR;
+                BTA_TRY(gemm64(as, g));
+                if (i > 0) BTA_TRY(arrow_F(i - 1, as));
+            }
             // Sigma_{i+1,i} = -Sigma_{i+1,i+1} G  (- Sigma_{t,i+1}^T F)
             g = Gemm64{};
             g.M = b; g.N = b; g.K = b;
@@ -78,6 +119,7 @@ int selinv_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
             g.batch = cnt; g.sA = S.sD; g.sB = sW; g.sC = S.sB;
             BTA_TRY(gemm_exec(ex, s, g));
             if (a > 0) {
+                // Sigma_{t,i+1} and F_i were made final by the previous step's join
                 g = Gemm64{};
                 g.M = b; g.N = b; g.K = a;
                 g.A = SR + (i + 1) * ab; g.lda = a; g.ta = 1;
@@ -86,32 +128,17 @@ int selinv_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
                 g.C = SBi; g.ldc = b; g.alpha = -1.0;
                 g.batch = cnt; g.sA = S.sR; g.sB = sW; g.sCi = S.sB; g.sC = S.sB;
                 BTA_TRY(gemm_exec(ex, s, g));
-                // Sigma_{t,i} = -Sigma_{t,i+1} G - Sigma_tt F
-                g = Gemm64{};
-                g.M = a; g.N = b; g.K = b;
-                g.A = SR + (i + 1) * ab; g.lda = a;
-                g.B = G; g.ldb = b;
-                g.C = SRi; g.ldc = a; g.alpha = -1.0;
-                g.batch = cnt; g.sA = S.sR; g.sB = sW; g.sC = S.sR;
-                BTA_TRY(gemm64(s, g));
-                g = Gemm64{};
-                g.M = a; g.N = b; g.K = a;
-                g.A = ST; g.lda = a;
-                g.B = F; g.ldb = a;
-                g.Cin = SRi; g.ldci = a; g.beta = 1.0;
-                g.C = SRi; g.ldc = a; g.alpha = -1.0;
-                g.batch = cnt; g.sA = S.sT; g.sB = sW; g.sCi = S.sR; g.sC = S.sR;
-                BTA_TRY(gemm64(s, g));
             }
         } else if (a > 0) {
-            // Sigma_{t,n-1} = -Sigma_tt F
+            // Sigma_{t,n-1} = -Sigma_tt F      (third stream, after F_{n-1})
             g = Gemm64{};
             g.M = a; g.N = b; g.K = a;
             g.A = ST; g.lda = a;
             g.B = F; g.ldb = a;
             g.C = SRi; g.ldc = a; g.alpha = -1.0;
             g.batch = cnt; g.sA = S.sT; g.sB = sW; g.sC = S.sR;
-            BTA_TRY(gemm64(s, g));
+            BTA_TRY(gemm64(as, g));
+            if (i > 0) BTA_TRY(arrow_F(i - 1, as));
         }
         // Sigma_ii = X_i^T X_i - Sigma_{i+1,i}^T G - Sigma_{t,i}^T F   (lower, then mirrored)
         g = Gemm64{};
@@ -132,6 +159,8 @@ int selinv_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
             BTA_TRY(gemm_exec(ex, s, g));
         }
         if (a > 0) {
+            // Sigma_{t,i} (and F_{i-1}) from the third stream
+            BTA_TRY(join());
             g = Gemm64{};
             g.M = b; g.N = b; g.K = a;
             g.A = SRi; g.lda = a; g.ta = 1;
