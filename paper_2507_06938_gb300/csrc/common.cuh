@@ -187,6 +187,8 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
 int chol_inv_df32_launch(cudaStream_t s, double* A, long long lda, long long sA, double* X, long long ldx,
                          long long sX, int n, long long row0, long long* status, int batch, int m_first,
                          int nbatch);
+// C = beta Cin + alpha op(A) op(B) in double-float on the FP32 pipe (leaf_df32.cu)
+int gemm_df32(cudaStream_t s, const Gemm64& g);
 int copy_mat64(cudaStream_t s, const double* src, long long lds, double* dst, long long ldd,
                int rows, int cols, int lower_only, int batch = 1, long long ss = 0, long long sd = 0);
 // C = beta Cin (C = 0 if beta == 0); only entries m >= n when lower

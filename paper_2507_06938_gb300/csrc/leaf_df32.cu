@@ -229,6 +229,111 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
     }
 }
 
+// ------------------------------------------------------------------ GEMM
+// C = beta Cin + alpha op(A) op(B) in double-float on the FP32 pipe, for the
+// small products of the recursive diagonal-block factorisation in the mixed
+// path (orders below the tensor-core threshold): no digit split, about 48
+// significand bits.  Tile (16 TI) x (16 TI) per CTA of 256 threads, TI x TI
+// outputs per thread; K tiles of 16 staged in shared memory as hi/lo pairs.
+// Triangular operand shapes, lower output and batching as in the FP64 GEMM.
+constexpr int DG_BK = 16, DG_T = 256;
+
+__device__ __forceinline__ double dg_loadA(const Gemm64& p, const double* A, int m, int k, int kend) {
+    if (m >= p.M || k >= kend) return 0.0;
+    if (p.shA == 1 && k > m) return 0.0;
+    if (p.shA == 2 && k < m) return 0.0;
+    return p.ta ? A[k + (long long)m * p.lda] : A[m + (long long)k * p.lda];
+}
+
+__device__ __forceinline__ double dg_loadB(const Gemm64& p, const double* B, int k, int nn, int kend) {
+    if (nn >= p.N || k >= kend) return 0.0;
+    if (p.shB == 1 && nn > k) return 0.0;
+    if (p.shB == 2 && nn < k) return 0.0;
+    return p.tb ? B[nn + (long long)k * p.ldb] : B[k + (long long)nn * p.ldb];
+}
+
+// acc + a b with a, b double-float (error-free product of the high words,
+// first-order cross terms, TwoSum into the accumulator)
+__device__ __forceinline__ df df_fma(df acc, df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    float t = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    t = __fadd_rn(t, __fadd_rn(acc.lo, e));
+    const float h = __fadd_rn(s, t);
+    return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+
+template <int TI>
+__global__ void __launch_bounds__(DG_T) gemm_df32_kernel(Gemm64 p) {
+    constexpr int TB = 16 * TI;
+    __shared__ float Ah[DG_BK][TB + 1], Al[DG_BK][TB + 1], Bh[DG_BK][TB + 1], Bl[DG_BK][TB + 1];
+    const int m0 = blockIdx.x * TB, n0 = blockIdx.y * TB, z = blockIdx.z;
+    if (p.lowerC && m0 + TB - 1 < n0) return;
+    const double* A = p.A + z * p.sA;
+    const double* B = p.B + z * p.sB;
+    const double* Cin = p.Cin ? p.Cin + z * p.sCi : nullptr;
+    double* C = p.C + z * p.sC;
+    int kb = 0, ke = p.K;
+    if (p.shA == 1) ke = min(ke, m0 + TB);
+    if (p.shA == 2) kb = max(kb, m0);
+    if (p.shB == 1) kb = max(kb, n0);
+    if (p.shB == 2) ke = min(ke, n0 + TB);
+    kb = (kb / DG_BK) * DG_BK;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    df acc[TI][TI];
+#pragma unroll
+    for (int i = 0; i < TI; ++i)
+#pragma unroll
+        for (int j = 0; j < TI; ++j) acc[i][j] = df{0.f, 0.f};
+    for (int k0 = kb; k0 < ke; k0 += DG_BK) {
+        for (int e = tid; e < TB * DG_BK; e += DG_T) {
+            int mm, kk;
+            if (!p.ta) { mm = e % TB; kk = e / TB; } else { kk = e % DG_BK; mm = e / DG_BK; }
+            const df v = df_from_double(dg_loadA(p, A, m0 + mm, k0 + kk, ke));
+            Ah[kk][mm] = v.hi;
+            Al[kk][mm] = v.lo;
+        }
+        for (int e = tid; e < TB * DG_BK; e += DG_T) {
+            int nn, kk;
+            if (!p.tb) { kk = e % DG_BK; nn = e / DG_BK; } else { nn = e % TB; kk = e / TB; }
+            const df v = df_from_double(dg_loadB(p, B, k0 + kk, n0 + nn, ke));
+            Bh[kk][nn] = v.hi;
+            Bl[kk][nn] = v.lo;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < DG_BK; ++kk) {
+            df a[TI], b[TI];
+#pragma unroll
+            for (int i = 0; i < TI; ++i) a[i] = df{Ah[kk][tx + 16 * i], Al[kk][tx + 16 * i]};
+#pragma unroll
+            for (int j = 0; j < TI; ++j) b[j] = df{Bh[kk][ty + 16 * j], Bl[kk][ty + 16 * j]};
+#pragma unroll
+            for (int i = 0; i < TI; ++i)
+#pragma unroll
+                for (int j = 0; j < TI; ++j) acc[i][j] = df_fma(acc[i][j], a[i], b[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < TI; ++j) {
+        const int nn = n0 + ty + 16 * j;
+        if (nn >= p.N) continue;
+#pragma unroll
+        for (int i = 0; i < TI; ++i) {
+            const int mm = m0 + tx + 16 * i;
+            if (mm >= p.M || (p.lowerC && mm < nn)) continue;
+            double v = p.alpha * df_to_double(acc[i][j]);
+            if (p.beta != 0.0) v += p.beta * Cin[mm + (long long)nn * p.ldci];
+            C[mm + (long long)nn * p.ldc] = v;
+        }
+    }
+}
+
 }  // namespace
 
 size_t chol_inv_df32_smem_bytes() {
@@ -249,6 +354,23 @@ int chol_inv_df32_launch(cudaStream_t s, double* A, long long lda, long long sA,
         attr_set = true;
     }
     chol_inv_df32_kernel<<<batch, DF_THREADS, smem, s>>>(A, lda, sA, X, ldx, sX, n, row0, status, m_first, nbatch);
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}
+
+// Double-float GEMM (same contract as gemm64, any batch <= 65535).
+int gemm_df32(cudaStream_t s, const Gemm64& g) {
+    if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return BTA_OK;
+    if (g.batch > 65535) return BTA_ERR_ARG;
+    // small outputs: 16 x 16 tiles (more CTAs); otherwise 32 x 32
+    const bool small = (long long)((g.M + 31) / 32) * ((g.N + 31) / 32) * g.batch < 2 * 152;
+    if (small) {
+        dim3 grid((g.M + 15) / 16, (g.N + 15) / 16, g.batch);
+        gemm_df32_kernel<1><<<grid, DG_T, 0, s>>>(g);
+    } else {
+        dim3 grid((g.M + 31) / 32, (g.N + 31) / 32, g.batch);
+        gemm_df32_kernel<2><<<grid, DG_T, 0, s>>>(g);
+    }
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }

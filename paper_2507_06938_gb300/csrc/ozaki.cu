@@ -934,9 +934,9 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
 
 // GEMM executor of the mixed path: products whose output is at least
 // min_dim x min_dim go to the tensor cores (a short K, as in the rank-a
-// updates of the selected inversion, is padded to one 64-wide K block), the
-// rest (arrow, tip, small panels of the recursive diagonal factorisation)
-// stay on the FP64 pipe.
+// updates of the selected inversion, is padded to one 64-wide K block); the
+// smaller panels of the recursive diagonal factorisation go to the
+// double-float GEMM on the FP32 pipe, arrow and tip products stay FP64.
 bool gemm_mixed_takes(const GemmExec* ex, const Gemm64& g) {
     return ex && ex->fn == gemm_mixed_fn && g.M >= ex->min_dim && g.N >= ex->min_dim && g.K >= 1 &&
            g.M <= ozaki_max_rows() && (size_t)g.batch * ozaki_workspace_bytes(g.M, g.N, g.K) <= ex->ws_bytes;
@@ -944,5 +944,8 @@ bool gemm_mixed_takes(const GemmExec* ex, const Gemm64& g) {
 
 int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
     if (gemm_mixed_takes(ex, g)) return ozaki_gemm(s, g, ex->ws, ex->err);
+    // below the tensor-core threshold: square-ish products of the diagonal
+    // recursion in double-float on the FP32 pipe, thin or tiny ones in FP64
+    if (g.M >= 32 && g.N >= 32 && g.K >= 32 && g.batch <= 65535) return gemm_df32(s, g);
     return gemm64(s, g);
 }
