@@ -132,9 +132,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def kernel_source_sha1(source: str, region=None):
+    """sha1 of a kernel's source text: the file, or the part of it between two
+    marker lines (the device code of the captured kernels)."""
+    try:
+        text = open(os.path.join(ROOT, source), "rb").read()
+    except OSError:
+        return None
+    if region:
+        start, end = (m.encode() for m in region)
+        i = text.find(start)
+        j = text.find(end, i + 1) if i >= 0 else -1
+        if i < 0 or j < 0:
+            return None
+        text = text[i:j]
+    return hashlib.sha1(text).hexdigest()
+
+
 def traffic_record(kernel_key: str):
     """DRAM bytes per launch of the dominant kernel from a committed ncu summary,
-    null if the kernel source changed since the capture."""
+    null if the kernel's source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get(kernel_key)
@@ -142,12 +159,8 @@ def traffic_record(kernel_key: str):
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, rec["source"])
-    try:
-        h = hashlib.sha1(open(src, "rb").read()).hexdigest()
-    except OSError:
-        return None
-    return rec["bytes_per_launch"] if h == rec["source_sha1"] else None
+    h = kernel_source_sha1(rec["source"], rec.get("region"))
+    return rec["bytes_per_launch"] if h is not None and h == rec["source_sha1"] else None
 
 
 def cpu_threads():
