@@ -605,13 +605,15 @@ __global__ void __launch_bounds__(THREADS, 1)
 // triangular mask (shape 1: X[r][k] = 0 for k > r; shape 2: for k < r).
 // e_r = exponent of the row maximum (|X[r][k]| < 2^{e_r}).  Each entry is
 // turned into the 35-bit fixed-point integer V = round(X[r][k] 2^{35 - e_r})
-// (|V| < 2^35) and V into balanced base-128 digits d_0..d_4,
-// V = sum_s d_s 128^{4-s}, |d_s| <= 64 for s >= 1 and |d_0| <= 128, so that
-// X[r][k] 2^{-e_r} = sum_s d_s 2^{-7(s+1)} up to 2^{-36}.  Only integer
-// operations on the FP64 bit pattern are used (the FP64 pipe of GB300 is the
-// slow one).  Output: dig[s][r][k] (bf16, rows padded to Rp, K padded to Kp
-// with zeros) and exp[r] (0 for padding rows).
-constexpr int SPLIT_ROWS = 16, SPLIT_K = 64, SPLIT_THREADS = 256;
+// (|V| < 2^35, ties rounded away from zero) and |V| into balanced base-128
+// digits u_0..u_4, |V| = sum_s u_s 128^{4-s}, |u_s| <= 64 for s >= 1 and
+// |u_0| <= 128; the digits of V are d_s = sign(X) u_s, so that
+// X[r][k] 2^{-e_r} = sum_s d_s 2^{-7(s+1)} up to 2^{-36}.  Only integer and
+// FP32 operations are used (the FP64 pipe of GB300 is the slow one).
+// Output: dig[s][r][k] (bf16, rows padded to Rp, K padded to Kp with zeros)
+// and exp[r] (0 for padding rows).
+constexpr int SPLIT_THREADS = 256;
+constexpr int SPLIT_SMEM_TARGET = 73728;   // rows x Kp staged per CTA: 3 CTAs per SM
 
 struct SplitJob {
     const double* P;
@@ -619,168 +621,118 @@ struct SplitJob {
     int R, K, shape, Rp, Kp;
     int* expo;              // Rp per matrix
     __nv_bfloat16* dig;     // S * Rp * Kp per matrix
-    int row_blocks;         // Rp / SPLIT_ROWS
 };
 
-__device__ __forceinline__ long long fixed_point35(double x, int e) {
-    // round(x 2^{35 - e}) for |x| < 2^e, by shifting the 53-bit significand
+// The five digits of x for a row with exponent e, as FP32 bit patterns whose
+// upper halves are the bf16 patterns (c = 1040 + e).  V comes from the
+// 53-bit significand m of |x| = m 2^{ef - 1075}: V = round(m 2^{-(c - ef)}),
+// with c - ef >= 18 whenever |x| < 2^e (a shift of 63 or more gives 0, which
+// also covers e = 4096 for rows holding a NaN or an infinity).  Each digit
+// is peeled off the low 28 bits as ((t + 64) mod 128) - 64 with the carry
+// (t + 64) >> 7; the sign enters through the FP32 offset trick: the bit
+// pattern 0x4B400000 + d is 1.5 2^23 + d, exact for |d| < 2^22, so
+// subtracting 1.5 2^23 leaves d exactly, and d ^ s - s (s = 0 or -1)
+// negates it.
+__device__ __forceinline__ void digits_of(double x, int c, uint32_t (&f)[S]) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    const int ef = (int)((bits >> 52) & 0x7FF);
-    if (ef == 0) return 0;   // zero (subnormals are far below the 36-bit resolution of any row here)
-    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // x = m 2^{ef - 1075}
-    const int sh = (ef - 1075) + 35 - e;                                           // V = m 2^{sh}
-    unsigned long long v;
-    if (sh >= 0) {
-        v = m << sh;                                   // cannot overflow: |x| < 2^e gives V < 2^35
-    } else if (sh > -64) {
-        const int rs = -sh;
-        v = (m >> rs) + ((m >> (rs - 1)) & 1ull);      // round half up on the magnitude
-    } else {
-        v = 0;
-    }
-    const long long sv = (long long)v;
-    return (bits >> 63) ? -sv : sv;
-}
-
-// bf16 bit pattern of a small integer d (|d| <= 256, exact): d as FP32 by
-// the 1.5 * 2^23 offset (exact for |d| < 2^22), then the upper half.
-__device__ __forceinline__ uint32_t small_int_bf16(int d) {
-    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
-    return __float_as_uint(f) >> 16;
-}
-
-// The five balanced base-128 digits of V (|V| < 2^35) as bf16 bit patterns,
-// most significant first: digits of |V| with 32-bit operations (the low 28
-// bits hold four digits, the top 7 bits plus the last carry the first), then
-// the sign of V on every digit.
-__device__ __forceinline__ void digits_bf16(long long V, uint32_t* out) {
-    const bool neg = V < 0;
-    const unsigned long long U = (unsigned long long)(neg ? -V : V);
-    unsigned int lo = (unsigned int)(U & 0xFFFFFFFull);
-    const unsigned int top = (unsigned int)(U >> 28);
-    int d[S];
+    const uint32_t h = (uint32_t)(bits >> 32);
+    const int ef = (int)((h >> 20) & 0x7FF);
+    // zero and subnormals (far below the 2^-35 resolution of any row) give 0
+    const unsigned long long m = ef ? ((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
+    const int sft = min(c - ef - 1, 63);
+    const unsigned long long V = ((m >> sft) + 1) >> 1;   // round half away from zero on |x|
+    uint32_t lo = (uint32_t)V & 0xFFFFFFFu;
+    const uint32_t top = (uint32_t)(V >> 28);
+    const uint32_t sg = (uint32_t)((int32_t)h >> 31);
+    const uint32_t base = 0x4B400000u - sg;
 #pragma unroll
     for (int sl = S - 1; sl >= 1; --sl) {
-        int r = (int)(lo & 127u);
-        lo >>= 7;
-        if (r >= 64) {          // balanced digit in [-64, 64), carry one into the rest
-            r -= 128;
-            lo += 1;
-        }
-        d[sl] = r;
+        const uint32_t t = lo + 64u;
+        const uint32_t d = (t & 127u) - 64u;
+        lo = t >> 7;
+        f[sl] = __float_as_uint(__uint_as_float(base + (d ^ sg)) - 12582912.0f);
     }
-    d[0] = (int)(top + lo);     // lo is the final carry (0 or 1); |d_0| <= 128
-#pragma unroll
-    for (int sl = 0; sl < S; ++sl) out[sl] = small_int_bf16(neg ? -d[sl] : d[sl]);
+    f[0] = __float_as_uint(__uint_as_float(base + ((top + lo) ^ sg)) - 12582912.0f);
 }
 
-// Each thread moves a fixed set of SPLIT_ROWS x SPLIT_K / SPLIT_THREADS tile
-// entries; lanes run along the contiguous stored dimension so that the
-// global reads are coalesced for either stride order.
-constexpr int SPLIT_PER_THREAD = SPLIT_ROWS * SPLIT_K / SPLIT_THREADS;
-
-__device__ __forceinline__ void tile_coord(const SplitJob& J, int e, int& rr, int& kk) {
-    if (J.sr == 1) { rr = e % SPLIT_ROWS; kk = e / SPLIT_ROWS; } else { kk = e % SPLIT_K; rr = e / SPLIT_K; }
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
-// Loads this thread's entries of the tile at (r0, k0) into registers.
-__device__ __forceinline__ void load_tile(const SplitJob& J, const double* P, int r0, int k0,
-                                          double (&v)[SPLIT_PER_THREAD]) {
-#pragma unroll
-    for (int q = 0; q < SPLIT_PER_THREAD; ++q) {
-        int rr, kk;
-        tile_coord(J, threadIdx.x + q * SPLIT_THREADS, rr, kk);
-        const int r = r0 + rr, k = k0 + kk;
-        double x = 0.0;
-        if (r < J.R && k < J.K && !(J.shape == 1 && k > r) && !(J.shape == 2 && k < r)) x = P[r * J.sr + k * J.sk];
-        v[q] = x;
-    }
+// Rows per CTA for a K extent: the largest of 8, 4, 2, 1 whose staged rows
+// fit SPLIT_SMEM_TARGET (1 row up to the 227 KB of one CTA).
+inline int split_rows(int Kp) {
+    for (int rs = 8; rs >= 1; rs >>= 1)
+        if ((size_t)rs * (Kp + 4) * 8 <= (size_t)SPLIT_SMEM_TARGET) return rs;
+    return 1;
 }
+inline size_t split_smem(int rs, int Kp) { return (size_t)rs * (Kp + 4) * 8; }
 
-__device__ __forceinline__ void store_tile(const SplitJob& J, const double (&v)[SPLIT_PER_THREAD],
-                                           double (*tile)[SPLIT_K + 1]) {
-#pragma unroll
-    for (int q = 0; q < SPLIT_PER_THREAD; ++q) {
-        int rr, kk;
-        tile_coord(J, threadIdx.x + q * SPLIT_THREADS, rr, kk);
-        tile[rr][kk] = v[q];
-    }
-}
-
-// One CTA per (SPLIT_ROWS-row block, matrix) of one or two operands
-// (blockIdx.x runs over the row blocks of job 0, then of job 1; blockIdx.y =
-// matrix).  Pass 1 finds the largest exponent field of every row over all
-// of K; pass 2 reads the rows again (from L2) and writes the digits.  In both
-// passes the next tile is loaded into registers while the current one is
-// processed from shared memory.
-__global__ void __launch_bounds__(SPLIT_THREADS, 4) split_fused_kernel(SplitJob j0, SplitJob j1) {
-    __shared__ double tile[SPLIT_ROWS][SPLIT_K + 1];
-    __shared__ int row_exp[SPLIT_ROWS];
+// One CTA per (RS-row block, matrix) of one or two operands (blockIdx.x runs
+// over the row blocks of job 0, then of job 1; blockIdx.y = matrix).  The RS
+// rows are read once from global memory into shared memory (cp.async, lanes
+// along the contiguous stored dimension; row stride Kp + 4 keeps the
+// column-order fills free of bank conflicts), then the row exponents and the
+// digits are computed from there; each thread writes four consecutive k of
+// every digit slice with one 8-byte store.
+template <int RS>
+__global__ void __launch_bounds__(SPLIT_THREADS) split_kernel(SplitJob j0, SplitJob j1) {
+    extern __shared__ double stile[];   // RS x (Kp + 4)
+    __shared__ int row_e[RS];
     int rb = blockIdx.x;
-    const bool second = rb >= j0.row_blocks;
+    const int nrb0 = j0.Rp / RS;
+    const bool second = rb >= nrb0;
     const SplitJob& J = second ? j1 : j0;
-    if (second) rb -= j0.row_blocks;
+    if (second) rb -= nrb0;
     const int z = blockIdx.y;
     const double* P = J.P + z * J.sP;
     int* expo = J.expo + (long long)z * J.Rp;
     __nv_bfloat16* dig = J.dig + (long long)z * S * J.Rp * J.Kp;
-    const int r0 = rb * SPLIT_ROWS;
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    constexpr int ROWS_PER_WARP = SPLIT_ROWS / (SPLIT_THREADS / 32);
-    unsigned int emax[ROWS_PER_WARP];
-#pragma unroll
-    for (int q = 0; q < ROWS_PER_WARP; ++q) emax[q] = 0;
-    double v[SPLIT_PER_THREAD];
-    // ---- pass 1: row maxima of the exponent field
-    load_tile(J, P, r0, 0, v);
-    for (int k0 = 0; k0 < J.K; k0 += SPLIT_K) {
-        store_tile(J, v, tile);
-        __syncthreads();
-        if (k0 + SPLIT_K < J.K) load_tile(J, P, r0, k0 + SPLIT_K, v);   // in flight during the max
-#pragma unroll
-        for (int q = 0; q < ROWS_PER_WARP; ++q) {
-            const int rr = warp * ROWS_PER_WARP + q;
-#pragma unroll
-            for (int h = 0; h < SPLIT_K / 32; ++h) {
-                const unsigned long long bits = (unsigned long long)__double_as_longlong(tile[rr][lane + 32 * h]);
-                const unsigned int ef = (unsigned int)((bits >> 52) & 0x7FF);
-                emax[q] = max(emax[q], ef);
-            }
-        }
-        __syncthreads();
+    const int r0 = rb * RS;
+    const int ld = J.Kp + 4;
+    for (int e = threadIdx.x; e < RS * J.Kp; e += SPLIT_THREADS) {
+        int rr, kk;
+        if (J.sr == 1) { rr = e % RS; kk = e / RS; } else { kk = e % J.Kp; rr = e / J.Kp; }
+        const int r = r0 + rr;
+        double* dst = stile + rr * ld + kk;
+        if (r < J.R && kk < J.K && !(J.shape == 1 && kk > r) && !(J.shape == 2 && kk < r))
+            cp_async8(dst, P + r * J.sr + kk * J.sk);
+        else
+            *dst = 0.0;
     }
-#pragma unroll
-    for (int q = 0; q < ROWS_PER_WARP; ++q) {
-        unsigned int m = emax[q];
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int rr = warp; rr < RS; rr += SPLIT_THREADS / 32) {
+        unsigned int m = 0;
+        const double* row = stile + rr * ld;
+        for (int k = lane; k < J.Kp; k += 32) m = max(m, (unsigned int)((__double2hiint(row[k]) >> 20) & 0x7FF));
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) {
-            const int rr = warp * ROWS_PER_WARP + q;
             // |x| < 2^(ef - 1023 + 1) for a normal number with exponent field ef;
             // a NaN or Inf in the row gives a huge exponent, so the product
             // overflows to a non-finite value instead of passing silently
             const int e = m == 0 ? 0 : (m == 0x7FF ? 4096 : (int)m - 1023 + 1);
-            row_exp[rr] = e;
-            if (r0 + rr < J.Rp) expo[r0 + rr] = e;
+            row_e[rr] = e;
+            expo[r0 + rr] = e;
         }
     }
-    // ---- pass 2: digits, two consecutive k per thread (4-byte stores)
-    load_tile(J, P, r0, 0, v);
-    for (int k0 = 0; k0 < J.Kp; k0 += SPLIT_K) {
-        __syncthreads();   // row_exp written; the previous tile's digits are done
-        store_tile(J, v, tile);
-        __syncthreads();
-        if (k0 + SPLIT_K < J.Kp) load_tile(J, P, r0, k0 + SPLIT_K, v);   // in flight during the digits
-        for (int e = threadIdx.x; e < SPLIT_ROWS * SPLIT_K / 2; e += SPLIT_THREADS) {
-            const int kk = 2 * (e % (SPLIT_K / 2)), rr = e / (SPLIT_K / 2);
-            const int r = r0 + rr, k = k0 + kk;
-            if (r >= J.Rp || k >= J.Kp) continue;   // Kp is even: k + 1 < Kp as well
-            uint32_t d0[S], d1[S];
-            digits_bf16(r < J.R ? fixed_point35(tile[rr][kk], row_exp[rr]) : 0, d0);
-            digits_bf16(r < J.R ? fixed_point35(tile[rr][kk + 1], row_exp[rr]) : 0, d1);
+    __syncthreads();
+    const int per = J.Kp / 4;   // Kp is a multiple of 64
+    for (int e = threadIdx.x; e < RS * per; e += SPLIT_THREADS) {
+        const int kk = 4 * (e % per), rr = e / per;
+        const double* row = stile + rr * ld + kk;
+        const int c = 1040 + row_e[rr];
+        uint32_t f0[S], f1[S], f2[S], f3[S];
+        digits_of(row[0], c, f0);
+        digits_of(row[1], c, f1);
+        digits_of(row[2], c, f2);
+        digits_of(row[3], c, f3);
+        __nv_bfloat16* out = dig + (size_t)(r0 + rr) * J.Kp + kk;
 #pragma unroll
-            for (int sl = 0; sl < S; ++sl)
-                *reinterpret_cast<uint32_t*>(dig + ((size_t)sl * J.Rp + r) * J.Kp + k) = d0[sl] | (d1[sl] << 16);
-        }
+        for (int sl = 0; sl < S; ++sl)
+            *reinterpret_cast<uint2*>(out + (size_t)sl * J.Rp * J.Kp) =
+                make_uint2(__byte_perm(f0[sl], f1[sl], 0x7632), __byte_perm(f2[sl], f3[sl], 0x7632));
     }
 }
 
@@ -832,6 +784,32 @@ int num_sms() {
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+template <int RS>
+int split_launch_rs(cudaStream_t s, const SplitJob& ja, const SplitJob& jb, bool same, int nb) {
+    const size_t smem = split_smem(RS, ja.Kp);
+    static int attr_bytes = 48 * 1024;   // set once per row count, raised when a larger K appears
+    if ((int)smem > attr_bytes) {
+        BTA_CUDA_TRY(cudaFuncSetAttribute(split_kernel<RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_bytes = (int)smem;
+    }
+    const dim3 grid(ja.Rp / RS + (same ? 0 : jb.Rp / RS), nb);
+    split_kernel<RS><<<grid, SPLIT_THREADS, smem, s>>>(ja, jb);
+    BTA_LAUNCH_CHECK();
+    return BTA_OK;
+}
+
+// Digits and row exponents of both operands (of one when they coincide).
+int split_launch(cudaStream_t s, const SplitJob& ja, const SplitJob& jb, bool same, int nb) {
+    const int rs = split_rows(ja.Kp);
+    if (split_smem(rs, ja.Kp) > 227 * 1024) return BTA_ERR_ARG;   // K beyond 29 000
+    switch (rs) {
+        case 8: return split_launch_rs<8>(s, ja, jb, same, nb);
+        case 4: return split_launch_rs<4>(s, ja, jb, same, nb);
+        case 2: return split_launch_rs<2>(s, ja, jb, same, nb);
+        default: return split_launch_rs<1>(s, ja, jb, same, nb);
+    }
+}
+
 }  // namespace oz
 
 // Workspace needed by ozaki_gemm for one M x N x K product (bytes; a batch of
@@ -867,10 +845,9 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     const int shBt = g.shB == 1 ? 2 : (g.shB == 2 ? 1 : 0);
     // op(B)^T = op(A) (A B^T or A^T A shapes on one matrix): one split serves both
     const bool same = g.A == g.B && g.sA == g.sB && g.M == g.N && srA == srB && skA == skB && g.shA == shBt;
-    SplitJob ja{g.A, srA, skA, g.sA, g.M, g.K, g.shA, Mp, Kp, expA, digA, Mp / SPLIT_ROWS};
-    SplitJob jb{g.B, srB, skB, g.sB, g.N, g.K, shBt, Np, Kp, expB, digB, Np / SPLIT_ROWS};
-    split_fused_kernel<<<dim3(ja.row_blocks + (same ? 0 : jb.row_blocks), nb), SPLIT_THREADS, 0, s>>>(ja, jb);
-    BTA_LAUNCH_CHECK();
+    SplitJob ja{g.A, srA, skA, g.sA, g.M, g.K, g.shA, Mp, Kp, expA, digA};
+    SplitJob jb{g.B, srB, skB, g.sB, g.N, g.K, shBt, Np, Kp, expB, digB};
+    BTA_TRY(split_launch(s, ja, jb, same, nb));
     // digit rows per slice of the B operand as the GEMM kernel reads them
     const int NpB = same ? Mp : Np;
     const __nv_bfloat16* digBr = same ? digA : digB;
