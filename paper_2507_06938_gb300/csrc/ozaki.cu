@@ -219,18 +219,37 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = 96.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                           ((uint32_t)(TM >> 4) << 24);
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128,
+// N = nlev * 96 (one or two level accumulators side by side).
+__host__ __device__ constexpr uint32_t idesc_for(int nlev) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((nlev * TN) >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
 
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+
+// The 15 digit-pair products of one K step as 9 MMAs.  The level
+// accumulators sit side by side in tensor memory (level s at column 96 s)
+// and the five B slices side by side in shared memory (slice q at row 96 q),
+// so A_p times the stacked slices B_q0 .. B_q0+n-1 (N = 96 n) adds the pairs
+// (p, q0 + j) into levels p + q0 + j at once.  Pieces of n = 1 or 2 keep
+// N <= 256 and give level 2, which restarts every chunk, a piece of its own
+// in the p = 0 row (the first writes of a chunk come from that row).
+struct Piece { int p, q0, n, kind; };   // kind: 0 accumulate, 1 first of levels 0 1 3 4, 2 first of level 2
+constexpr int PIECES = 9;
+__device__ constexpr Piece kPieces[PIECES] = {
+    {0, 0, 2, 1}, {0, 2, 1, 2}, {0, 3, 2, 1},
+    {1, 0, 2, 0}, {1, 2, 2, 0},
+    {2, 0, 2, 0}, {2, 2, 1, 0},
+    {3, 0, 2, 0},
+    {4, 0, 1, 0}};
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -410,28 +429,26 @@ __global__ void __launch_bounds__(THREADS, 1)
                         const uint32_t sB = sA + S * A_SLICE_BYTES;
                         const uint64_t dA = smem_desc_sw64(sA), dB = smem_desc_sw64(sB);
 #pragma unroll
-                        for (int lv = 0; lv < S; ++lv) {
-                            const uint32_t d_tmem = tmem_base + lv * TN;
-                            if (lv == 2 && kb == kb0) {
-                                // level 2 restarts every chunk: its previous sums must be drained
-                                if (!mbar_wait(emptyB, (nB & 1) ^ 1, abort_flag, a.err)) {
-                                    ok = false;
-                                    break;
-                                }
-                                fence_after_sync();
-                            }
+                        for (int k = 0; k < TK / 16; ++k) {
 #pragma unroll
-                            for (int p = 0; p <= lv; ++p) {
-                                const int q = lv - p;
-#pragma unroll
-                                for (int k = 0; k < TK / 16; ++k) {
-                                    // descriptor start addresses are in 16-byte units
-                                    const uint64_t offA = (uint64_t)((p * A_SLICE_BYTES + k * 32) >> 4);
-                                    const uint64_t offB = (uint64_t)((q * B_SLICE_BYTES + k * 32) >> 4);
-                                    const bool first = (kb == kb0) && p == 0 && k == 0 && (lv == 2 || resetA);
-                                    umma_bf16(d_tmem, dA + offA, dB + offB, first ? 0u : 1u);
+                            for (int i = 0; i < PIECES; ++i) {
+                                const Piece pc = kPieces[i];
+                                if (pc.kind == 2 && kb == kb0 && k == 0) {
+                                    // level 2 restarts every chunk: its previous sums must be drained
+                                    if (!mbar_wait(emptyB, (nB & 1) ^ 1, abort_flag, a.err)) {
+                                        ok = false;
+                                        break;
+                                    }
+                                    fence_after_sync();
                                 }
+                                // descriptor start addresses are in 16-byte units
+                                const uint64_t offA = (uint64_t)((pc.p * A_SLICE_BYTES + k * 32) >> 4);
+                                const uint64_t offB = (uint64_t)((pc.q0 * B_SLICE_BYTES + k * 32) >> 4);
+                                const bool first = kb == kb0 && k == 0 && (pc.kind == 2 || (pc.kind == 1 && resetA));
+                                umma_bf16(tmem_base + (pc.p + pc.q0) * TN, dA + offA, dB + offB, idesc_for(pc.n),
+                                          first ? 0u : 1u);
                             }
+                            if (!ok) break;
                         }
                         if (!ok) break;
                         umma_commit(&empty[st]);
