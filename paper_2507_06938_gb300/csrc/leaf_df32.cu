@@ -12,19 +12,20 @@
 //   1/sqrt by one Newton-Raphson step in double-float from an FP32 seed,
 //   FP64 <-> double-float conversion on the bit patterns (one FP64 addition
 //   per stored element).
-// Both phases are right-looking with one barrier per step, and the updates of
-// a step are dealt to consecutive threads densely (an index table of the
-// lower triangle for phase 1, a rectangle for phase 2), so that warps issue
-// only useful work:
-// Phase 1: Cholesky.  Step k subtracts (a_ik / a_kk) a_jk from a_ij for
-//   k < j <= i; the thread that finishes a_{k+1,k+1} computes the next
-//   1/sqrt pivot at once; column k is scaled to L one step later (nobody
-//   reads it then).
-// Phase 2: X = L^{-1} by forward substitution on the identity.  B starts as
-//   the identity; step i makes row i of X final (X(i, j) = B(i, j) / L_ii)
-//   and subtracts L(r, i) X(i, j) from B(r, j) for r > i, j <= i.  The strict
+// Two right-looking recurrences share one loop with one barrier per step,
+// and the updates of a step are dealt to consecutive threads densely (an
+// index table of the lower triangle for the Cholesky, a rectangle for the
+// inverse), so that warps issue only useful work:
+// Cholesky.  Step k subtracts (a_ik / a_kk) a_jk from a_ij for k < j <= i;
+//   the thread that finishes a_{k+1,k+1} computes the next 1/sqrt pivot at
+//   once; column k is scaled to L one step later (nobody reads it then).
+// Inverse: X = L^{-1} by forward substitution on the identity.  Step i makes
+//   row i + 1 of X final and subtracts L(r, i) X(i, j) from B(r, j) for
+//   r > i, j <= i.  It needs only column i of L and row i of X, so it runs
+//   two steps behind the Cholesky, in the same barrier interval.  The strict
 //   lower triangle of B / X lives transposed in the strict upper triangle of
-//   the shared-memory matrix, whose lower triangle holds L.
+//   the shared-memory matrix, whose lower triangle holds L: the two
+//   recurrences never touch the same entry.
 // A non-positive pivot records BTA_ERR_NOT_PD (global row, matrix) in the
 // status word and poisons the results with NaN.
 
@@ -151,9 +152,26 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
         yh[0] = y.hi;
         yl[0] = y.lo;
     }
-    // ---------------------------------------------------------------- phase 1
+    // Cholesky (right-looking, on the lower triangle) and the inverse X = L^-1
+    // (right-looking forward substitution, on the strict upper triangle, which
+    // holds B(r, j) (r > j) at M[j][r]; zero from the load) run in one loop of
+    // n + 1 barrier intervals.  Interval k does Cholesky step k and inverse
+    // step i = k - 2, which needs column i of L (scaled in interval i + 1),
+    // row i of X (final after inverse step i - 1) and y_{i+1} (computed in
+    // interval i): the two steps touch disjoint entries.
+    //   Cholesky step k: M[i][j] -= M[i][k] y_k^2 M[j][k] for i >= j > k (the
+    //   columns stay unscaled until complete; column k-1 is scaled by y_{k-1}
+    //   in the same interval, nobody reads it then).
+    //   Inverse step i: B(r, j) -= L(r, i) X(i, j) for r > i, j <= i, with
+    //   X(i, i) = y_i; row i + 1 is final after this step, X(i+1, j) =
+    //   B(i+1, j) y_{i+1}.
     for (int k = 0; k <= n; ++k) {
         __syncthreads();
+        const int count1 = k < n ? (n - k - 1) * (n - k) / 2 : 0;
+        const int i2 = k - 2;
+        const int R2 = n - 1 - i2;
+        const int count2 = (i2 >= 0 && i2 <= n - 2) ? R2 * (i2 + 1) : 0;
+        df y2 = {0.f, 0.f};
         if (k < n) {
             const df y = df{yh[k], yl[k]};
             if (tid == 0 && !(y.hi > 0.f) && status) {
@@ -163,12 +181,13 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
                     status[2] = 2 * (mm % nbatch) + mm / nbatch;
                 }
             }
-            const df y2 = df_mul(y, y);
-            const int base = colstart(k + 1);
-            const int count = (n - k - 1) * (n - k) / 2;
-            // the first entry of the suffix is the next pivot (k+1, k+1): thread 0
-            // updates it first and computes its 1/sqrt at once
-            for (int t = tid; t < count; t += DF_THREADS) {
+            y2 = df_mul(y, y);
+        }
+        const int base = k < n ? colstart(k + 1) : 0;
+        // the first Cholesky entry is the next pivot (k+1, k+1): thread 0
+        // updates it first and computes its 1/sqrt at once
+        for (int t = tid; t < count1 + count2; t += DF_THREADS) {
+            if (t < count1) {
                 const int ij = tri[base + t];
                 const int i = ij >> 8, j = ij & 255;
                 const df aik = df{Sh[k * DF_LD + i], Sl[k * DF_LD + i]};
@@ -181,10 +200,20 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
                     yh[k + 1] = yn.hi;
                     yl[k + 1] = yn.lo;
                 }
+            } else {
+                const int u = t - count1;
+                const int j = u / R2;
+                const int r = i2 + 1 + (u - j * R2);
+                const df lri = df{Sh[i2 * DF_LD + r], Sl[i2 * DF_LD + r]};
+                const df xij = (j == i2) ? df{yh[i2], yl[i2]} : df{Sh[i2 * DF_LD + j], Sl[i2 * DF_LD + j]};
+                df bv = df_fnms(df{Sh[r * DF_LD + j], Sl[r * DF_LD + j]}, lri, xij);
+                if (r == i2 + 1) bv = df_mul(bv, df{yh[r], yl[r]});
+                Sh[r * DF_LD + j] = bv.hi;
+                Sl[r * DF_LD + j] = bv.lo;
             }
         }
         if (k > 0) {
-            // column k-1 is complete: scale it to L (nobody reads it in this iteration)
+            // column k-1 is complete: scale it to L
             const int c = k - 1;
             const int rowc = c + (DF_THREADS - 1 - tid);   // the last threads, least loaded above
             if (rowc < n && tid >= DF_THREADS - (n - c)) {
@@ -199,27 +228,6 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
         const int i = e % n, j = e / n;
         A[i + (long long)j * lda] = (i >= j) ? df_to_double(df{Sh[j * DF_LD + i], Sl[j * DF_LD + i]}) : 0.0;
     }
-    // ---------------------------------------------------------------- phase 2
-    // B(r, j) (r > j) at M[j][r]; zero from the load (the strict upper
-    // triangle of the input is never read).  Step i updates the (n-1-i) x (i+1)
-    // rectangle r > i, j <= i; X(i, j) = B(i, j) y_i is final for j < i
-    // (written by the last update of row i), X(i, i) = y_i.
-    for (int i = 0; i < n - 1; ++i) {
-        __syncthreads();
-        const int R = n - 1 - i;
-        const int count = R * (i + 1);
-        for (int t = tid; t < count; t += DF_THREADS) {
-            const int j = t / R;
-            const int r = i + 1 + (t - j * R);
-            const df lri = df{Sh[i * DF_LD + r], Sl[i * DF_LD + r]};
-            const df xij = (j == i) ? df{yh[i], yl[i]} : df{Sh[i * DF_LD + j], Sl[i * DF_LD + j]};
-            df b = df_fnms(df{Sh[r * DF_LD + j], Sl[r * DF_LD + j]}, lri, xij);
-            if (r == i + 1) b = df_mul(b, df{yh[r], yl[r]});   // row r is final after this step
-            Sh[r * DF_LD + j] = b.hi;
-            Sl[r * DF_LD + j] = b.lo;
-        }
-    }
-    __syncthreads();
     for (int e = tid; e < n * n; e += DF_THREADS) {
         const int i = e % n, j = e / n;
         double v = 0.0;
