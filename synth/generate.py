@@ -223,6 +223,9 @@ CONFIGS = {
     "c2": dict(nv=1, mesh=("grid", 32), nt=64, nr=4, seed=2, per_step=1024),
     # c2 with 8 time steps (same block size b=1024; for kernel profiling)
     "c2s": dict(nv=1, mesh=("grid", 32), nt=8, nr=4, seed=2, per_step=1024),
+    # c2 with 2 time steps: one Schur update of b=1024 blocks per factorisation,
+    # small enough on the device for multi-pass kernel captures
+    "c2p": dict(nv=1, mesh=("grid", 32), nt=2, nr=4, seed=2, per_step=1024),
     # trivariate coregional, b=3072, nt=48, a=6, N=147,462; 300 sites per step
     "c3": dict(nv=3, mesh=("grid", 32), nt=48, nr=2, seed=3, per_step=300,
                shared_sites=True),
