@@ -55,6 +55,8 @@ namespace oz {
 
 constexpr int S = 5;                      // digit slices = accumulated levels
 constexpr int TM = 128, TN = 96, TK = 32; // output tile; K block (64-byte rows)
+constexpr int ROW_BYTES = TK * 2;         // one digit row of a K block; the swizzle span
+static_assert(ROW_BYTES == 32 || ROW_BYTES == 64 || ROW_BYTES == 128, "K block of 16, 32 or 64");
 constexpr int STAGES = 2;
 constexpr int KB_PER_CHUNK = 512 / TK;    // exactness bound of the level-2 accumulation
 constexpr int EPI_WARPS = 16;            // 4 per TMEM lane quarter
@@ -206,16 +208,18 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major tile whose rows are 64 bytes
-// (32 bf16) long, 8-row groups 512 bytes apart, 64-byte swizzle (the layout a
-// TMA copy with CU_TENSOR_MAP_SWIZZLE_64B writes).
-__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+// Shared-memory matrix descriptor: K-major tile whose rows are ROW_BYTES
+// long, 8-row groups 8 ROW_BYTES apart, swizzled over ROW_BYTES (the layout a
+// TMA copy with the matching CU_TENSOR_MAP_SWIZZLE_* mode writes).  Layout
+// codes of the descriptor: 6 = 32-byte, 4 = 64-byte, 2 = 128-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t addr) {
+    constexpr uint64_t layout = ROW_BYTES == 32 ? 6 : (ROW_BYTES == 64 ? 4 : 2);
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)(16 >> 4) << 16;      // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(512 >> 4) << 32;     // stride byte offset: next 8-row group
-    d |= (uint64_t)1 << 46;              // descriptor version
-    d |= (uint64_t)4 << 61;              // 64-byte swizzle
+    d |= (uint64_t)(16 >> 4) << 16;                // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((8 * ROW_BYTES) >> 4) << 32;   // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                        // descriptor version
+    d |= layout << 61;
     return d;
 }
 
@@ -427,7 +431,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         fence_after_sync();
                         const uint32_t sA = smem_u32(smem + st * STAGE_BYTES);
                         const uint32_t sB = sA + S * A_SLICE_BYTES;
-                        const uint64_t dA = smem_desc_sw64(sA), dB = smem_desc_sw64(sB);
+                        const uint64_t dA = smem_desc_sw(sA), dB = smem_desc_sw(sB);
 #pragma unroll
                         for (int k = 0; k < TK / 16; ++k) {
 #pragma unroll
@@ -772,7 +776,7 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2D map over `rows` digit rows of kp bf16 each; box = TK x box_rows, 64-byte swizzle.
+// 2D map over `rows` digit rows of kp bf16 each; box = TK x box_rows, swizzled over ROW_BYTES.
 int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int kp, int box_rows) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return BTA_ERR_CUDA;
@@ -781,7 +785,10 @@ int make_map(CUtensorMap* map, const __nv_bfloat16* base, int rows, int kp, int 
     cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    ROW_BYTES == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                    : (ROW_BYTES == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B),
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? BTA_OK : BTA_ERR_CUDA;
 }
