@@ -258,6 +258,37 @@ int fobj_eval(bta_ctx_t ctx, bta_model_t model, const double* thetas_dev, int n_
 int bta_fobj_grad(bta_ctx_t ctx, bta_model_t model, const double* thetas_dev, int n_theta, double* f_out_dev,
                   double* grad_out_dev);
 
+/*
+ * bta_fobj_eval_multi -- f_obj (and, where asked, its gradient) for `count`
+ * independent problems that may differ in shape, e.g. univariate models of
+ * several (ns, nt) evaluated together: the independent function evaluations
+ * of Section IV-D.1 without the constraint that they share one model.  One
+ * context and one model per problem.  Each problem runs fobj_eval, or
+ * bta_fobj_grad when grad_out_dev[i] is not NULL, asynchronously on its own
+ * context's stream, so problems whose contexts were created on distinct
+ * streams overlap on the GPU; then `join` waits (events) for all of them, so
+ * that work queued on `join` afterwards sees every result.
+ *   count:        number of problems, >= 1.
+ *   ctxs, models: count handles (host arrays); ctxs[i] must have the (n, b, a)
+ *                 of models[i].  A context may appear more than once; its
+ *                 problems then run one after the other.
+ *   thetas_dev:   count device pointers, n_theta[i] x dim(theta of model i).
+ *   n_theta:      count host ints >= 1.
+ *   f_out_dev:    count device pointers, n_theta[i] values each.
+ *   mu_out_dev:   NULL, or count device pointers (entries may be NULL), each
+ *                 n_theta[i] x N_i conditional means (fobj_eval problems only).
+ *   grad_out_dev: NULL, or count device pointers (entries may be NULL), each
+ *                 n_theta[i] x dim(theta of model i).
+ *   join:         stream that waits for every problem (NULL: the legacy
+ *                 default stream).
+ * Returns BTA_ERR_ARG before launching anything if an argument is invalid,
+ * else the first error of a launch; the problems launched until then are
+ * still joined.  Device errors are read per context with bta_sync.
+ */
+int bta_fobj_eval_multi(int count, const bta_ctx_t* ctxs, const bta_model_t* models,
+                        const double* const* thetas_dev, const int* n_theta, double* const* f_out_dev,
+                        double* const* mu_out_dev, double* const* grad_out_dev, cudaStream_t join);
+
 /* bta_sync -- wait for the context's stream; return the first error the
  * device recorded since the last bta_sync (and clear it), else BTA_OK. */
 int bta_sync(bta_ctx_t ctx);

@@ -88,6 +88,8 @@ def lib():
         "bta_profile_read": (ip, [vp, C.POINTER(dp), C.POINTER(C.c_longlong), C.POINTER(dp)]),
         "bta_chol_inv_noalloc": (ip, [vp, ip, ip, vp, ip, vp, vp]),
         "bta_autotune": (ip, [vp, ip, C.POINTER(C.c_int)]),
+        "bta_fobj_eval_multi": (ip, [ip, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(ip),
+                                     C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]),
         "bta_flops_factor": (dp, [ip, ip, ip]),
         "bta_flops_selinv": (dp, [ip, ip, ip]),
     }
@@ -107,7 +109,7 @@ def exported_symbols():
             "bta_strerror", "bta_flops_factor", "bta_flops_selinv", "bta_selinv_diag",
             "bta_launch_count", "bta_profile", "bta_profile_read", "bta_chol_inv_noalloc",
             "bta_create_batched", "bta_batch_size", "bta_factor_batch", "bta_selinv_batch",
-            "bta_last_error_matrix", "bta_fobj_grad", "bta_autotune"]
+            "bta_last_error_matrix", "bta_fobj_grad", "bta_autotune", "bta_fobj_eval_multi"]
 
 
 def _check(code: int, where: str):
@@ -353,6 +355,27 @@ def fobj_eval(ctx: BtaContext, model: BtaModel, thetas, f_out, mu_out=None):
 
 def bta_fobj_grad(ctx: BtaContext, model: BtaModel, thetas, f_out, grad_out):
     ctx.fobj_grad(model, thetas, f_out, grad_out)
+
+
+def bta_fobj_eval_multi(contexts, models, thetas, f_outs, mu_outs=None, grad_outs=None, join_stream=None):
+    """f_obj (and gradients where grad_outs[i] is a tensor) of independent
+    problems of any shapes, one context and model per problem; each runs on its
+    context's stream and `join_stream` (default: the current stream) waits for
+    all.  thetas[i]: (n_theta_i, dim_i) CUDA float64; f_outs[i]: n_theta_i
+    values; mu_outs[i] / grad_outs[i]: None or (n_theta_i, N_i) / (n_theta_i, dim_i)."""
+    count = len(contexts)
+    if not (len(models) == len(thetas) == len(f_outs) == count) or count < 1:
+        raise ValueError("bta_fobj_eval_multi: one context, model, theta block and f output per problem")
+    vparr = C.c_void_p * count
+    ctx_arr = vparr(*[c.handle for c in contexts])
+    mod_arr = vparr(*[m.handle for m in models])
+    th_arr = vparr(*[_ptr(t) for t in thetas])
+    nth = (C.c_int * count)(*[int(t.shape[0]) if t.dim() == 2 else 1 for t in thetas])
+    f_arr = vparr(*[_ptr(f) for f in f_outs])
+    mu_arr = vparr(*[_ptr(m) for m in mu_outs]) if mu_outs is not None else None
+    g_arr = vparr(*[_ptr(g) for g in grad_outs]) if grad_outs is not None else None
+    _check(lib().bta_fobj_eval_multi(count, ctx_arr, mod_arr, th_arr, nth, f_arr, mu_arr, g_arr,
+                                     C.c_void_p(_stream_handle(join_stream))), "bta_fobj_eval_multi")
 
 
 def bta_sync(ctx: BtaContext):

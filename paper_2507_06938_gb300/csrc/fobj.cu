@@ -172,3 +172,39 @@ extern "C" int fobj_eval(bta_ctx_t ctx, bta_model_t m, const double* thetas_dev,
     }
     return BTA_OK;
 }
+
+// Independent problems of any shapes: each on its own context's stream, all
+// joined onto `join` by events (the evaluations of Section IV-D.1 need no
+// common model; concurrency comes from the contexts' distinct streams).
+extern "C" int bta_fobj_eval_multi(int count, const bta_ctx_t* ctxs, const bta_model_t* models,
+                                   const double* const* thetas_dev, const int* n_theta, double* const* f_out_dev,
+                                   double* const* mu_out_dev, double* const* grad_out_dev, cudaStream_t join) {
+    if (count < 1 || !ctxs || !models || !thetas_dev || !n_theta || !f_out_dev) return BTA_ERR_ARG;
+    for (int i = 0; i < count; ++i) {
+        const bta_ctx_t c = ctxs[i];
+        const bta_model_t m = models[i];
+        if (!c || !m || !thetas_dev[i] || !f_out_dev[i] || n_theta[i] < 1) return BTA_ERR_ARG;
+        if (m->n != c->n || m->b != c->b || m->a != c->a) return BTA_ERR_ARG;
+        if (grad_out_dev && grad_out_dev[i] && mu_out_dev && mu_out_dev[i]) return BTA_ERR_ARG;
+    }
+    int rc = BTA_OK;
+    int launched = 0;
+    for (int i = 0; i < count && rc == BTA_OK; ++i) {
+        double* g = grad_out_dev ? grad_out_dev[i] : nullptr;
+        double* mu = mu_out_dev ? mu_out_dev[i] : nullptr;
+        rc = g ? bta_fobj_grad(ctxs[i], models[i], thetas_dev[i], n_theta[i], f_out_dev[i], g)
+               : fobj_eval(ctxs[i], models[i], thetas_dev[i], n_theta[i], f_out_dev[i], mu);
+        launched = i + 1;   // a failed call may still have queued work
+    }
+    for (int i = 0; i < launched; ++i) {
+        cudaEvent_t ev = nullptr;
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) {
+            e = cudaEventRecord(ev, ctxs[i]->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(join, ev, 0);
+            cudaEventDestroy(ev);   // released once the recorded work has completed
+        }
+        if (e != cudaSuccess && rc == BTA_OK) rc = bta_cuda_fail(e);
+    }
+    return rc;
+}

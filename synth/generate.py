@@ -251,6 +251,15 @@ CONFIGS = {
 }
 
 
+# The uneven batch of univariate instances (ns in {256, 512, 1024} on 16x16,
+# 16x32 and 32x32 grids, nt in {16, 32, 64}; one site per mesh node and
+# time step on average), evaluated together through one call.
+for _gx, _gy in ((16, 16), (16, 32), (32, 32)):
+    for _nt in (16, 32, 64):
+        CONFIGS[f"c4b_{_gx * _gy}_{_nt}"] = dict(nv=1, mesh=("grid", _gx, _gy), nt=_nt, nr=4,
+                                                 seed=40 + _nt + _gx * _gy, per_step=_gx * _gy)
+
+
 def problem_from_config(name: str, **overrides) -> Problem:
     spec = dict(CONFIGS[name])
     spec.update(overrides)
