@@ -32,7 +32,10 @@ class Objective:
 
     gradient: "adjoint" (bta_fobj_grad) or "fd" (Eq. 10 in one batch).
     batch: theta points per group of the context (default 2 dim + 1, which
-    holds one stencil or one Hessian column set in a single group)."""
+    holds one stencil or one Hessian column set in a single group).  Single
+    points go to a second context of batch 1: a group smaller than its
+    context's batch factors Q_p and Q_c as two chains (their storage ranges
+    are not adjacent), a full group as one."""
 
     def __init__(self, problem, precision: int = bta.BTA_MIXED, gradient: str = "adjoint", h: float = 1e-3,
                  batch: int | None = None, stream=None):
@@ -46,8 +49,18 @@ class Objective:
         self.batch = int(batch) if batch else 2 * self.dim + 1
         self.model = bta.BtaModel(problem)
         self.ctx = bta.BtaContext(problem.nt, problem.b, problem.a, precision, stream, self.batch)
+        self._ctx1 = None
+        self._precision, self._stream = precision, stream
         self._torch = torch
         self.n_eval = 0
+
+    def _context(self, count: int):
+        if count != 1 or self.batch == 1:
+            return self.ctx
+        if self._ctx1 is None:
+            p = self.problem
+            self._ctx1 = bta.BtaContext(p.nt, p.b, p.a, self._precision, self._stream, 1)
+        return self._ctx1
 
     def _dev(self, x):
         return self._torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
@@ -56,8 +69,9 @@ class Objective:
         """f_obj at each row of thetas (one batched call)."""
         th = np.atleast_2d(np.asarray(thetas, dtype=np.float64))
         f = self._torch.zeros(th.shape[0], dtype=self._torch.float64, device="cuda")
-        self.ctx.fobj_eval(self.model, self._dev(th), f)
-        self.ctx.sync()
+        ctx = self._context(th.shape[0])
+        ctx.fobj_eval(self.model, self._dev(th), f)
+        ctx.sync()
         self.n_eval += th.shape[0]
         return f.cpu().numpy()
 
@@ -67,8 +81,9 @@ class Objective:
         t = self._torch
         f = t.zeros(th.shape[0], dtype=t.float64, device="cuda")
         g = t.zeros(th.shape, dtype=t.float64, device="cuda")
-        self.ctx.fobj_grad(self.model, self._dev(th), f, g)
-        self.ctx.sync()
+        ctx = self._context(th.shape[0])
+        ctx.fobj_grad(self.model, self._dev(th), f, g)
+        ctx.sync()
         self.n_eval += th.shape[0]
         return f.cpu().numpy(), g.cpu().numpy()
 
@@ -87,16 +102,19 @@ class Objective:
         N = self.problem.N
         f = t.zeros(1, dtype=t.float64, device="cuda")
         mu = t.zeros((1, N), dtype=t.float64, device="cuda")
-        self.ctx.fobj_eval(self.model, self._dev(np.asarray(theta)[None, :]), f, mu)
+        ctx = self._context(1)
+        ctx.fobj_eval(self.model, self._dev(np.asarray(theta)[None, :]), f, mu)
         which = 2 * 0 + bta.BTA_QC          # slot 0 holds the last (only) point
-        self.ctx.selinv(which)
+        ctx.selinv(which)
         var = t.zeros(N, dtype=t.float64, device="cuda")
-        self.ctx.selinv_diag(which, var)
-        self.ctx.sync()
+        ctx.selinv_diag(which, var)
+        ctx.sync()
         self.n_eval += 1
         return mu[0].cpu().numpy(), var.cpu().numpy()
 
     def close(self):
+        if self._ctx1 is not None:
+            self._ctx1.close()
         self.ctx.close()
         self.model.close()
 
