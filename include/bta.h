@@ -233,7 +233,9 @@ int bta_matvec(bta_ctx_t ctx, int which, const double* x_dev, double* y_dev);
  * + mu^T Q_p mu.  f_out_dev receives n_theta values.  If mu_out_dev is not
  * NULL it receives the n_theta conditional means (n_theta x N, row j for
  * theta j).  The thetas are evaluated in groups of the context's batch size,
- * each group's 2 x batch matrices going through the same launches; in
+ * each group's 2 x batch matrices going through the same launches (a last,
+ * partial group factors its Q_p and Q_c in two passes, as their storage
+ * ranges are not adjacent; a context of batch 1 keeps single points in one); in
  * mixed precision the solve takes two refinement steps with an FP64
  * residual.  Afterwards slot j holds the matrices and factors of theta
  * (last group start + j).  From the second full group on, a full group is
