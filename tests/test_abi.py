@@ -60,3 +60,10 @@ def test_host_only_entry_points(lib):
     assert lib.bta_create(0, 10, 2, 0, None, ctypes.byref(h)) == 1
     assert lib.bta_create(4, 10, 2, 7, None, ctypes.byref(h)) == 1
     assert lib.bta_model_create(None, ctypes.byref(h)) == 1
+    # the multi-problem entry rejects an empty or incomplete request before launching anything
+    P = ctypes.c_void_p
+    one = (ctypes.c_int * 1)(1)
+    null = (P * 1)(None)
+    assert lib.bta_fobj_eval_multi(0, null, null, null, one, null, None, None, None) == 1
+    assert lib.bta_fobj_eval_multi(1, null, null, null, one, null, None, None, None) == 1
+    assert lib.bta_fobj_eval_multi(1, None, None, None, None, None, None, None, None) == 1
