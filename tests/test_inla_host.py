@@ -119,3 +119,22 @@ def test_gaussian_marginals_at_the_mode(small):
     terms = ofobj.f_obj_terms(p, th, tier="dense", fd=obj.fd)
     assert np.allclose(res.mu, terms["mu"], rtol=0, atol=1e-12 * np.max(np.abs(terms["mu"])))
     assert np.all(res.var > 0)
+
+
+def test_line_search_returns_a_strong_wolfe_step():
+    # phi along a descent direction of Rosenbrock's function from a far point
+    x = np.array([-1.2, 1.0])
+    g = _rosen_grad(x)
+    p = -g / np.linalg.norm(g)
+    c1, c2 = 1e-4, 0.9
+
+    def phi(alpha):
+        z = x + alpha * p
+        return _rosen(z), float(_rosen_grad(z) @ p), None
+
+    phi0, dphi0 = _rosen(x), float(g @ p)
+    for alpha1 in (1.0, 1e-3, 10.0):
+        alpha, v, _ = inla._line_search(phi, phi0, dphi0, c1=c1, c2=c2, alpha1=alpha1)
+        d = phi(alpha)[1]
+        assert v <= phi0 + c1 * alpha * dphi0          # sufficient decrease
+        assert abs(d) <= c2 * abs(dphi0)               # curvature (strong form)
