@@ -281,15 +281,17 @@ int bta_fobj_grad(bta_ctx_t ctx, bta_model_t model, const double* thetas_dev, in
  *                 n_theta[i] x N_i conditional means (fobj_eval problems only).
  *   grad_out_dev: NULL, or count device pointers (entries may be NULL), each
  *                 n_theta[i] x dim(theta of model i).
- *   join:         stream that waits for every problem (NULL: the legacy
- *                 default stream).
+ *   join:         a cudaStream_t (NULL: the legacy default stream).  Every
+ *                 problem's stream first waits for the work queued on `join`
+ *                 before the call (so inputs written there are complete),
+ *                 and `join` then waits for every problem.
  * Returns BTA_ERR_ARG before launching anything if an argument is invalid,
  * else the first error of a launch; the problems launched until then are
  * still joined.  Device errors are read per context with bta_sync.
  */
 int bta_fobj_eval_multi(int count, const bta_ctx_t* ctxs, const bta_model_t* models,
                         const double* const* thetas_dev, const int* n_theta, double* const* f_out_dev,
-                        double* const* mu_out_dev, double* const* grad_out_dev, cudaStream_t join);
+                        double* const* mu_out_dev, double* const* grad_out_dev, void* join);
 
 /* bta_sync -- wait for the context's stream; return the first error the
  * device recorded since the last bta_sync (and clear it), else BTA_OK. */
@@ -352,7 +354,8 @@ int bta_autotune(bta_ctx_t ctx, int reps, int* chosen);
  * block order to b <= 2048 (larger b returns BTA_ERR_ARG, as do bad pointers
  * or leading dimensions).  The first call on a device looks up the device
  * address of that array, so make that first call before any stream
- * capture.  All calls share the one array: calls whose executions overlap
+ * capture; the address is kept for the life of the process, so the entry
+ * point must not be used on a device after cudaDeviceReset there.  All calls share the one array: calls whose executions overlap
  * on the GPU (other streams, other host threads) race and give wrong
  * results; serialise them.
  */

@@ -202,7 +202,9 @@ class BtaContext:
 
     def __init__(self, n: int, b: int, a: int, precision: int = BTA_FP64, stream=None, batch: int = 1):
         L = lib()
-        self._stream_obj = stream
+        import torch
+        # the torch stream the context runs on (the current one when none is given)
+        self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         _check(L.bta_create_batched(n, b, a, precision, batch, C.c_void_p(_stream_handle(stream)), C.byref(h)),
                "bta_create_batched")
@@ -376,6 +378,13 @@ def bta_fobj_eval_multi(contexts, models, thetas, f_outs, mu_outs=None, grad_out
     g_arr = vparr(*[_ptr(g) for g in grad_outs]) if grad_outs is not None else None
     _check(lib().bta_fobj_eval_multi(count, ctx_arr, mod_arr, th_arr, nth, f_arr, mu_arr, g_arr,
                                      C.c_void_p(_stream_handle(join_stream))), "bta_fobj_eval_multi")
+    # the problems' streams use these tensors: keep their memory from being
+    # reused by torch's caching allocator before those streams are done
+    for k, c in enumerate(contexts):
+        for t in (thetas[k], f_outs[k], None if mu_outs is None else mu_outs[k],
+                  None if grad_outs is None else grad_outs[k]):
+            if t is not None:
+                t.record_stream(c._stream_obj)
 
 
 def bta_sync(ctx: BtaContext):
@@ -404,17 +413,28 @@ NOALLOC_MAX_B = 2048
 def bta_chol_inv_noalloc(A, X, info, stream=None):
     """Allocation-free Cholesky + inverse of one SPD block (no counterpart in
     the paper): A (b x b, CUDA float64, column-major data of a symmetric
-    matrix) is overwritten in its lower triangle by L, X receives L^{-1},
-    info (1 int64 element) receives -1 or the first failing row.  Nothing is
-    allocated by the library; the workspace is a fixed 8.5 MiB device array,
-    so b is limited to 2048 and concurrent calls on the GPU race."""
+    matrix) is overwritten in its lower triangle by L, X (b x b) receives
+    L^{-1}, info (at least one int64 element) receives -1 or the first failing
+    row.  Nothing is allocated by the library; the workspace is a fixed
+    8.5 MiB device array of the current device, so b is limited to 2048,
+    every tensor must live on the current device, and concurrent calls on the
+    GPU race."""
     import torch
-    b = int(A.shape[0])
-    if b > NOALLOC_MAX_B:
-        raise ValueError(f"bta_chol_inv_noalloc: block order {b} exceeds the maximum {NOALLOC_MAX_B}")
     for t, dt in ((A, torch.float64), (X, torch.float64), (info, torch.int64)):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
             raise TypeError("expected contiguous CUDA tensors (float64 A, X; int64 info)")
+    if A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError(f"bta_chol_inv_noalloc: A must be square, got {tuple(A.shape)}")
+    b = int(A.shape[0])
+    if tuple(X.shape) != (b, b):
+        raise ValueError(f"bta_chol_inv_noalloc: X must be {b} x {b}, got {tuple(X.shape)}")
+    if info.numel() < 1:
+        raise ValueError("bta_chol_inv_noalloc: info needs one element")
+    if b > NOALLOC_MAX_B:
+        raise ValueError(f"bta_chol_inv_noalloc: block order {b} exceeds the maximum {NOALLOC_MAX_B}")
+    dev = torch.cuda.current_device()
+    if any(t.device.index != dev for t in (A, X, info)):
+        raise ValueError("bta_chol_inv_noalloc: A, X and info must be on the current CUDA device")
     _check(lib().bta_chol_inv_noalloc(A.data_ptr(), b, b, X.data_ptr(), b, info.data_ptr(),
                                       C.c_void_p(_stream_handle(stream))), "bta_chol_inv_noalloc")
 

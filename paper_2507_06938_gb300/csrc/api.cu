@@ -5,6 +5,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -20,6 +22,29 @@ int bta_cuda_fail(cudaError_t e) {
     g_last_cuda = e;
     if (e == cudaErrorMemoryAllocation) return BTA_ERR_OOM;
     return BTA_ERR_CUDA;
+}
+
+namespace {
+struct SmemAttr { const void* fn; int dev; int bytes; };
+std::mutex g_attr_mutex;
+std::vector<SmemAttr> g_attr;
+}  // namespace
+
+int ensure_dyn_smem(const void* fn, int bytes) {
+    if (bytes <= 48 * 1024) return BTA_OK;
+    int dev = 0;
+    BTA_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    for (SmemAttr& e : g_attr) {
+        if (e.fn != fn || e.dev != dev) continue;
+        if (e.bytes >= bytes) return BTA_OK;
+        BTA_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        e.bytes = bytes;
+        return BTA_OK;
+    }
+    BTA_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    g_attr.push_back(SmemAttr{fn, dev, bytes});
+    return BTA_OK;
 }
 
 namespace {

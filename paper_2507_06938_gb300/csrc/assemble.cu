@@ -189,9 +189,7 @@ static int assemble_run(bta_ctx_t ctx, bta_model_t m, const double* params, long
     p.D = Q.D; p.B = Q.B; p.R = Q.R; p.T = Q.T;
     p.sD = Q.sD; p.sB = Q.sB; p.sR = Q.sR; p.sT = Q.sT;
     const size_t smem = (size_t)p.b * sizeof(double);
-    if (smem > 48 * 1024)
-        BTA_CUDA_TRY(cudaFuncSetAttribute(assemble_db_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BTA_TRY(ensure_dyn_smem((const void*)assemble_db_kernel, (int)smem));
     dim3 grid(p.b, 2 * p.n - 1, count);
     assemble_db_kernel<<<grid, ASM_THREADS, smem, s>>>(p);
     BTA_LAUNCH_CHECK();

@@ -27,6 +27,11 @@
 
 int bta_cuda_fail(cudaError_t e);
 
+// Raise kernel `fn`'s dynamic shared-memory limit to at least `bytes` on the
+// current device.  The attribute is per device and context, so the setting is
+// remembered per (kernel, device); thread safe.
+int ensure_dyn_smem(const void* fn, int bytes);
+
 // Every kernel launch of the library is followed by BTA_LAUNCH_CHECK(): it
 // counts the launch (bta_launch_count) and turns a launch error into a code.
 void bta_note_launch();

@@ -533,13 +533,8 @@ int gemm_exec(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
 
 static int leaf_launch(cudaStream_t s, double* A, long long lda, long long sA, double* X, long long ldx,
                        long long sX, int n, long long row0, long long* status, int batch, int m_first, int nbatch) {
-    static bool attr_set = false;
     const size_t smem = (3 * LDS * LEAF_MAX + LEAF_MAX + 1) * sizeof(double);
-    if (!attr_set) {
-        BTA_CUDA_TRY(cudaFuncSetAttribute(chol_inv_leaf_kernel,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
+    BTA_TRY(ensure_dyn_smem((const void*)chol_inv_leaf_kernel, (int)smem));
     const int threads = 256;
     chol_inv_leaf_kernel<<<batch, threads, smem, s>>>(A, lda, sA, X, ldx, sX, n, row0, status, m_first, nbatch);
     BTA_LAUNCH_CHECK();

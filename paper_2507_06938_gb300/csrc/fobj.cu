@@ -178,7 +178,7 @@ extern "C" int fobj_eval(bta_ctx_t ctx, bta_model_t m, const double* thetas_dev,
 // common model; concurrency comes from the contexts' distinct streams).
 extern "C" int bta_fobj_eval_multi(int count, const bta_ctx_t* ctxs, const bta_model_t* models,
                                    const double* const* thetas_dev, const int* n_theta, double* const* f_out_dev,
-                                   double* const* mu_out_dev, double* const* grad_out_dev, cudaStream_t join) {
+                                   double* const* mu_out_dev, double* const* grad_out_dev, void* join_stream) {
     if (count < 1 || !ctxs || !models || !thetas_dev || !n_theta || !f_out_dev) return BTA_ERR_ARG;
     for (int i = 0; i < count; ++i) {
         const bta_ctx_t c = ctxs[i];
@@ -186,6 +186,21 @@ extern "C" int bta_fobj_eval_multi(int count, const bta_ctx_t* ctxs, const bta_m
         if (!c || !m || !thetas_dev[i] || !f_out_dev[i] || n_theta[i] < 1) return BTA_ERR_ARG;
         if (m->n != c->n || m->b != c->b || m->a != c->a) return BTA_ERR_ARG;
         if (grad_out_dev && grad_out_dev[i] && mu_out_dev && mu_out_dev[i]) return BTA_ERR_ARG;
+    }
+    cudaStream_t join = (cudaStream_t)join_stream;
+    // inputs (thetas) and outputs may have been written or zeroed on `join`
+    // just before the call: every distinct problem stream waits for that work
+    {
+        cudaEvent_t ev = nullptr;
+        BTA_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, join);
+        for (int i = 0; i < count && e == cudaSuccess; ++i) {
+            bool seen = false;
+            for (int k = 0; k < i; ++k) seen = seen || ctxs[k]->stream == ctxs[i]->stream;
+            if (!seen) e = cudaStreamWaitEvent(ctxs[i]->stream, ev, 0);
+        }
+        cudaEventDestroy(ev);
+        BTA_CUDA_TRY(e);
     }
     int rc = BTA_OK;
     int launched = 0;

@@ -354,13 +354,8 @@ int chol_inv_df32_launch(cudaStream_t s, double* A, long long lda, long long sA,
                          long long sX, int n, long long row0, long long* status, int batch, int m_first,
                          int nbatch) {
     if (n > DF_MAX || n < 1 || batch < 1) return BTA_ERR_ARG;
-    static bool attr_set = false;
     const size_t smem = chol_inv_df32_smem_bytes();
-    if (!attr_set) {
-        BTA_CUDA_TRY(cudaFuncSetAttribute(chol_inv_df32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-        attr_set = true;
-    }
+    BTA_TRY(ensure_dyn_smem((const void*)chol_inv_df32_kernel, (int)smem));
     chol_inv_df32_kernel<<<batch, DF_THREADS, smem, s>>>(A, lda, sA, X, ldx, sX, n, row0, status, m_first, nbatch);
     BTA_LAUNCH_CHECK();
     return BTA_OK;

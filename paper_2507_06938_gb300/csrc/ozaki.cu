@@ -29,11 +29,12 @@
 // Kernel (persistent, one CTA of 576 threads per SM, 128 x 96 output tiles):
 //   warp 0      TMA producer: for every 32-wide K block all five digit slices
 //               of the A tile (128 x 32) and of the B tile (96 x 32), 64-byte
-//               swizzle, into a 3-stage shared-memory ring (70 KB a stage), so
+//               swizzle, into a 2-stage shared-memory ring (70 KB a stage), so
 //               that each digit is read from L2 once per tile
-//   warp 1      allocates 512 TMEM columns (five 96-column accumulators) and
-//               issues tcgen05.mma (M = 128, N = 96, K = 16) for the 15 digit
-//               pairs of each K block from one thread
+//   warp 1      allocates 512 TMEM columns (five 96-column accumulators) and,
+//               from one thread, issues the 15 digit pairs of each 16-wide K
+//               step as 9 tcgen05.mma (M = 128, K = 16) over stacked B slices
+//               (N = 96 or 192, see kPieces)
 //   warps 2..17 drain level 2 after every 512-long K chunk and the other
 //               levels after every second chunk, then update C while the
 //               next tile's products run
@@ -811,11 +812,7 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 template <int RS>
 int split_launch_rs(cudaStream_t s, const SplitJob& ja, const SplitJob& jb, bool same, int nb) {
     const size_t smem = split_smem(RS, ja.Kp);
-    static int attr_bytes = 48 * 1024;   // set once per row count, raised when a larger K appears
-    if ((int)smem > attr_bytes) {
-        BTA_CUDA_TRY(cudaFuncSetAttribute(split_kernel<RS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_bytes = (int)smem;
-    }
+    BTA_TRY(ensure_dyn_smem((const void*)split_kernel<RS>, (int)smem));
     const dim3 grid(ja.Rp / RS + (same ? 0 : jb.Rp / RS), nb);
     split_kernel<RS><<<grid, SPLIT_THREADS, smem, s>>>(ja, jb);
     BTA_LAUNCH_CHECK();
@@ -921,12 +918,7 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     a.shA = g.shA;
     a.shB = g.shB;
     a.err = err;
-    static bool attr = false;
-    if (!attr) {
-        BTA_CUDA_TRY(cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)SMEM_BYTES));
-        attr = true;
-    }
+    BTA_TRY(ensure_dyn_smem((const void*)ozaki_gemm_kernel, (int)SMEM_BYTES));
     const int grid = (int)std::min<long long>(a.units, sms);
     ozaki_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(mA, mB, a);
     BTA_LAUNCH_CHECK();

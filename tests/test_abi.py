@@ -67,3 +67,57 @@ def test_host_only_entry_points(lib):
     assert lib.bta_fobj_eval_multi(0, null, null, null, one, null, None, None, None) == 1
     assert lib.bta_fobj_eval_multi(1, null, null, null, one, null, None, None, None) == 1
     assert lib.bta_fobj_eval_multi(1, None, None, None, None, None, None, None, None) == 1
+
+
+C_PROGRAM = r"""
+#include "bta.h"
+#include <stdio.h>
+#include <string.h>
+
+int main(void) {
+    bta_ctx_t ctx = NULL;
+    bta_model_t model = NULL;
+    const bta_ctx_t ctxs[1] = {NULL};
+    const bta_model_t models[1] = {NULL};
+    const double* thetas[1] = {NULL};
+    double* fs[1] = {NULL};
+    const int n_theta[1] = {1};
+    const char* ok = bta_strerror(BTA_OK);
+    double f = bta_flops_factor(64, 1024, 4) + bta_flops_selinv(64, 1024, 4);
+    if (strcmp(ok, "ok") != 0 || !(f > 0.0)) return 10;
+    if (bta_create(0, 10, 2, BTA_FP64, NULL, &ctx) != BTA_ERR_ARG) return 11;
+    if (bta_create_batched(4, 10, 2, BTA_MIXED, 0, NULL, &ctx) != BTA_ERR_ARG) return 12;
+    if (bta_model_create(NULL, &model) != BTA_ERR_ARG) return 13;
+    if (bta_fobj_eval_multi(0, ctxs, models, thetas, n_theta, fs, NULL, NULL, NULL) != BTA_ERR_ARG) return 14;
+    if (bta_fobj_eval_multi(1, ctxs, models, thetas, n_theta, fs, NULL, NULL, NULL) != BTA_ERR_ARG) return 15;
+    if (bta_chol_inv_noalloc(NULL, 4, 4, NULL, 4, NULL, NULL) != BTA_ERR_ARG) return 16;
+    printf("%s|%s\n", bta_strerror(BTA_ERR_ARG), bta_strerror(BTA_ERR_STATE));
+    return 0;
+}
+"""
+
+
+def test_header_compiles_as_c_and_links(lib, tmp_path):
+    """include/bta.h is self-contained C99: a C program that includes only it
+    compiles with -Wall -Werror, links libbta.so and gets the host-side
+    answers (no GPU needed)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("cc") or shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_bta.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "use_bta"
+    libdir = os.path.dirname(lib._name)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                        "-L", libdir, "-lbta", "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    env = dict(os.environ)
+    cuda_lib = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64")
+    env["LD_LIBRARY_PATH"] = cuda_lib + os.pathsep + env.get("LD_LIBRARY_PATH", "")
+    r = subprocess.run([str(exe)], capture_output=True, text=True, env=env)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.strip() == "invalid argument|call out of order"

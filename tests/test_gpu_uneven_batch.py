@@ -71,7 +71,8 @@ def _run_multi(setup, names, precision, with_grad):
             gs.append(torch.zeros((3, d["thetas"].shape[1]), dtype=torch.float64, device="cuda"))
         else:
             mus.append(torch.zeros((3, p.N), dtype=torch.float64, device="cuda"))
-    torch.cuda.synchronize()
+    # no synchronisation here: the thetas and zeroed outputs were queued on the
+    # current stream, which every problem's stream waits for inside the call
     bta.bta_fobj_eval_multi(ctxs, models, ths, fs, mu_outs=None if with_grad else mus,
                             grad_outs=gs if with_grad else None)
     torch.cuda.current_stream().synchronize()

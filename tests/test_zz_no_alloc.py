@@ -1,6 +1,7 @@
 """The allocation-free entry point bta_chol_inv_noalloc against the existing
 path (bta_factor of a one-block BTA matrix, which runs the same recursive
-Cholesky + inverse on workspace that the context allocated).
+Cholesky + inverse on workspace that the context allocated) and against the
+plain definitions (LAPACK Cholesky and inverse of the same matrix).
 
 Callers that may not call cudaMalloc -- a framework whose memory pool owns
 the device budget, a serving loop that cannot take cudaMalloc's
@@ -55,9 +56,12 @@ def test_noalloc_matches_existing_entry_point_twice():
         pytest.skip("no CUDA device")
     from paper_2507_06938_gb300 import _build
     _build.build()
-    for b, seed in ((300, 1), (1000, 2)):
+    for b, seed in ((300, 1), (1000, 2), (2048, 5)):
         S = _spd(b, seed)
         L_ref, X_ref = _existing_path(S)
+        # the definitions: S = L L^T with positive diagonal, X = L^{-1}
+        L_np = np.linalg.cholesky(S)
+        X_np = np.linalg.inv(L_np)
         for call in range(2):
             L, X, info = _noalloc(S)
             assert info == -1
@@ -65,10 +69,13 @@ def test_noalloc_matches_existing_entry_point_twice():
             scale_x = np.max(np.abs(X_ref))
             assert np.max(np.abs(L - L_ref)) <= 1e-9 * scale_l, (b, call)
             assert np.max(np.abs(X - X_ref)) <= 1e-9 * scale_x, (b, call)
+            assert np.max(np.abs(L - L_np)) <= 1e-9 * np.max(np.abs(L_np)), (b, call)
+            assert np.max(np.abs(X - X_np)) <= 1e-9 * np.max(np.abs(X_np)), (b, call)
             assert np.all(np.triu(X, 1) == 0.0)
 
 
-def test_noalloc_reports_pivot_and_rejects_large_blocks():
+def test_noalloc_reports_pivot_and_rejects_bad_arguments():
+    import ctypes
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -81,6 +88,24 @@ def test_noalloc_reports_pivot_and_rejects_large_blocks():
     # the following call starts from a cleared status word
     _, _, info = _noalloc(_spd(200, 4))
     assert info == -1
-    big = torch.zeros((bta.NOALLOC_MAX_B + 1, 1), dtype=torch.float64, device="cuda")
+    f64 = dict(dtype=torch.float64, device="cuda")
+    info = torch.zeros(1, dtype=torch.int64, device="cuda")
+    big = torch.zeros((bta.NOALLOC_MAX_B + 1, bta.NOALLOC_MAX_B + 1), **f64)
     with pytest.raises(ValueError):
-        bta.bta_chol_inv_noalloc(big, big, torch.zeros(1, dtype=torch.int64, device="cuda"))
+        bta.bta_chol_inv_noalloc(big, big, info)
+    # non-square A, undersized X, empty info: rejected before the library is called
+    with pytest.raises(ValueError):
+        bta.bta_chol_inv_noalloc(torch.zeros((64, 32), **f64), torch.zeros((64, 64), **f64), info)
+    with pytest.raises(ValueError):
+        bta.bta_chol_inv_noalloc(torch.zeros((64, 64), **f64), torch.zeros((64, 32), **f64), info)
+    with pytest.raises(ValueError):
+        bta.bta_chol_inv_noalloc(torch.zeros((64, 64), **f64), torch.zeros((64, 64), **f64),
+                                 torch.zeros(0, dtype=torch.int64, device="cuda"))
+    # the C entry point itself refuses an order above its fixed workspace and
+    # leading dimensions below the order (host checks, nothing is launched)
+    lib = bta.lib()
+    A = torch.zeros((64, 64), **f64)
+    assert lib.bta_chol_inv_noalloc(A.data_ptr(), bta.NOALLOC_MAX_B + 1, bta.NOALLOC_MAX_B + 1, A.data_ptr(),
+                                    bta.NOALLOC_MAX_B + 1, info.data_ptr(), ctypes.c_void_p(None)) == bta.BTA_ERR_ARG
+    assert lib.bta_chol_inv_noalloc(A.data_ptr(), 64, 32, A.data_ptr(), 64, info.data_ptr(),
+                                    ctypes.c_void_p(None)) == bta.BTA_ERR_ARG
