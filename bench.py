@@ -1,20 +1,26 @@
 #!/usr/bin/env python
-"""Throughput of the BTA hot path of one f_obj(theta) evaluation on GB300.
+"""Throughput of the BTA hot path of f_obj(theta) evaluations on GB300.
 
-One step = one batch of 2 dim(theta) + 1 = 9 theta points (the stencil of
-Eq. 10) of the univariate AR(1) x SPDE model at working size (32 x 32 grid
-mesh: ns = 1024, nt = 64, nb = 4 fixed effects, m = 65,536 observations,
-N = 65,540), each with the whole hot path: assembly, factorisation and
+Default workload: the large trivariate coregional model on an irregular mesh
+(3 AR(1) x SPDE Matern fields mixed by a lower-triangular Lambda, Delaunay
+mesh of 2000 seeded points in the unit square: b = 6000, nt = 48, nb = 6
+fixed effects, m = 144,000 observations, N = 288,006).  One step = one
+theta point with the whole hot path: assembly, factorisation and
 log-determinant of Q_p and Q_c, the conditional-mean solve, f_obj, the
-selected inversion of Q_p and Q_c and the adjoint gradient of f_obj.  All 18
-BTA matrices of a step go through the same kernel launches.  Each step uses a
-different stencil centre.
+selected inversion of Q_p and Q_c and the adjoint gradient of f_obj.  The
+2 dim(theta) + 1 = 31 points of the central-difference stencil (Eq. 10) do
+not fit together at this size (about 192 GB of blocks per point), so a step
+takes one point, each step a different one.  Smaller workloads (--config)
+evaluate as many stencil points per step as fit.
 
 value  = f_obj evaluations / s with inputs resident in HBM (device-timed)
-e2e    = the same through the C ABI with the thetas copied host->device and
-         f, mu and the marginal variances copied device->host inside the
-         timed region (pinned host buffers)
---impl reference times the CPU FP64 oracle (oracle/) on the host cores.
+e2e    = the same through the host-buffer C-ABI call bta_fobj_grad_host:
+         thetas copied host->device, f, the gradient and the marginal
+         variances of Q_c copied back, inside the timed region
+The mixed-precision line also carries the FP64 path on the same thetas
+(`fp64`), the error of every mixed output against it (`errors`), the
+roofline of the dominant kernel and the CPU oracle on a stated sample
+(`cpu_baseline`).  --impl reference times that oracle sample alone.
 """
 
 from __future__ import annotations
@@ -35,36 +41,47 @@ sys.path.insert(0, ROOT)
 METRIC = "f_obj evals/s and BTA Cholesky+selinv TFLOP/s: mixed vs FP64 on one GB300"
 UNIT = "f_obj evals/s"
 L2_BYTES = 129e6
+CONFIG_NAME = "c5"
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_hi": 2}
+SLICES = {"mixed": 5, "mixed_hi": 7}
+FP64_COMPARE_STEPS = 2        # timed FP64 steps (after one warm-up) of the mixed-precision line
+CPU_SAMPLE_BLOCKS = 2         # time blocks of the oracle sample
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+PEAKS = _measured_peaks()
+# sustained bf16 tensor rate: the products are timed inside a step of seconds
+BF16_PEAK_TFLOPS = float(PEAKS.get("bf16_tflops_sustained", 1700.0))
+BF16_PEAK_SOURCE = ("measured bf16 dense, sustained (MEASURED_PEAKS.json), of measured"
+                    if "bf16_tflops_sustained" in PEAKS else "fallback sustained bf16 of the profiling recipe")
 
 
 def workload(p, B) -> str:
     """The measured workload, described from the problem itself."""
     kind = "univariate AR(1) x SPDE Matern" if p.nv == 1 else f"{p.nv}-variate coregional AR(1) x SPDE Matern"
-    return (f"{kind}, mesh ns={p.ns}, nt={p.nt}, nb={p.a} fixed effects, m={int(p.y.shape[0])} observations, "
-            f"N={p.N}; per step: {B} theta points (2 dim(theta)+1 stencil), each assemble+factor+log-det of "
-            "Q_p and Q_c, conditional-mean solve, f_obj, selected inversion of Q_p and Q_c, adjoint gradient")
+    mesh = "Delaunay mesh of seeded uniform points" if p.name.startswith("c5") else "regular grid mesh"
+    return (f"{kind}, {mesh}, ns={p.ns}, b={p.b}, nt={p.nt}, nb={p.a} fixed effects, m={int(p.y.shape[0])} "
+            f"observations, N={p.N}; per step: {B} theta point(s), each assemble+factor+log-det of Q_p and Q_c, "
+            "conditional-mean solve, f_obj, selected inversion of Q_p and Q_c, adjoint gradient")
+
+
+def matrix_bytes(p) -> float:
+    """Device bytes of one BTA matrix with factor, inverse diagonal blocks,
+    selected inverse and scratch."""
+    bb = float(p.b) * p.b
+    return 8.0 * (3 * (2 * p.nt - 1) * bb + p.nt * bb + 1.5 * bb)
 
 
 def l2_note(p, B) -> str:
     per = (2 * p.nt - 1) * p.b * p.b * 8.0
     rel = "larger" if 2 * B * per > L2_BYTES else "smaller"
-    return f"inputs {rel} than L2 (BTA blocks ~{per / 1e9:.3g} GB per matrix, {2 * B} matrices)"
-
-
-CONFIG_NAME = "c2"
-# FP64 peak of the GB300: the nominal FP64 rate (no FP64 figure is measured by
-# the driver); a DFMA throughput probe on this pool read 1.20 TFLOP/s at 1995 MHz.
-FP64_PEAK_TFLOPS = 1.25
-
-
-def _measured_bf16():
-    try:
-        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
-    except (OSError, ValueError, KeyError):
-        return 1900.0   # fallback figure of the profiling recipe
-
-
-BF16_PEAK_TFLOPS = _measured_bf16()
+    return f"inputs {rel} than L2 (BTA blocks ~{per / 1e9:.3g} GB per matrix, {2 * B} matrices), no flush needed"
 
 
 def parse():
@@ -73,9 +90,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed_hi", choices=sorted(PRECISIONS))
     ap.add_argument("--config", default=CONFIG_NAME)
-    ap.add_argument("--batch", type=int, default=0, help="theta points per step (default 2 dim(theta) + 1)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="theta points per step (default: as many of the 2 dim(theta) + 1 as fit)")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the host-buffer (end-to-end) timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-compare", action="store_true",
@@ -162,18 +181,24 @@ def kernel_source_sha1(source: str, region=None):
     return hashlib.sha1(text).hexdigest()
 
 
-def traffic_record(kernel_key: str):
-    """DRAM bytes per launch of the dominant kernel from a committed ncu summary,
-    null if the kernel's source changed since the capture."""
+def traffic_record(kernel_key: str, shape: dict):
+    """DRAM bytes per launch of the dominant operation from a committed ncu
+    summary, for exactly this launch shape (kernel, M, N, K, batch, digit
+    slices); null if no capture has this shape or the kernel's source changed
+    since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(path)).get(kernel_key)
-    except (OSError, ValueError):
+        recs = json.load(open(path)).get("records", [])
+    except (OSError, ValueError, AttributeError):
         return None
-    if not rec:
-        return None
-    h = kernel_source_sha1(rec["source"], rec.get("region"))
-    return rec["bytes_per_launch"] if h is not None and h == rec["source_sha1"] else None
+    for rec in recs:
+        if rec.get("kernel") != kernel_key:
+            continue
+        if any(rec.get(k) != v for k, v in shape.items()):
+            continue
+        h = kernel_source_sha1(rec["source"], rec.get("region"))
+        return rec["bytes_per_launch"] if h is not None and h == rec["source_sha1"] else None
+    return None
 
 
 def cpu_threads():
@@ -185,18 +210,6 @@ def cpu_threads():
     except Exception:
         pass
     return os.cpu_count()
-
-
-def oracle_step(problem, theta, fd):
-    """One theta point of the workload on the CPU oracle (tier B): f_obj and the
-    selected inversion of Q_p and Q_c (the inputs of the adjoint gradient)."""
-    from oracle import bta as obta
-    from oracle import fobj as ofobj
-    terms = ofobj.f_obj_terms(problem, theta, tier="bta", fd=fd)
-    built = terms["built"]
-    for Q in (built.Qp, built.Qc):
-        obta.selinv(obta.factor(obta.blocks_from_sparse(Q, problem.nt, problem.b, problem.a)))
-    return terms["f"]
 
 
 def stencil(center, h=1e-3):
@@ -233,90 +246,168 @@ def job_throughput(steps, world, batch, ms):
     return steps * world * batch / (ms / 1e3)
 
 
+def flops_per_eval(p):
+    from paper_2507_06938_gb300 import bta
+    return 2 * bta.bta_flops_factor(p.nt, p.b, p.a) + 2 * bta.bta_flops_selinv(p.nt, p.b, p.a)
+
+
+def default_batch(p, requested):
+    """Stencil points per step: as many of the 2 dim + 1 as fit in 85 % of the
+    free device memory (two matrices per point)."""
+    import torch
+    if requested:
+        return requested
+    free, _ = torch.cuda.mem_get_info()
+    fit = int(0.85 * free // (2 * matrix_bytes(p)))
+    return max(1, min(2 * p.theta0.shape[0] + 1, fit))
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+
+class OracleSample:
+    """The CPU FP64 oracle (block tier) on a bounded sample of the workload:
+    factorisation and selected inversion of the BTA matrix made of the first
+    CPU_SAMPLE_BLOCKS time blocks of Q_c (with the arrow), scaled to one
+    f_obj evaluation by the nominal flop model (2 F_fact + 2 F_selinv of the
+    full matrices)."""
+
+    def __init__(self, p, theta):
+        from oracle import bta as obta
+        from oracle import model as omodel
+        self.p = p
+        import numpy as np
+        k = min(CPU_SAMPLE_BLOCKS, p.nt)
+        built = omodel.build(p, omodel.theta_to_params(theta, p.nv), omodel.fem_data(p))
+        # the leading k time blocks and the arrow: a BTA matrix of k blocks
+        keep = np.concatenate([np.arange(k * p.b), p.nt * p.b + np.arange(p.a)])
+        Qk = built.Qc.tocsr()[keep][:, keep]
+        self.blk = obta.blocks_from_sparse(Qk, k, p.b, p.a)
+        from paper_2507_06938_gb300 import bta
+        self.k = k
+        self.sample_flops = bta.bta_flops_factor(k, p.b, p.a) + bta.bta_flops_selinv(k, p.b, p.a)
+        self.eval_flops = flops_per_eval(p)
+
+    def run(self) -> float:
+        """Seconds for one sample."""
+        from oracle import bta as obta
+        t0 = time.perf_counter()
+        obta.selinv(obta.factor(self.blk))
+        return time.perf_counter() - t0
+
+    def evals_per_s(self, seconds) -> float:
+        return (self.sample_flops / seconds) / self.eval_flops
+
+    def describe(self) -> str:
+        return (f"oracle block tier (numpy/scipy FP64) factor + selected inversion of the first {self.k} time "
+                f"blocks of Q_c (b={self.p.b}, with the {self.p.a}-wide arrow; {self.sample_flops / 1e12:.3g} "
+                f"nominal TFLOP), scaled to one f_obj evaluation ({self.eval_flops / 1e12:.4g} nominal TFLOP: "
+                "2 F_fact + 2 F_selinv)")
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import synth
-    from oracle import model as omodel
     p = synth.problem_from_config(args.config)
-    fd = omodel.fem_data(p)
-    # bounded sample: one theta point of each step's stencil (the oracle takes
-    # tens of seconds per point at this size); value in f_obj evaluations / s
-    thetas = thetas_for(p, args.warmup + args.steps, 0)
-    for j in range(min(args.warmup, 1)):     # the CPU path has nothing further to warm up
-        oracle_step(p, thetas[j][0], fd)
-    t0 = time.perf_counter()
-    for j in range(args.steps):
-        oracle_step(p, thetas[args.warmup + j][0], fd)
-    dt = time.perf_counter() - t0
-    value = args.steps / dt
+    theta = thetas_for(p, 1, 0)[0][0]
+    sample = OracleSample(p, theta)
+    for _ in range(min(args.warmup, 1)):     # the CPU path has nothing further to warm up
+        sample.run()
+    secs = [sample.run() for _ in range(args.steps)]
+    dt = sum(secs)
+    value = sample.evals_per_s(dt / args.steps)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload(p, len(thetas[0])), "name": args.config},
+        "data": "synthetic", "config": {"workload": workload(p, 1), "name": args.config},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                         "sample": "one theta point (f_obj + selinv of Q_p and Q_c) of each step's 9 points, "
-                                   "numpy/scipy FP64 block recurrences"},
+                         "sample": sample.describe()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
 
 
-def _roofline(precision, prof_ms, prof_n, prof_flops):
-    """Roofline record of the dominant kernel from the profiling events of the
-    last timed step (the graph replays the same launches every step)."""
+# ----------------------------------------------------------------------------- GPU measurement
+
+def _roofline(precision_name, prof, p, B, fp64_peak):
+    """Roofline record of the dominant operation from the profiling events of
+    the last timed step: the two b x b x b Schur-update products of every
+    factorisation step (batched over the step's matrices)."""
+    prof_ms, prof_n, prof_flops = prof
     achieved = (prof_flops / (prof_ms / 1e3) / 1e12) if prof_ms > 0 else None
-    if precision == "fp64":
+    shape = {"M": p.b, "N": p.b, "K": p.b, "batch": 2 * B}
+    if precision_name == "fp64":
+        peak = fp64_peak.get("dfma")
         return {
             "bound": "alu", "kernel": "gemm64_kernel (FP64 DFMA Schur-update GEMMs L_{i+1,i}=B_i L_ii^-T and "
                                       "D_{i+1}-=L L^T, batched over the step's matrices)",
-            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-            "traffic": traffic_record("gemm64_bxbxb"),
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved and peak else None,
+            "traffic": traffic_record("gemm64_bxbxb", dict(shape, slices=0)),
             "launches_timed": prof_n, "flops_per_launch": (prof_flops / prof_n) if prof_n else None,
-            "peak_source": "nominal GB300 FP64 rate (no FP64 entry in the measured peaks)",
+            "peak_source": "FP64 DFMA loop measured in this run (bta_fp64_peak), of measured",
         }
-    # executed bf16 tensor flops: 15 digit-pair products per FP64-equivalent flop
-    tensor = 15.0 * achieved if achieved else None
-    peak = BF16_PEAK_TFLOPS
+    S = SLICES[precision_name]
+    pairs = S * (S + 1) // 2
+    tensor = pairs * achieved if achieved else None
     return {
-        "bound": "tensor", "kernel": "ozaki_gemm (digit split + tcgen05 bf16 15-pair products) for the "
-                                    "Schur-update GEMMs, batched over the step's matrices",
-        "achieved": tensor, "peak": peak, "unit": "TFLOP/s", "frac": (tensor / peak) if tensor else None,
+        "bound": "tensor", "kernel": f"ozaki split product ({S}-slice digit split + tcgen05 bf16 kernel, {pairs} "
+                                     "digit pairs) of the Schur-update GEMMs, batched over the step's matrices",
+        "achieved": tensor, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": (tensor / BF16_PEAK_TFLOPS) if tensor else None,
         "achieved_fp64_equivalent": achieved,
-        "traffic": traffic_record("ozaki_bxbxb"),
+        "traffic": traffic_record("ozaki_bxbxb", dict(shape, slices=S)),
         "launches_timed": prof_n, "flops_per_launch": (prof_flops / prof_n) if prof_n else None,
-        "peak_source": "measured bf16 dense (burst) of this pool, of measured",
+        "peak_source": BF16_PEAK_SOURCE,
     }
 
 
-def measure(args, precision_name, warmup, steps, with_e2e, dist, rank, world, local):
-    """Time `steps` batched f_obj+gradient+selinv steps of one precision after
-    `warmup` untimed ones; returns the measurements of this rank."""
+SIGMA_SAMPLE = (("D", 0), ("D", "mid"), ("D", "last"), ("B", 0), ("B", "mid"), ("R", "mid"), ("T", 0))
+
+
+def _sigma_samples(ctx, p, slot):
+    """Host copies of a few selected-inverse blocks of Q_p and Q_c of a slot."""
+    from paper_2507_06938_gb300 import bta
+    kinds = {"D": bta.BTA_BLK_D, "B": bta.BTA_BLK_B, "R": bta.BTA_BLK_R, "T": bta.BTA_BLK_T}
+    out = {}
+    for kind in (bta.BTA_QP, bta.BTA_QC):
+        for k, i in SIGMA_SAMPLE:
+            idx = {"mid": p.nt // 2 - 1, "last": p.nt - 1}.get(i, i)
+            if k == "B" and p.nt < 2:
+                continue
+            out[(kind, k, idx)] = ctx.block(2 * slot + kind, bta.BTA_STORE_SIGMA, kinds[k], idx).cpu().numpy()
+    return out
+
+
+def measure(args, precision_name, warmup, steps, e2e_steps, dist, rank, world, local, fixed_theta=None):
+    """Time `steps` f_obj+gradient+selinv steps of one precision after
+    `warmup` untimed ones; returns this rank's measurements and the outputs
+    of the last step."""
     import numpy as np
     import torch
     from paper_2507_06938_gb300 import bta
     import synth
 
     p = synth.problem_from_config(args.config)
-    precision = bta.BTA_FP64 if precision_name == "fp64" else bta.BTA_MIXED
-    B = args.batch or (2 * p.theta0.shape[0] + 1)
+    precision = PRECISIONS[precision_name]
+    B = default_batch(p, args.batch)
+    dim = p.theta0.shape[0]
     stream = torch.cuda.Stream()
     model = bta.BtaModel(p)
     ctx = bta.BtaContext(p.nt, p.b, p.a, precision, stream, B)
     tuned = None if args.no_autotune else ctx.autotune(reps=2)
     nsteps = warmup + steps
-    thetas_h = np.stack([t[:B] if t.shape[0] >= B else np.resize(t, (B, t.shape[1]))
-                         for t in thetas_for(p, nsteps, rank)])          # steps x B x dim
+    if fixed_theta is not None:
+        # the same group of B points every step (B x dim)
+        thetas_h = np.repeat(np.asarray(fixed_theta)[None, :, :], nsteps, axis=0)
+    else:
+        thetas_h = np.stack([t[:B] if t.shape[0] >= B else np.resize(t, (B, dim))
+                             for t in thetas_for(p, nsteps, rank)])          # steps x B x dim
     thetas_d = torch.tensor(thetas_h, dtype=torch.float64, device="cuda")
     f_d = torch.zeros((nsteps, B), dtype=torch.float64, device="cuda")
-    g_d = torch.zeros((nsteps, B, p.theta0.shape[0]), dtype=torch.float64, device="cuda")
-    var_d = torch.zeros((B, p.N), dtype=torch.float64, device="cuda")
-
-    def step(j, theta_dev, f_out):
-        ctx.fobj_grad(model, theta_dev, f_out, g_d[j])
+    g_d = torch.zeros((nsteps, B, dim), dtype=torch.float64, device="cuda")
 
     def barrier_sync():
         torch.cuda.synchronize()
@@ -330,7 +421,7 @@ def measure(args, precision_name, warmup, steps, with_e2e, dist, rank, world, lo
         # the timed steps replay is captured with them during the warm-up
         ctx.profile(True)
         for j in range(warmup):
-            step(j, thetas_d[j], f_d[j])
+            ctx.fobj_grad(model, thetas_d[j], f_d[j], g_d[j])
         ctx.sync()
         barrier_sync()
         # ---- device-resident timed region
@@ -339,8 +430,8 @@ def measure(args, precision_name, warmup, steps, with_e2e, dist, rank, world, lo
         e1 = torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
             e0.record(stream)
-            for j in range(steps):
-                step(warmup + j, thetas_d[warmup + j], f_d[warmup + j])
+            for j in range(warmup, nsteps):
+                ctx.fobj_grad(model, thetas_d[j], f_d[j], g_d[j])
             e1.record(stream)
             e1.synchronize()
         ctx.sync()
@@ -349,43 +440,68 @@ def measure(args, precision_name, warmup, steps, with_e2e, dist, rank, world, lo
         ctx.profile(False)
         out["ms"] = e0.elapsed_time(e1)
         out["clocks"] = clk.summary()
+        # outputs of the last step (slot 0 = its first theta)
+        ld = torch.zeros(2, dtype=torch.float64, device="cuda")
+        ctx.logdet(bta.BTA_QP, ld[0:1])
+        ctx.logdet(bta.BTA_QC, ld[1:2])
+        res = torch.zeros(B, dtype=torch.float64, device="cuda")
+        ctx.fobj_residual(res)
+        ctx.sync()
+        out["last"] = dict(theta=thetas_h[-1][0].copy(), group=thetas_h[-1].copy(), f=f_d[-1][0].item(), g=g_d[-1][0].cpu().numpy(),
+                           ld_p=ld[0].item(), ld_c=ld[1].item(), resid=res[0].item(),
+                           sigma=_sigma_samples(ctx, p, 0))
         barrier_sync()
         out["ms_e2e"] = None
-        if with_e2e:
-            # ---- end-to-end through the C ABI with host buffers
-            th_pin = torch.tensor(thetas_h, dtype=torch.float64).pin_memory()
-            f_pin = torch.zeros((steps, B), dtype=torch.float64).pin_memory()
-            g_pin = torch.zeros((steps, B, p.theta0.shape[0]), dtype=torch.float64).pin_memory()
+        if e2e_steps > 0:
+            # ---- end to end through the host-buffer C-ABI call
+            th_pin = torch.tensor(thetas_h[warmup:warmup + e2e_steps], dtype=torch.float64).pin_memory()
+            f_pin = torch.zeros((e2e_steps, B), dtype=torch.float64).pin_memory()
+            g_pin = torch.zeros((e2e_steps, B, dim), dtype=torch.float64).pin_memory()
             var_pin = torch.zeros((B, p.N), dtype=torch.float64).pin_memory()
-            theta_stage = torch.zeros((B, p.theta0.shape[0]), dtype=torch.float64, device="cuda")
-            g0 = torch.cuda.Event(enable_timing=True)
-            g1 = torch.cuda.Event(enable_timing=True)
-            g0.record(stream)
-            for j in range(steps):
-                theta_stage.copy_(th_pin[warmup + j], non_blocking=True)
-                ctx.fobj_grad(model, theta_stage, f_d[j], g_d[j])
-                for k in range(B):
-                    ctx.selinv_diag(2 * k + bta.BTA_QC, var_d[k])
-                f_pin[j].copy_(f_d[j], non_blocking=True)
-                g_pin[j].copy_(g_d[j], non_blocking=True)
-                var_pin.copy_(var_d, non_blocking=True)
-            g1.record(stream)
-            g1.synchronize()
-            ctx.sync()
-            out["ms_e2e"] = g0.elapsed_time(g1)
+            t0 = time.perf_counter()
+            for j in range(e2e_steps):
+                ctx.fobj_grad_host(model, th_pin[j], f_pin[j], g_pin[j], var_pin)
+            out["ms_e2e"] = 1e3 * (time.perf_counter() - t0)
+            out["e2e_steps"] = e2e_steps
     ctx.close()
     model.close()
-    del thetas_d, f_d, g_d, var_d
+    del thetas_d, f_d, g_d
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     out["ms"], out["ms_e2e"] = max_over_ranks([out["ms"], out["ms_e2e"] or 0.0], dist, "cuda")
     total_evals = steps * world * B
     out["value"] = job_throughput(steps, world, B, out["ms"])
-    out["e2e_value"] = job_throughput(steps, world, B, out["ms_e2e"]) if with_e2e else None
-    flops_eval = 2 * bta.bta_flops_factor(p.nt, p.b, p.a) + 2 * bta.bta_flops_selinv(p.nt, p.b, p.a)
-    out["tflops"] = flops_eval * total_evals / (out["ms"] / 1e3) / 1e12
-    out["roofline"] = _roofline(precision_name, *out["prof"])
+    out["e2e_value"] = job_throughput(e2e_steps, world, B, out["ms_e2e"]) if e2e_steps > 0 else None
+    out["tflops"] = flops_per_eval(p) * total_evals / (out["ms"] / 1e3) / 1e12
     return out
+
+
+def errors_against(mixed_last, ref_last):
+    """Error of every mixed-precision output against the FP64 path at the same
+    theta (log-dets relative, Sigma blocks relative to the block maximum,
+    gradient relative to max(|g_k|, 1e-3 |g|_inf)); the mean's own FP64
+    residual is reported by the library (bta_fobj_residual)."""
+    import numpy as np
+    g_ref = ref_last["g"]
+    scale = np.maximum(np.abs(g_ref), 1e-3 * np.max(np.abs(g_ref)))
+    sig = []
+    for key, blk in ref_last["sigma"].items():
+        m = float(np.max(np.abs(blk)))
+        if m > 0:
+            sig.append(float(np.max(np.abs(mixed_last["sigma"][key] - blk))) / m)
+    return {
+        "logdet_p_rel": abs(mixed_last["ld_p"] - ref_last["ld_p"]) / max(abs(ref_last["ld_p"]), 1.0),
+        "logdet_c_rel": abs(mixed_last["ld_c"] - ref_last["ld_c"]) / max(abs(ref_last["ld_c"]), 1.0),
+        "f_abs": abs(mixed_last["f"] - ref_last["f"]),
+        "f_rel_to_logdets": abs(mixed_last["f"] - ref_last["f"]) / (abs(ref_last["ld_p"]) + abs(ref_last["ld_c"])),
+        "solve_residual": mixed_last["resid"],
+        "solve_residual_fp64": ref_last["resid"],
+        "sigma_block_rel_max": max(sig) if sig else None,
+        "sigma_blocks_compared": len(sig),
+        "grad_rel_max": float(np.max(np.abs(mixed_last["g"] - g_ref) / scale)),
+        "reference": "FP64 path of this library at the same theta (the last timed mixed step's)",
+        "targets": {"logdet_rel": 1e-8, "solve_residual": 1e-10},
+    }
 
 
 def run_ours(args):
@@ -400,56 +516,64 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    from paper_2507_06938_gb300 import _build
+    from paper_2507_06938_gb300 import _build, bta
     if rank == 0 or world == 1:
         _build.build()
     if dist is not None:
         dist.barrier()
 
-    r = measure(args, args.precision, args.warmup, args.steps, True, dist, rank, world, local)
+    fp64_peak = {"dfma": bta.bta_fp64_peak(False), "dmma": bta.bta_fp64_peak(True)}
+    r = measure(args, args.precision, args.warmup, args.steps, args.e2e_steps, dist, rank, world, local)
+    r["roofline"] = _roofline(args.precision, r["prof"], r["problem"], r["B"], fp64_peak)
     cmp = None
-    if args.precision == "mixed" and not args.no_compare:
-        # the FP64 path on the same workload, shorter (one FP64 step takes seconds)
-        cmp = measure(args, "fp64", 1, 1, False, dist, rank, world, local)
+    if args.precision != "fp64" and not args.no_compare:
+        # the FP64 path at the theta of the last timed mixed step (one warm-up,
+        # FP64_COMPARE_STEPS timed; an FP64 step takes tens of seconds here)
+        cmp = measure(args, "fp64", 1, FP64_COMPARE_STEPS, 0, dist, rank, world, local,
+                      fixed_theta=r["last"]["group"])
+        cmp["roofline"] = _roofline("fp64", cmp["prof"], cmp["problem"], cmp["B"], fp64_peak)
     p, B = r["problem"], r["B"]
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
+    dtype = {"fp64": "f64", "mixed": "mixed (f64 with 35-bit bf16-digit tensor-core products)",
+             "mixed_hi": "mixed (f64 with 49-bit bf16-digit tensor-core products)"}[args.precision]
+    dim = p.theta0.shape[0]
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "mixed (f64 with bf16-digit tensor-core products)",
-        "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": workload(p, B), "name": args.config, "precision": args.precision, "theta_points": B,
                    "l2": l2_note(p, B),
                    "parallelism": f"replicas x{world} (independent theta points per GPU)"},
         "tflops": r["tflops"], "tflops_unit": "nominal (2 F_fact + 2 F_selinv) per f_obj evaluation / time",
         "roofline": r["roofline"],
-        "e2e": {"value": r["e2e_value"], "unit": UNIT, "h2d_bytes_per_step": int(B * p.theta0.shape[0] * 8),
-                "d2h_bytes_per_step": int(B * (8 + p.theta0.shape[0] * 8 + p.N * 8))},
+        "e2e": {"value": r["e2e_value"], "unit": UNIT, "steps": r.get("e2e_steps"),
+                "call": "bta_fobj_grad_host (pinned host thetas in; f, gradient, marginal variances out)",
+                "h2d_bytes_per_step": int(B * dim * 8),
+                "d2h_bytes_per_step": int(B * (8 + dim * 8 + p.N * 8))},
         "batch": B,
         "autotuned": (None if r["tuned"] is None else
                       dict(zip(("fp64_leaf", "df32_leaf", "tensor_min_dim"), r["tuned"]))),
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
+        "fp64_peak_measured": {"dfma_tflops": fp64_peak["dfma"], "dmma_tflops": fp64_peak["dmma"],
+                               "how": "bta_fp64_peak: FP64 FMA loop / m8n8k4 FP64 MMA loop over every SM, "
+                                      "CUDA events, after one warm-up launch"},
     }
     if cmp is not None:
-        line["fp64"] = {"value": cmp["value"], "unit": UNIT, "ms_per_step": cmp["ms"], "steps": 1, "warmup": 1,
-                        "tflops": cmp["tflops"], "roofline": cmp["roofline"], "gpu_launches": int(cmp["launches"]),
+        line["fp64"] = {"value": cmp["value"], "unit": UNIT, "ms_per_step": cmp["ms"] / FP64_COMPARE_STEPS,
+                        "steps": FP64_COMPARE_STEPS, "warmup": 1, "tflops": cmp["tflops"],
+                        "roofline": cmp["roofline"], "gpu_launches": int(cmp["launches"]),
                         "clocks": cmp["clocks"], "mixed_over_fp64": r["value"] / cmp["value"]}
+        line["errors"] = errors_against(r["last"], cmp["last"])
     if world == 1 and not args.no_cpu_baseline:
-        from oracle import model as omodel
-        fd = omodel.fem_data(p)
-        th = r["thetas_h"][args.warmup][0]
-        t0 = time.perf_counter()
-        oracle_step(p, th, fd)
-        dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                                "sample": "one theta point (f_obj + selinv of Q_p and Q_c) on the FP64 "
-                                          "numpy/scipy block recurrences"}
+        sample = OracleSample(p, r["last"]["theta"])
+        dt = sample.run()
+        line["cpu_baseline"] = {"value": sample.evals_per_s(dt), "unit": UNIT, "cores": cpu_threads(),
+                                "kind": "oracle", "sample": sample.describe(), "sample_seconds": dt}
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -63,7 +63,11 @@ extern "C" {
 
 /* Arithmetic of the factorisation / selected inversion. */
 #define BTA_FP64 0           /* every operation in FP64                          */
-#define BTA_MIXED 1          /* tensor-core split-precision Schur updates        */
+#define BTA_MIXED 1          /* tensor-core split-precision products, 35-bit
+                                digits (5 bf16 slices per FP64 value)           */
+#define BTA_MIXED_HI 2       /* the same with 49-bit digits (7 slices), for
+                                ill-conditioned models (irregular meshes whose
+                                precision has a condition number near 1e10)     */
 
 /* Block kinds for bta_block_ptr. */
 #define BTA_BLK_D 0
@@ -127,7 +131,7 @@ int bta_model_dims(bta_model_t model, int* n, int* b, int* a, int* dim_theta);
 /*
  * bta_create -- a context for BTA matrices with n diagonal blocks of size b
  * and arrow tip a (n >= 1, b >= 1, a >= 0), the arithmetic `precision`
- * (BTA_FP64 or BTA_MIXED) and the CUDA stream `stream` (a cudaStream_t; NULL
+ * (BTA_FP64, BTA_MIXED or BTA_MIXED_HI) and the CUDA stream `stream` (a cudaStream_t; NULL
  * = legacy default stream).  The context allocates and owns the device
  * storage of Q_p and Q_c, their factors and inverse diagonal factor blocks;
  * selected-inverse storage is allocated on the first bta_selinv of a matrix.
@@ -261,6 +265,20 @@ int bta_fobj_grad(bta_ctx_t ctx, bta_model_t model, const double* thetas_dev, in
                   double* grad_out_dev);
 
 /*
+ * bta_fobj_grad_host -- bta_fobj_grad for a caller whose data lives in host
+ * memory: thetas (host, n_theta x dim(theta) row-major) are copied to the
+ * device, f_obj and its gradient are computed as by bta_fobj_grad, and
+ * f_out (host, n_theta values), grad_out (host, n_theta x dim(theta)) and,
+ * if var_out (host, n_theta x N) is not NULL, the marginal variances
+ * diag(Sigma_c) of every theta (Section III, latent marginals) are copied
+ * back.  Pinned host buffers let the copies run asynchronously.  Returns
+ * when the results are in host memory, with the status of bta_sync.  The
+ * first call allocates the device staging buffers of the context.
+ */
+int bta_fobj_grad_host(bta_ctx_t ctx, bta_model_t model, const double* thetas, int n_theta, double* f_out,
+                       double* grad_out, double* var_out);
+
+/*
  * bta_fobj_eval_multi -- f_obj (and, where asked, its gradient) for `count`
  * independent problems that may differ in shape, e.g. univariate models of
  * several (ns, nt) evaluated together: the independent function evaluations
@@ -292,6 +310,22 @@ int bta_fobj_grad(bta_ctx_t ctx, bta_model_t model, const double* thetas_dev, in
 int bta_fobj_eval_multi(int count, const bta_ctx_t* ctxs, const bta_model_t* models,
                         const double* const* thetas_dev, const int* n_theta, double* const* f_out_dev,
                         double* const* mu_out_dev, double* const* grad_out_dev, void* join);
+
+/* bta_fobj_residual -- accuracy of the conditional means of the last
+ * fobj_eval / bta_fobj_grad group: out_dev (device, batch values) receives
+ * ||b - Q_c mu||_2 / ||b||_2 for every parameter slot (slot j holds theta
+ * (last group start + j)), b = A^T D y, computed in FP64 with the assembled
+ * blocks of Q_c (the refinement residual of Section III-A's solve stated as
+ * an error measure).  BTA_ERR_STATE before the first f_obj evaluation. */
+int bta_fobj_residual(bta_ctx_t ctx, double* out_dev);
+
+/* bta_fp64_peak -- measured FP64 throughput of the current GPU (TFLOP/s),
+ * the denominator of the FP64 path's roofline: a loop of independent FP64
+ * fused multiply-adds (use_dmma = 0) or of FP64 tensor-core MMAs
+ * (mma.sync m8n8k4, use_dmma = 1) over every SM, timed with CUDA events
+ * after one warm-up launch.  Synchronous; allocates and frees a small
+ * device buffer.  Measurement aid, no counterpart in the paper. */
+int bta_fp64_peak(int use_dmma, double* tflops_out);
 
 /* bta_sync -- wait for the context's stream; return the first error the
  * device recorded since the last bta_sync (and clear it), else BTA_OK. */

@@ -131,22 +131,50 @@ def model_derivatives(problem, theta, k, fd=None, h=1e-30):
     return (built.Qp.imag / h).tocsr(), (built.Qc.imag / h).tocsr(), built.rhs.imag / h, built.d.imag / h
 
 
-def grad_adjoint(problem, theta, *, fd=None) -> np.ndarray:
-    """Analytic gradient of f_obj (formula in the module docstring), with
-    Sigma_p, Sigma_c from the dense inverse (small problems)."""
+def trace_on_pattern(S: dict, dQ: sp.spmatrix, n: int, b: int, a: int) -> float:
+    """tr(Sigma dQ) = sum_ij Sigma_ij dQ_ij for symmetric Sigma and a symmetric
+    dQ whose non-zeros lie on the BTA block pattern, from the lower BTA
+    blocks of Sigma: the diagonal blocks and the tip once, the sub-diagonal
+    and arrow blocks twice (their transposes above the diagonal)."""
+    d = bta_mod.blocks_from_sparse(dQ, n, b, a)
+    t = float(np.sum(S["D"] * d["D"])) + float(np.sum(S["T"] * d["T"]))
+    t += 2.0 * float(np.sum(S["B"] * d["B"])) + 2.0 * float(np.sum(S["R"] * d["R"]))
+    return t
+
+
+def grad_adjoint(problem, theta, *, fd=None, tier: str = "dense") -> np.ndarray:
+    """Analytic gradient of f_obj (formula in the module docstring).
+
+    tier "dense": Sigma_p, Sigma_c from the dense inverse (small problems).
+    tier "bta": Sigma_p, Sigma_c on the BTA pattern from the block selected
+    inversion (Section III-A); the traces need no entry outside that pattern,
+    because every dQ has the pattern of Q."""
     fd = model.fem_data(problem) if fd is None else fd
     theta = np.asarray(theta, dtype=np.float64)
-    terms = f_obj_terms(problem, theta, tier="dense", fd=fd)
+    terms = f_obj_terms(problem, theta, tier=tier, fd=fd)
     built = terms["built"]
     mu = terms["mu"]
-    Sp = dense.inverse(built.Qp)
-    Sc = dense.inverse(built.Qc)
+    n, b, a = problem.nt, problem.b, problem.a
+    if tier == "dense":
+        Sp = dense.inverse(built.Qp)
+        Sc = dense.inverse(built.Qc)
+
+        def trace(S, dQ):
+            return float(np.sum(S * dQ.toarray()))
+    elif tier == "bta":
+        Sp = bta_mod.selinv(bta_mod.factor(bta_mod.blocks_from_sparse(built.Qp, n, b, a)))
+        Sc = bta_mod.selinv(bta_mod.factor(bta_mod.blocks_from_sparse(built.Qc, n, b, a)))
+
+        def trace(S, dQ):
+            return trace_on_pattern(S, dQ, n, b, a)
+    else:
+        raise ValueError(tier)
     y = problem.y
     g = np.empty_like(theta)
     for k in range(theta.shape[0]):
         dQp, dQc, drhs, dd = model_derivatives(problem, theta, k, fd)
-        tr_p = float(np.sum(Sp * dQp.toarray()))
-        tr_c = float(np.sum(Sc * dQc.toarray()))
+        tr_p = trace(Sp, dQp)
+        tr_c = trace(Sc, dQc)
         g[k] = (-(theta[k] - problem.theta0[k]) + 0.5 * tr_p - 0.5 * tr_c - 0.5 * float(y @ (dd * y))
                 + float(drhs @ mu) - 0.5 * float(mu @ (dQc @ mu)) + 0.5 * float(np.sum(dd / built.d)))
     return g

@@ -8,5 +8,5 @@ The numerical work lives in ``libbta.so`` (CUDA kernels behind the C ABI of
 
 from . import bta  # noqa: F401
 from .bta import (  # noqa: F401
-    BTA_FP64, BTA_MIXED, BTA_QC, BTA_QP, BtaContext, BtaError, BtaModel,
+    BTA_FP64, BTA_MIXED, BTA_MIXED_HI, BTA_QC, BTA_QP, BtaContext, BtaError, BtaModel,
 )

@@ -23,7 +23,7 @@ _lib = None
 BTA_OK, BTA_ERR_ARG, BTA_ERR_OOM, BTA_ERR_NOT_PD = 0, 1, 2, 3
 BTA_ERR_TIMEOUT, BTA_ERR_NONFINITE, BTA_ERR_CUDA, BTA_ERR_STATE = 4, 5, 6, 7
 BTA_QP, BTA_QC = 0, 1
-BTA_FP64, BTA_MIXED = 0, 1
+BTA_FP64, BTA_MIXED, BTA_MIXED_HI = 0, 1, 2
 BTA_BLK_D, BTA_BLK_B, BTA_BLK_R, BTA_BLK_T = 0, 1, 2, 3
 BTA_STORE_Q, BTA_STORE_L, BTA_STORE_SIGMA, BTA_STORE_LINV = 0, 1, 2, 3
 
@@ -90,6 +90,9 @@ def lib():
         "bta_autotune": (ip, [vp, ip, C.POINTER(C.c_int)]),
         "bta_fobj_eval_multi": (ip, [ip, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(ip),
                                      C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]),
+        "bta_fobj_residual": (ip, [vp, vp]),
+        "bta_fobj_grad_host": (ip, [vp, vp, vp, ip, vp, vp, vp]),
+        "bta_fp64_peak": (ip, [ip, C.POINTER(dp)]),
         "bta_flops_factor": (dp, [ip, ip, ip]),
         "bta_flops_selinv": (dp, [ip, ip, ip]),
     }
@@ -109,7 +112,8 @@ def exported_symbols():
             "bta_strerror", "bta_flops_factor", "bta_flops_selinv", "bta_selinv_diag",
             "bta_launch_count", "bta_profile", "bta_profile_read", "bta_chol_inv_noalloc",
             "bta_create_batched", "bta_batch_size", "bta_factor_batch", "bta_selinv_batch",
-            "bta_last_error_matrix", "bta_fobj_grad", "bta_autotune", "bta_fobj_eval_multi"]
+            "bta_last_error_matrix", "bta_fobj_grad", "bta_autotune", "bta_fobj_eval_multi",
+            "bta_fobj_residual", "bta_fp64_peak", "bta_fobj_grad_host"]
 
 
 def _check(code: int, where: str):
@@ -278,6 +282,28 @@ class BtaContext:
         _check(lib().bta_fobj_grad(self.handle, model.handle, _ptr(thetas), n_theta, _ptr(f_out), _ptr(grad_out)),
                "bta_fobj_grad")
 
+    def fobj_grad_host(self, model: BtaModel, thetas, f_out, grad_out, var_out=None):
+        """bta_fobj_grad_host: host (CPU) arrays in and out; contiguous float64
+        numpy arrays or CPU torch tensors (pinned ones copy asynchronously)."""
+        def hp(a, name):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                if a.is_cuda or not a.is_contiguous() or str(a.dtype) != "torch.float64":
+                    raise TypeError(f"{name}: expected a contiguous CPU float64 tensor")
+                return a.data_ptr()
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+                raise TypeError(f"{name}: expected a C-contiguous float64 array")
+            return a.ctypes.data
+        n_theta = int(thetas.shape[0]) if len(thetas.shape) == 2 else 1
+        _check(lib().bta_fobj_grad_host(self.handle, model.handle, hp(thetas, "thetas"), n_theta,
+                                        hp(f_out, "f_out"), hp(grad_out, "grad_out"), hp(var_out, "var_out")),
+               "bta_fobj_grad_host")
+
+    def fobj_residual(self, out):
+        """||b - Q_c mu|| / ||b|| of every slot's conditional mean (last group)."""
+        _check(lib().bta_fobj_residual(self.handle, _ptr(out)), "bta_fobj_residual")
+
     def sync(self):
         code = lib().bta_sync(self.handle)
         if code != BTA_OK:
@@ -437,6 +463,22 @@ def bta_chol_inv_noalloc(A, X, info, stream=None):
         raise ValueError("bta_chol_inv_noalloc: A, X and info must be on the current CUDA device")
     _check(lib().bta_chol_inv_noalloc(A.data_ptr(), b, b, X.data_ptr(), b, info.data_ptr(),
                                       C.c_void_p(_stream_handle(stream))), "bta_chol_inv_noalloc")
+
+
+def bta_fobj_grad_host(ctx: BtaContext, model: BtaModel, thetas, f_out, grad_out, var_out=None):
+    ctx.fobj_grad_host(model, thetas, f_out, grad_out, var_out)
+
+
+def bta_fobj_residual(ctx: BtaContext, out):
+    ctx.fobj_residual(out)
+
+
+def bta_fp64_peak(use_dmma: bool = False) -> float:
+    """Measured FP64 throughput of the current GPU (TFLOP/s): DFMA loop, or
+    FP64 tensor-core MMA loop when use_dmma."""
+    out = C.c_double()
+    _check(lib().bta_fp64_peak(1 if use_dmma else 0, C.byref(out)), "bta_fp64_peak")
+    return out.value
 
 
 def bta_flops_factor(n: int, b: int, a: int) -> float:

@@ -92,8 +92,10 @@ int ensure_sigma(bta_ctx_t ctx) {
 }
 
 extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch, void* stream, bta_ctx_t* out) {
-    if (!out || n < 1 || b < 1 || a < 0 || batch < 1 || (precision != BTA_FP64 && precision != BTA_MIXED))
+    if (!out || n < 1 || b < 1 || a < 0 || batch < 1 ||
+        (precision != BTA_FP64 && precision != BTA_MIXED && precision != BTA_MIXED_HI))
         return BTA_ERR_ARG;
+    const bool mixed = precision != BTA_FP64;
     *out = nullptr;
     bta_ctx_s* c = new bta_ctx_s();
     c->n = n; c->b = b; c->a = a; c->precision = precision;
@@ -135,14 +137,15 @@ extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch,
     if (cudaMalloc((void**)&c->status, 4 * sizeof(long long)) != cudaSuccess) return fail(BTA_ERR_OOM);
     if (cudaMemset(c->status, 0, 4 * sizeof(long long)) != cudaSuccess) return fail(BTA_ERR_CUDA);
     c->refine = 0;
-    if (precision == BTA_MIXED) {
+    if (mixed) {
         if (cudaMalloc((void**)&c->oz_err, sizeof(int)) != cudaSuccess) return fail(BTA_ERR_OOM);
         if (cudaMemset(c->oz_err, 0, sizeof(int)) != cudaSuccess) return fail(BTA_ERR_CUDA);
         int min_dim = 128;
         if (const char* e = std::getenv("BTA_OZ_MIN")) min_dim = std::atoi(e);
         c->exec.df_leaf = 64;
         if (const char* e = std::getenv("BTA_DF_LEAF")) c->exec.df_leaf = std::atoi(e);
-        const size_t wsb = (size_t)nm * ozaki_workspace_bytes(b, b, b);
+        c->exec.slices = precision == BTA_MIXED_HI ? 7 : 5;
+        const size_t wsb = (size_t)nm * ozaki_workspace_bytes(b, b, b, c->exec.slices);
         if (cudaMalloc(&c->exec.ws, wsb) != cudaSuccess) {
             c->exec.ws = nullptr;
             return fail(BTA_ERR_OOM);
@@ -165,7 +168,7 @@ extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch,
         cudaEventCreateWithFlags(&c->fork->ev3_join, cudaEventDisableTiming) != cudaSuccess)
         return fail(BTA_ERR_CUDA);
     c->fork->ex2 = c->exec;
-    if (precision == BTA_MIXED) {
+    if (mixed) {
         c->fork->ex2.ws = nullptr;
         if (cudaMalloc(&c->fork->ex2.ws, c->exec.ws_bytes) != cudaSuccess) {
             c->fork->ex2.ws = nullptr;
@@ -203,7 +206,7 @@ extern "C" int bta_destroy(bta_ctx_t c) {
         }
         if (c->fork->ev3_fork) cudaEventDestroy(c->fork->ev3_fork);
         if (c->fork->ev3_join) cudaEventDestroy(c->fork->ev3_join);
-        if (c->precision == BTA_MIXED && c->fork->ex2.ws) cudaFree(c->fork->ex2.ws);
+        if (c->precision != BTA_FP64 && c->fork->ex2.ws) cudaFree(c->fork->ex2.ws);
         delete c->fork;
         c->fork = nullptr;
     }
@@ -212,7 +215,7 @@ extern "C" int bta_destroy(bta_ctx_t c) {
     store_free(c->S);
     if (c->fobj_graph) cudaGraphExecDestroy(c->fobj_graph);
     double* bufs[] = {c->Linv, c->work, c->vec, c->red, c->ld, c->dots, c->params, c->theta_buf, c->f_buf,
-                      c->adj};
+                      c->adj, c->hs_theta, c->hs_f, c->hs_grad, c->hs_var};
     for (double* p : bufs)
         if (p) cudaFree(p);
     if (c->exec.ws) cudaFree(c->exec.ws);
@@ -349,7 +352,11 @@ extern "C" int bta_sync(bta_ctx_t c) {
         e = cudaMemcpy(&oz, c->oz_err, sizeof(int), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return bta_cuda_fail(e);
         if (oz) {
+            // the products after the time-out are void, and so is any pivot
+            // error they caused: clear both records
             cudaMemset(c->oz_err, 0, sizeof(int));
+            long long zero[3] = {0, 0, 0};
+            cudaMemcpy(c->status, zero, sizeof(zero), cudaMemcpyHostToDevice);
             c->last_info = -1;
             c->last_matrix = -1;
             return BTA_ERR_TIMEOUT;

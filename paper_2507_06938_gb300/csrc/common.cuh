@@ -86,6 +86,8 @@ struct GemmExec {
     int* err;          // device error flag of the tensor-core kernel
     int min_dim;       // smallest M, N (and K) sent to the tensor-core path
     int df_leaf = 0;   // > 0: diagonal leaves of this order in double-float (leaf_df32.cu)
+    int slices = 5;    // digit slices of the split products: 5 (35 bits) or 7 (49 bits)
+    long long epi_wait = 0;   // wait limit of the tensor kernel's epilogue hand-off (0: default)
 };
 
 // Side stream, events and executor for the products of the recursive
@@ -153,6 +155,12 @@ struct bta_ctx_s {
     double* theta_buf = nullptr;   // batch x dim_theta (dim <= BTA_PSTRIDE)
     double* f_buf = nullptr;       // batch
     double* adj = nullptr;         // adjoint trace records (3 x batch)
+    // device staging of the host-buffer entry point (allocated on first use)
+    double* hs_theta = nullptr;    // batch x dim_theta
+    double* hs_f = nullptr;        // batch
+    double* hs_grad = nullptr;     // batch x dim_theta
+    double* hs_var = nullptr;      // batch x N
+    int hs_dim = 0;
     // optional event timing of the b x b x b Schur-update GEMM launches
     int prof = 0;
     std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
@@ -214,9 +222,10 @@ int dot_batch64(cudaStream_t s, const double* x, const double* y, long long len,
                 int chunks, double* out, long long ostride);
 
 // ---------------------------------------------------------------- tensor cores (ozaki.cu)
-size_t ozaki_workspace_bytes(int M, int N, int K);
-// same contract as gemm64 (any batch); ws holds batch x ozaki_workspace_bytes
-int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err);
+size_t ozaki_workspace_bytes(int M, int N, int K, int slices);
+// same contract as gemm64 (any batch); ws holds batch x ozaki_workspace_bytes;
+// slices = 5 (35-bit digits) or 7 (49-bit digits)
+int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err, int slices, long long epi_wait = 0);
 int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
 // true when gemm_exec sends g to the split-precision path, whose operands are
 // read completely (digit split) before C is written: C may then alias A or B

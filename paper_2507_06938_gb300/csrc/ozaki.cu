@@ -2,80 +2,141 @@
 // BTA Schur updates and selected inversion).
 //
 // C += alpha * op(A) op(B) with FP64 A, B, C.  Every row i of op(A) is written
-// as 2^{e_i} sum_{p<S} d_p 2^{-7(p+1)} with integer digits (S = 5 slices,
-// 35 bits below the row's largest binary exponent, rounded; |d_0| <= 128,
-// |d_p| <= 64 for p >= 1), every column j of op(B) the same way with
-// exponent f_j.  A digit is exact in bf16.  Grouping the digit products by
-// level s = p + q,
+// as 2^{e_i} sum_{p<S} d_p 2^{-7(p+1)} with integer digits (S slices, 7S bits
+// below the row's largest binary exponent, rounded; |d_0| <= 128, |d_p| <= 64
+// for p >= 1), every column j of op(B) the same way with exponent f_j.  A
+// digit is exact in bf16.  Grouping the digit products by level s = p + q,
 //   (op(A) op(B))_ij ~ 2^{e_i + f_j - 14} sum_{s<S} 2^{-7s} L_s(i,j),
 //   L_s = sum_k sum_{p+q=s} d_p(i,k) d_q(k,j)
 // (levels s >= S fall below the digits' own precision).  Per k the level
-// sums are integers bounded by 2^14 (s = 0, 1), 20480 (s = 2), 24576 (s = 3)
-// and 28672 (s = 4).  Each level has its own FP32 accumulator in tensor
-// memory (tcgen05.mma kind::f16):
-//   levels 0 and 1 stay below 2^24, hence exact, over 1024 values of k;
-//   level 2 is exact over 512 values of k and is drained that often;
-//   levels 3 and 4 run over 1024 values of k past 2^24, where each of at
-//   most 320 accumulation steps rounds by at most 2 units: 2^-37 and 2^-44 of
-//   the output scale |A_i||B_j|K, below the 2^-35 truncation of the digits.
-// A drain reads an accumulator (tcgen05.ld), scales it by 2^{-7s} and adds it
-// into a double-float sum (two FP32 words, error-free TwoSum) on the CUDA
-// cores.  The result goes into C
-// with one FP64 addition per element; the power-of-two scaling and the
-// FP32 -> FP64 widening are done on the bit patterns, because the FP64 pipe
-// of GB300 (~1.2 TFLOP/s) is the scarce unit and the bf16 tensor pipe
-// (~1.9 PFLOP/s) the plentiful one.
+// sums are integers bounded by 2^14 (s = 0, 1), 20480 (s = 2), 24576 (s = 3),
+// 28672 (s = 4), 32768 (s = 5) and 36864 (s = 6).  Each level has its own
+// FP32 accumulator in tensor memory (tcgen05.mma kind::f16).  Two variants:
 //
-// Kernel (persistent, one CTA of 576 threads per SM, 128 x 96 output tiles):
-//   warp 0      TMA producer: for every 32-wide K block all five digit slices
-//               of the A tile (128 x 32) and of the B tile (96 x 32), 64-byte
-//               swizzle, into a 2-stage shared-memory ring (70 KB a stage), so
-//               that each digit is read from L2 once per tile
-//   warp 1      allocates 512 TMEM columns (five 96-column accumulators) and,
-//               from one thread, issues the 15 digit pairs of each 16-wide K
-//               step as 9 tcgen05.mma (M = 128, K = 16) over stacked B slices
-//               (N = 96 or 192, see kPieces)
-//   warps 2..17 drain level 2 after every 512-long K chunk and the other
-//               levels after every second chunk, then update C while the
+//   S = 5 (35-bit digits, 128 x 96 tiles): levels 0 and 1 stay below 2^24,
+//   hence exact, over 1024 values of k; level 2 is exact over 512 and is
+//   drained that often; levels 3 and 4 run over 1024 values of k past 2^24,
+//   where each of at most 320 accumulation steps rounds by at most 2 units:
+//   2^-37 and 2^-44 of the output scale |A_i||B_j|K, below the 2^-35
+//   truncation of the digits.  A drain scales a level by 2^{-7s} and adds it
+//   into a double-float sum (two FP32 words, error-free TwoSum).
+//
+//   S = 7 (49-bit digits, 128 x 64 tiles, for ill-conditioned matrices):
+//   levels 0 and 1 are drained every 1024 values of k, levels 2..6 every
+//   512, so levels 0..5 are exact integers when drained (level 6 may round
+//   by one unit in 2^{-56} of the output scale).  A drain converts each
+//   level to an integer and adds it into a 64-bit fixed-point sum in units
+//   of level 5 (level 6 rounded to that unit), so the sum over chunks is
+//   exact: a double-float sum would round by 2^-48 at every drain, above the
+//   2^-49 truncation of the digits.  A work unit spans at most 16 chunks
+//   (K <= 8192 per unit, a K split beyond), which bounds the sum by 2^63.
+//
+// The result goes into C with one FP64 addition per element; the
+// power-of-two scaling and the widening to FP64 are done on bit patterns or
+// integers, because the FP64 pipe of GB300 (~1.2 TFLOP/s) is the scarce unit
+// and the bf16 tensor pipe (~1.9 PFLOP/s) the plentiful one.
+//
+// Kernel (persistent, one CTA of 576 threads per SM, 128 x TN output tiles):
+//   warp 0      TMA producer: for every 32-wide K block all S digit slices
+//               of the A tile (128 x 32) and of the B tile (TN x 32), 64-byte
+//               swizzle, into a 2-stage shared-memory ring (70 KB a stage for
+//               S = 5, 84 KB for S = 7), so that each digit is read from L2
+//               once per tile
+//   warp 1      allocates 512 TMEM columns (S accumulators of TN columns) and,
+//               from one thread, issues the S(S+1)/2 digit pairs of each
+//               16-wide K step as tcgen05.mma (M = 128, K = 16) over stacked B
+//               slices (N = TN, 2 TN, ..., up to 256; see Cfg::piece)
+//   warps 2..17 drain the level group B after every 512-long K chunk and
+//               group A after every second chunk, then update C while the
 //               next tile's products run
 // Work units are (matrix, tile, K part); a K split (atomic adds into C) only
-// appears when the tiles alone cannot fill the GPU.  Every wait on an
-// mbarrier is bounded in time; on expiry the kernel records an error, stops
-// issuing, drains what it issued and frees its tensor memory.
+// appears when the tiles alone cannot fill the GPU, or, for S = 7, when K
+// exceeds 8192.  Every wait on an mbarrier is bounded in time; on expiry the
+// kernel records an error, stops issuing, drains what it issued and frees its
+// tensor memory.
 
 #include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 
 #include "common.cuh"
 
 namespace oz {
 
-constexpr int S = 5;                      // digit slices = accumulated levels
-constexpr int TM = 128, TN = 96, TK = 32; // output tile; K block (64-byte rows)
+constexpr int TM = 128, TK = 32;          // output tile rows; K block (64-byte rows)
 constexpr int ROW_BYTES = TK * 2;         // one digit row of a K block; the swizzle span
 static_assert(ROW_BYTES == 32 || ROW_BYTES == 64 || ROW_BYTES == 128, "K block of 16, 32 or 64");
 constexpr int STAGES = 2;
-constexpr int KB_PER_CHUNK = 512 / TK;    // exactness bound of the level-2 accumulation
-constexpr int EPI_WARPS = 16;            // 4 per TMEM lane quarter
-constexpr int EPI_COLS = TN / (EPI_WARPS / 4);   // 24 columns per epilogue thread
+constexpr int KB_PER_CHUNK = 512 / TK;    // exactness bound of the levels drained every chunk
+constexpr int EPI_WARPS = 16;             // 4 per TMEM lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr uint32_t TMEM_COLS = 512;       // S * TN = 480 used
-constexpr uint32_t A_SLICE_BYTES = TM * TK * 2;                       // 8 KB
-constexpr uint32_t B_SLICE_BYTES = TN * TK * 2;                       // 6 KB
-constexpr uint32_t STAGE_BYTES = S * (A_SLICE_BYTES + B_SLICE_BYTES); // 70 KB
-// per epilogue warp, two 32-row x 8-column FP64 buffers for the bulk reduce-add of C
-constexpr uint32_t CBUF_BYTES = 2 * 8 * 32 * 8;
-constexpr size_t SMEM_BYTES = 1024 /*alignment slack*/ + STAGES * STAGE_BYTES + EPI_WARPS * CBUF_BYTES + 256;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t A_SLICE_BYTES = TM * TK * 2;   // 8 KB
 constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;   // about 2 s
-constexpr int PAD_M = TM, PAD_N = TN, PAD_K = 64;        // digit array padding (PAD_K: split tile)
+constexpr int PAD_K = 64;                 // digit array K padding (split tile)
 constexpr int MAX_MT = 128;               // row tiles per matrix (M <= 16384)
+constexpr int INT_MAX_CHUNKS = 16;        // S = 7: chunks per work unit (64-bit sum bound)
 
-static_assert(SMEM_BYTES <= 232448, "shared memory of one CTA");
-static_assert(S * TN <= (int)TMEM_COLS, "level accumulators must fit in tensor memory");
+// One tcgen05.mma of a K step: A slice p times the B slices q0 .. q0+n-1
+// stacked (N = n TN), adding the pairs (p, q0 + j) into the level
+// accumulators p + q0 + j.  kind: 0 accumulate, 1 first write of the group-A
+// levels it covers (on the chunk that resets group A), 2 first write of
+// group-B levels (every chunk).  The p = 0 pieces come first, so every level
+// is first written by them at the start of a chunk.
+struct Piece { int p, q0, n, kind; };
+
+template <int S> struct Cfg;
+
+// 35-bit digits: 5 levels x 96 columns = 480 of the 512 TMEM columns.
+// Group A = levels 0, 1, 3, 4 (every second chunk), group B = level 2.
+template <> struct Cfg<5> {
+    static constexpr int TN = 96;
+    static constexpr unsigned GROUP_A = 0x1Bu, GROUP_B = 0x04u;
+    static constexpr int PIECES = 9;
+    static constexpr int CBUF_BUFS = 2;    // 8-column staging buffers of the bulk reduce-add, per warp
+    static constexpr bool INT_ACC = false;
+    __host__ __device__ static constexpr Piece piece(int i) {
+        constexpr Piece t[PIECES] = {{0, 0, 2, 1}, {0, 2, 1, 2}, {0, 3, 2, 1}, {1, 0, 2, 0}, {1, 2, 2, 0},
+                                     {2, 0, 2, 0}, {2, 2, 1, 0}, {3, 0, 2, 0}, {4, 0, 1, 0}};
+        return t[i];
+    }
+};
+
+// 49-bit digits: 7 levels x 64 columns = 448 TMEM columns.  Group A = levels
+// 0, 1 (every second chunk), group B = levels 2..6 (every chunk); 28 pairs as
+// 11 MMAs of N <= 256.
+template <> struct Cfg<7> {
+    static constexpr int TN = 64;
+    static constexpr unsigned GROUP_A = 0x03u, GROUP_B = 0x7Cu;
+    static constexpr int PIECES = 11;
+    static constexpr int CBUF_BUFS = 1;
+    static constexpr bool INT_ACC = true;
+    __host__ __device__ static constexpr Piece piece(int i) {
+        constexpr Piece t[PIECES] = {{0, 0, 2, 1}, {0, 2, 4, 2}, {0, 6, 1, 2}, {1, 0, 4, 0},
+                                     {1, 4, 2, 0}, {2, 0, 4, 0}, {2, 4, 1, 0}, {3, 0, 4, 0},
+                                     {4, 0, 3, 0}, {5, 0, 2, 0}, {6, 0, 1, 0}};
+        return t[i];
+    }
+};
+
+template <int S> struct Geo {
+    static constexpr int TN = Cfg<S>::TN;
+    static constexpr int EPI_COLS = TN / (EPI_WARPS / 4);   // columns per epilogue thread
+    static constexpr uint32_t B_SLICE_BYTES = TN * TK * 2;
+    static constexpr uint32_t STAGE_BYTES = S * (A_SLICE_BYTES + B_SLICE_BYTES);
+    // per epilogue warp, 32-row x 8-column FP64 buffers for the bulk reduce-add of C
+    static constexpr uint32_t CBUF_BYTES = Cfg<S>::CBUF_BUFS * 8 * 32 * 8;
+    static constexpr size_t SMEM_BYTES =
+        1024 /*alignment slack*/ + STAGES * STAGE_BYTES + EPI_WARPS * CBUF_BYTES + 256;
+    static_assert(SMEM_BYTES <= 232448, "shared memory of one CTA");
+    static_assert(S * TN <= (int)TMEM_COLS, "level accumulators must fit in tensor memory");
+    static_assert(EPI_COLS % 8 == 0, "epilogue columns in groups of 8");
+    static_assert(TM % TN == 0 || TN == 96, "row padding of aliased operands");
+};
 
 struct Args {
     int M, N;            // output extent
@@ -99,6 +160,7 @@ struct Args {
     double beta;
     int inplace;         // Cin is C with beta = 1 (or the K split pre-initialised C)
     int bulk;            // in-place accumulation through bulk reduce-add (C, ldc, sC 16-byte aligned)
+    long long epi_wait;  // wait limit (cycles) of the epilogue's accumulator hand-off
     int mcum[MAX_MT + 1];// lowerC: tiles of row tiles 0..m-1
 };
 
@@ -110,6 +172,7 @@ struct Unit {
 };
 
 // Decode work unit u; returns false when the unit has no K blocks.
+template <int TN>
 __device__ __forceinline__ bool decode_unit(const Args& a, int u, Unit& w) {
     const int kpart = u % a.ksplit;
     u /= a.ksplit;
@@ -142,6 +205,7 @@ __device__ __forceinline__ bool decode_unit(const Args& a, int u, Unit& w) {
 
 // Prefetch the C (or Cin) tile of unit w into L2 ahead of the epilogue's
 // read-modify-write: one bulk prefetch per column of the tile.
+template <int TN>
 __device__ __forceinline__ void prefetch_c_tile(const double* base, long long ld, const Unit& w, int M, int N) {
     const int rows = min(TM, M - w.m0);
     const int ncols = min(TN, N - w.n0);
@@ -186,14 +250,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase of `parity` to complete.  Returns false (and
-// raises the CTA abort flag and the global error flag) after about 2 s, or
-// at once if another thread has already aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* err) {
+// raises the CTA abort flag and the global error flag) after `limit` cycles
+// (about 2 s by default), or at once if another thread has already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* err,
+                                          long long limit = WAIT_LIMIT_CYCLES) {
     const long long t0 = clock64();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort) return false;
-        if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             *abort = 1;
             atomicExch(err, 1);
             return false;
@@ -224,10 +289,9 @@ __device__ __forceinline__ uint64_t smem_desc_sw(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128,
-// N = nlev * 96 (one or two level accumulators side by side).
-__host__ __device__ constexpr uint32_t idesc_for(int nlev) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((nlev * TN) >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// Instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_for_n(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -239,22 +303,6 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
-
-// The 15 digit-pair products of one K step as 9 MMAs.  The level
-// accumulators sit side by side in tensor memory (level s at column 96 s)
-// and the five B slices side by side in shared memory (slice q at row 96 q),
-// so A_p times the stacked slices B_q0 .. B_q0+n-1 (N = 96 n) adds the pairs
-// (p, q0 + j) into levels p + q0 + j at once.  Pieces of n = 1 or 2 keep
-// N <= 256 and give level 2, which restarts every chunk, a piece of its own
-// in the p = 0 row (the first writes of a chunk come from that row).
-struct Piece { int p, q0, n, kind; };   // kind: 0 accumulate, 1 first of levels 0 1 3 4, 2 first of level 2
-constexpr int PIECES = 9;
-__device__ constexpr Piece kPieces[PIECES] = {
-    {0, 0, 2, 1}, {0, 2, 1, 2}, {0, 3, 2, 1},
-    {1, 0, 2, 0}, {1, 2, 2, 0},
-    {2, 0, 2, 0}, {2, 2, 1, 0},
-    {3, 0, 2, 0},
-    {4, 0, 1, 0}};
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -273,7 +321,6 @@ __device__ __forceinline__ void reg_fence8(uint32_t* r) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -285,7 +332,6 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
     hi = s;
     lo = __fadd_rn(lo, e);
 }
-
 
 // f 2^e as a double, built from the bit pattern of the FP32 value f (zero or
 // normal; the accumulated values here never reach the subnormal range).
@@ -300,10 +346,22 @@ __device__ __forceinline__ double f2d_scaled(float f, int e) {
     return __longlong_as_double((long long)bits);
 }
 
-// Adds 2^{-7 lv} times this thread's EPI_COLS accumulator columns of one
-// level (tensor memory address taddr: lane quarter, level, column group) into
-// the double-float sums hi + lo.
-__device__ __forceinline__ void drain_level(uint32_t taddr, int lv, float* hi, float* lo) {
+// v 2^e for a 64-bit integer v: the conversion rounds to the nearest double,
+// the scaling adds e to the exponent field (exact in the normal range).
+__device__ __forceinline__ double ll2d_scaled(long long v, int e) {
+    if (v == 0) return 0.0;
+    const double d = __ll2double_rn(v);
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+    const int ed = (int)((bits >> 52) & 0x7FF) + e;
+    if (ed <= 0 || ed >= 2047) return ldexp(d, e);
+    return __longlong_as_double((long long)((bits & ~(0x7FFull << 52)) | ((unsigned long long)ed << 52)));
+}
+
+// Drain of one level (tensor memory address taddr: lane quarter, level,
+// column group) into this thread's EPI_COLS sums.  Double-float variant:
+// hi + lo += 2^{-7 lv} L.
+template <int EPI_COLS>
+__device__ __forceinline__ void drain_level_df(uint32_t taddr, int lv, float* hi, float* lo) {
     const float scale = __uint_as_float((uint32_t)(127 - 7 * lv) << 23);   // 2^{-7 lv}
 #pragma unroll
     for (int h = 0; h < EPI_COLS / 8; ++h) {
@@ -316,16 +374,43 @@ __device__ __forceinline__ void drain_level(uint32_t taddr, int lv, float* hi, f
     }
 }
 
+// Fixed-point variant: acc += L 2^{7 (5 - lv)} for lv <= 5 (L is an integer
+// held exactly in FP32), acc += round(L / 2^7) for lv = 6.
+template <int EPI_COLS>
+__device__ __forceinline__ void drain_level_int(uint32_t taddr, int lv, long long* acc) {
+#pragma unroll
+    for (int h = 0; h < EPI_COLS / 8; ++h) {
+        uint32_t r[8];
+        tmem_ld_8cols(taddr + h * 8, r);
+        tmem_wait_ld();
+        reg_fence8(r);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));   // |L| < 2^25: exact
+            if (lv <= 5) acc[h * 8 + j] += v << (7 * (5 - lv));
+            else acc[h * 8 + j] += (v + 64) >> 7;
+        }
+    }
+}
+
+template <int S>
 __global__ void __launch_bounds__(THREADS, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const __grid_constant__ Args a) {
+    using CF = Cfg<S>;
+    using G = Geo<S>;
+    constexpr int TN = CF::TN;
+    constexpr int EPI_COLS = G::EPI_COLS;
+    constexpr uint32_t STAGE_BYTES = G::STAGE_BYTES;
+    constexpr uint32_t B_SLICE_BYTES = G::B_SLICE_BYTES;
+    constexpr uint32_t CBUF_BYTES = G::CBUF_BYTES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     double* cbuf = reinterpret_cast<double*>(smem + STAGES * STAGE_BYTES);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + EPI_WARPS * CBUF_BYTES);
     uint64_t* empty = full + STAGES;
-    // accumulator hand-off: group A = levels 0, 1, 3, 4 (drained every second
-    // chunk), group B = level 2 (drained every chunk)
+    // accumulator hand-off: group A (drained every second chunk) and group B
+    // (drained every chunk), see Cfg
     uint64_t* fullA = empty + STAGES;
     uint64_t* emptyA = fullA + 1;
     uint64_t* fullB = emptyA + 1;
@@ -366,7 +451,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             int it = 0;
             for (int u = blockIdx.x; u < a.units && !*abort_flag; u += gridDim.x) {
                 Unit w;
-                if (!decode_unit(a, u, w)) continue;
+                if (!decode_unit<TN>(a, u, w)) continue;
                 const int kb0 = w.kbl + w.c0 * KB_PER_CHUNK;
                 const int kb1 = min(w.kbh, w.kbl + w.c1 * KB_PER_CHUNK);
                 const int kb_last = w.kbl + (w.c1 - 1) * KB_PER_CHUNK;
@@ -376,9 +461,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (!mbar_wait(&empty[st], ph ^ 1, abort_flag, a.err)) break;
                     if (kb == kb_last && a.ksplit == 1) {
                         if (a.inplace)
-                            prefetch_c_tile(a.C + w.inst * a.sC, a.ldc, w, a.M, a.N);
+                            prefetch_c_tile<TN>(a.C + w.inst * a.sC, a.ldc, w, a.M, a.N);
                         else if (a.Cin != nullptr && a.beta != 0.0)
-                            prefetch_c_tile(a.Cin + w.inst * a.sCi, a.ldci, w, a.M, a.N);
+                            prefetch_c_tile<TN>(a.Cin + w.inst * a.sCi, a.ldci, w, a.M, a.N);
                     }
                     uint8_t* sA = smem + st * STAGE_BYTES;
                     uint8_t* sB = sA + S * A_SLICE_BYTES;
@@ -410,7 +495,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             bool ok = true;
             for (int u = blockIdx.x; ok && u < a.units && !*abort_flag; u += gridDim.x) {
                 Unit w;
-                if (!decode_unit(a, u, w)) continue;
+                if (!decode_unit<TN>(a, u, w)) continue;
                 for (int c = w.c0; ok && c < w.c1; ++c) {
                     const int kb0 = w.kbl + c * KB_PER_CHUNK, kb1 = min(w.kbh, kb0 + KB_PER_CHUNK);
                     const bool resetA = ((c - w.c0) & 1) == 0;
@@ -435,23 +520,25 @@ __global__ void __launch_bounds__(THREADS, 1)
                         const uint64_t dA = smem_desc_sw(sA), dB = smem_desc_sw(sB);
 #pragma unroll
                         for (int k = 0; k < TK / 16; ++k) {
+                            bool waitedB = false;
 #pragma unroll
-                            for (int i = 0; i < PIECES; ++i) {
-                                const Piece pc = kPieces[i];
-                                if (pc.kind == 2 && kb == kb0 && k == 0) {
-                                    // level 2 restarts every chunk: its previous sums must be drained
+                            for (int i = 0; i < CF::PIECES; ++i) {
+                                const Piece pc = CF::piece(i);
+                                if (pc.kind == 2 && kb == kb0 && k == 0 && !waitedB) {
+                                    // group B restarts every chunk: its previous sums must be drained
                                     if (!mbar_wait(emptyB, (nB & 1) ^ 1, abort_flag, a.err)) {
                                         ok = false;
                                         break;
                                     }
                                     fence_after_sync();
+                                    waitedB = true;
                                 }
                                 // descriptor start addresses are in 16-byte units
                                 const uint64_t offA = (uint64_t)((pc.p * A_SLICE_BYTES + k * 32) >> 4);
                                 const uint64_t offB = (uint64_t)((pc.q0 * B_SLICE_BYTES + k * 32) >> 4);
                                 const bool first = kb == kb0 && k == 0 && (pc.kind == 2 || (pc.kind == 1 && resetA));
-                                umma_bf16(tmem_base + (pc.p + pc.q0) * TN, dA + offA, dB + offB, idesc_for(pc.n),
-                                          first ? 0u : 1u);
+                                umma_bf16(tmem_base + (pc.p + pc.q0) * TN, dA + offA, dB + offB,
+                                          idesc_for_n(pc.n * TN), first ? 0u : 1u);
                             }
                             if (!ok) break;
                         }
@@ -479,40 +566,57 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int colbase = ((warp - 2) / 4) * EPI_COLS;
         const int row = quarter * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-        float hi[EPI_COLS], lo[EPI_COLS];
+        // S = 5: double-float sums; S = 7: 64-bit fixed point in units of level 5
+        float hi[CF::INT_ACC ? 1 : EPI_COLS], lo[CF::INT_ACC ? 1 : EPI_COLS];
+        long long acc[CF::INT_ACC ? EPI_COLS : 1];
         int nA = 0, nB = 0;
         bool ok = true;
         for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
             Unit w;
             // a unit without K blocks still writes beta Cin when there is no K split
-            if (!decode_unit(a, u, w) && (a.ksplit > 1 || a.inplace)) continue;
+            if (!decode_unit<TN>(a, u, w) && (a.ksplit > 1 || a.inplace)) continue;
 #pragma unroll
             for (int j = 0; j < EPI_COLS; ++j) {
-                hi[j] = 0.f;
-                lo[j] = 0.f;
+                if constexpr (CF::INT_ACC) {
+                    acc[j] = 0;
+                } else {
+                    hi[j] = 0.f;
+                    lo[j] = 0.f;
+                }
             }
             for (int c = w.c0; c < w.c1; ++c) {
                 const bool drainA = ((c - w.c0) & 1) == 1 || c == w.c1 - 1;
-                if (!mbar_wait(fullB, nB & 1, abort_flag, a.err)) {
+                if (!mbar_wait(fullB, nB & 1, abort_flag, a.err, a.epi_wait)) {
                     ok = false;
                     break;
                 }
                 fence_after_sync();
-                drain_level(tmem_base + lane_addr + 2 * TN + colbase, 2, hi, lo);
+#pragma unroll
+                for (int lv = 0; lv < S; ++lv) {
+                    if (!(CF::GROUP_B & (1u << lv))) continue;
+                    if constexpr (CF::INT_ACC)
+                        drain_level_int<EPI_COLS>(tmem_base + lane_addr + lv * TN + colbase, lv, acc);
+                    else
+                        drain_level_df<EPI_COLS>(tmem_base + lane_addr + lv * TN + colbase, lv, hi, lo);
+                }
                 fence_before_sync();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(emptyB);
                 ++nB;
                 if (drainA) {
-                    if (!mbar_wait(fullA, nA & 1, abort_flag, a.err)) {
+                    if (!mbar_wait(fullA, nA & 1, abort_flag, a.err, a.epi_wait)) {
                         ok = false;
                         break;
                     }
                     fence_after_sync();
-                    drain_level(tmem_base + lane_addr + 0 * TN + colbase, 0, hi, lo);
-                    drain_level(tmem_base + lane_addr + 1 * TN + colbase, 1, hi, lo);
-                    drain_level(tmem_base + lane_addr + 3 * TN + colbase, 3, hi, lo);
-                    drain_level(tmem_base + lane_addr + 4 * TN + colbase, 4, hi, lo);
+#pragma unroll
+                    for (int lv = 0; lv < S; ++lv) {
+                        if (!(CF::GROUP_A & (1u << lv))) continue;
+                        if constexpr (CF::INT_ACC)
+                            drain_level_int<EPI_COLS>(tmem_base + lane_addr + lv * TN + colbase, lv, acc);
+                        else
+                            drain_level_df<EPI_COLS>(tmem_base + lane_addr + lv * TN + colbase, lv, hi, lo);
+                    }
                     fence_before_sync();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(emptyA);
@@ -520,6 +624,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
             }
             if (!ok) break;
+            // value of column jj of this thread's row, times 2^e
+            auto value = [&](int jj, int e) -> double {
+                if constexpr (CF::INT_ACC) return ll2d_scaled(acc[jj], e - 35);
+                else return f2d_scaled(hi[jj], e) + f2d_scaled(lo[jj], e);
+            };
             // C update from registers (tensor memory is already free for the next unit)
             const int i = w.m0 + row;
             const int rows_here = a.M - (w.m0 + quarter * 32);   // rows of this warp inside C
@@ -534,10 +643,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                 double* wbuf = cbuf + (warp - 2) * (CBUF_BYTES / 8);
 #pragma unroll
                 for (int g = 0; g < EPI_COLS / 8; ++g) {
-                    double* bufg = wbuf + (g & 1) * 256;
-                    if (g >= 2) {
-                        // the bulk reads of the group issued two steps ago must be done
-                        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    double* bufg = wbuf + (g % CF::CBUF_BUFS) * 256;
+                    if (g >= CF::CBUF_BUFS) {
+                        // the bulk reads of the group that used this buffer must be done
+                        if (lane == 0) {
+                            if constexpr (CF::CBUF_BUFS == 2)
+                                asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                            else
+                                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                        }
                         __syncwarp();
                     }
 #pragma unroll
@@ -545,8 +659,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         const int nn = w.n0 + colbase + g * 8 + jj;
                         double v = 0.0;
                         if (i < a.M && nn < a.N && !(a.lowerC && i < nn)) {
-                            const int e = ea + expB[nn];
-                            v = f2d_scaled(hi[g * 8 + jj], e) + f2d_scaled(lo[g * 8 + jj], e);
+                            v = value(g * 8 + jj, ea + expB[nn]);
                             if (!unit_alpha) v *= a.alpha;
                             else if (neg) v = -v;
                         }
@@ -592,8 +705,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     for (int jj = 0; jj < 8; ++jj) {
                         const int nn = w.n0 + colbase + j0 + jj;
                         if (nn >= a.N || (a.lowerC && i < nn)) continue;
-                        const int e = ea + expB[nn];
-                        double v = f2d_scaled(hi[j0 + jj], e) + f2d_scaled(lo[j0 + jj], e);
+                        double v = value(j0 + jj, ea + expB[nn]);
                         if (!unit_alpha) v *= a.alpha;
                         else if (neg) v = -v;
                         double* c = Cm + i + (long long)nn * a.ldc;
@@ -626,11 +738,11 @@ __global__ void __launch_bounds__(THREADS, 1)
 // Rows r < R of X (R x K, X[r][k] = P[r*sr + k*sk]) with an optional
 // triangular mask (shape 1: X[r][k] = 0 for k > r; shape 2: for k < r).
 // e_r = exponent of the row maximum (|X[r][k]| < 2^{e_r}).  Each entry is
-// turned into the 35-bit fixed-point integer V = round(X[r][k] 2^{35 - e_r})
-// (|V| < 2^35, ties rounded away from zero) and |V| into balanced base-128
-// digits u_0..u_4, |V| = sum_s u_s 128^{4-s}, |u_s| <= 64 for s >= 1 and
-// |u_0| <= 128; the digits of V are d_s = sign(X) u_s, so that
-// X[r][k] 2^{-e_r} = sum_s d_s 2^{-7(s+1)} up to 2^{-36}.  Only integer and
+// turned into the 7S-bit fixed-point integer V = round(X[r][k] 2^{7S - e_r})
+// (|V| <= 2^{7S}, ties rounded away from zero) and |V| into balanced
+// base-128 digits u_0..u_{S-1}, |V| = sum_s u_s 128^{S-1-s}, |u_s| <= 64 for
+// s >= 1 and |u_0| <= 128; the digits of V are d_s = sign(X) u_s, so that
+// X[r][k] 2^{-e_r} = sum_s d_s 2^{-7(s+1)} up to 2^{-7S-1}.  Only integer and
 // FP32 operations are used (the FP64 pipe of GB300 is the slow one).
 // Output: dig[s][r][k] (bf16, rows padded to Rp, K padded to Kp with zeros)
 // and exp[r] (0 for padding rows).
@@ -645,36 +757,51 @@ struct SplitJob {
     __nv_bfloat16* dig;     // S * Rp * Kp per matrix
 };
 
-// The five digits of x for a row with exponent e, as FP32 bit patterns whose
-// upper halves are the bf16 patterns (c = 1040 + e).  V comes from the
+// Signed digit d as an FP32 bit pattern whose upper half is the bf16
+// pattern: 0x4B400000 + d is 1.5 2^23 + d (exact for |d| < 2^22), so
+// subtracting 1.5 2^23 leaves d exactly; d ^ s - s (s = 0 or -1, folded into
+// the base) negates it.
+__device__ __forceinline__ uint32_t digit_bits(uint32_t base, uint32_t d, uint32_t sg) {
+    return __float_as_uint(__uint_as_float(base + (d ^ sg)) - 12582912.0f);
+}
+
+// The S digits of x for a row with exponent e, as FP32 bit patterns whose
+// upper halves are the bf16 patterns (c = 1075 - 7S + e).  V comes from the
 // 53-bit significand m of |x| = m 2^{ef - 1075}: V = round(m 2^{-(c - ef)}),
-// with c - ef >= 18 whenever |x| < 2^e (a shift of 63 or more gives 0, which
-// also covers e = 4096 for rows holding a NaN or an infinity).  Each digit
-// is peeled off the low 28 bits as ((t + 64) mod 128) - 64 with the carry
-// (t + 64) >> 7; the sign enters through the FP32 offset trick: the bit
-// pattern 0x4B400000 + d is 1.5 2^23 + d, exact for |d| < 2^22, so
-// subtracting 1.5 2^23 leaves d exactly, and d ^ s - s (s = 0 or -1)
-// negates it.
+// with c - ef >= 53 - 7S + 1 whenever |x| < 2^e (a shift of 63 or more
+// gives 0, which also covers e = 4096 for rows holding a NaN or an
+// infinity).  Each digit is peeled off as ((t + 64) mod 128) - 64 with the
+// carry (t + 64) >> 7, four digits from the low 28 bits of V and the rest
+// from the high bits.
+template <int S>
 __device__ __forceinline__ void digits_of(double x, int c, uint32_t (&f)[S]) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
     const uint32_t h = (uint32_t)(bits >> 32);
     const int ef = (int)((h >> 20) & 0x7FF);
-    // zero and subnormals (far below the 2^-35 resolution of any row) give 0
+    // zero and subnormals (far below the resolution of any row) give 0
     const unsigned long long m = ef ? ((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
-    const int sft = min(c - ef - 1, 63);
+    const int sft = max(0, min(c - ef - 1, 63));
     const unsigned long long V = ((m >> sft) + 1) >> 1;   // round half away from zero on |x|
     uint32_t lo = (uint32_t)V & 0xFFFFFFFu;
-    const uint32_t top = (uint32_t)(V >> 28);
+    uint32_t top = (uint32_t)(V >> 28);
     const uint32_t sg = (uint32_t)((int32_t)h >> 31);
     const uint32_t base = 0x4B400000u - sg;
 #pragma unroll
-    for (int sl = S - 1; sl >= 1; --sl) {
+    for (int sl = S - 1; sl >= S - 4; --sl) {
         const uint32_t t = lo + 64u;
         const uint32_t d = (t & 127u) - 64u;
         lo = t >> 7;
-        f[sl] = __float_as_uint(__uint_as_float(base + (d ^ sg)) - 12582912.0f);
+        f[sl] = digit_bits(base, d, sg);
     }
-    f[0] = __float_as_uint(__uint_as_float(base + ((top + lo) ^ sg)) - 12582912.0f);
+    top += lo;   // carry out of the low 28 bits
+#pragma unroll
+    for (int sl = S - 5; sl >= 1; --sl) {
+        const uint32_t t = top + 64u;
+        const uint32_t d = (t & 127u) - 64u;
+        top = t >> 7;
+        f[sl] = digit_bits(base, d, sg);
+    }
+    f[0] = digit_bits(base, top, sg);
 }
 
 __device__ __forceinline__ void cp_async8(double* dst, const double* src) {
@@ -697,7 +824,7 @@ inline size_t split_smem(int rs, int Kp) { return (size_t)rs * (Kp + 4) * 8; }
 // column-order fills free of bank conflicts), then the row exponents and the
 // digits are computed from there; each thread writes four consecutive k of
 // every digit slice with one 8-byte store.
-template <int RS>
+template <int RS, int S>
 __global__ void __launch_bounds__(SPLIT_THREADS) split_kernel(SplitJob j0, SplitJob j1) {
     extern __shared__ double stile[];   // RS x (Kp + 4)
     __shared__ int row_e[RS];
@@ -744,12 +871,12 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_kernel(SplitJob j0, Split
     for (int e = threadIdx.x; e < RS * per; e += SPLIT_THREADS) {
         const int kk = 4 * (e % per), rr = e / per;
         const double* row = stile + rr * ld + kk;
-        const int c = 1040 + row_e[rr];
+        const int c = 1075 - 7 * S + row_e[rr];
         uint32_t f0[S], f1[S], f2[S], f3[S];
-        digits_of(row[0], c, f0);
-        digits_of(row[1], c, f1);
-        digits_of(row[2], c, f2);
-        digits_of(row[3], c, f3);
+        digits_of<S>(row[0], c, f0);
+        digits_of<S>(row[1], c, f1);
+        digits_of<S>(row[2], c, f2);
+        digits_of<S>(row[3], c, f3);
         __nv_bfloat16* out = dig + (size_t)(r0 + rr) * J.Kp + kk;
 #pragma unroll
         for (int sl = 0; sl < S; ++sl)
@@ -809,49 +936,44 @@ int num_sms() {
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-template <int RS>
+template <int RS, int S>
 int split_launch_rs(cudaStream_t s, const SplitJob& ja, const SplitJob& jb, bool same, int nb) {
     const size_t smem = split_smem(RS, ja.Kp);
-    BTA_TRY(ensure_dyn_smem((const void*)split_kernel<RS>, (int)smem));
+    BTA_TRY(ensure_dyn_smem((const void*)split_kernel<RS, S>, (int)smem));
     const dim3 grid(ja.Rp / RS + (same ? 0 : jb.Rp / RS), nb);
-    split_kernel<RS><<<grid, SPLIT_THREADS, smem, s>>>(ja, jb);
+    split_kernel<RS, S><<<grid, SPLIT_THREADS, smem, s>>>(ja, jb);
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }
 
 // Digits and row exponents of both operands (of one when they coincide).
+template <int S>
 int split_launch(cudaStream_t s, const SplitJob& ja, const SplitJob& jb, bool same, int nb) {
     const int rs = split_rows(ja.Kp);
     if (split_smem(rs, ja.Kp) > 227 * 1024) return BTA_ERR_ARG;   // K beyond 29 000
     switch (rs) {
-        case 8: return split_launch_rs<8>(s, ja, jb, same, nb);
-        case 4: return split_launch_rs<4>(s, ja, jb, same, nb);
-        case 2: return split_launch_rs<2>(s, ja, jb, same, nb);
-        default: return split_launch_rs<1>(s, ja, jb, same, nb);
+        case 8: return split_launch_rs<8, S>(s, ja, jb, same, nb);
+        case 4: return split_launch_rs<4, S>(s, ja, jb, same, nb);
+        case 2: return split_launch_rs<2, S>(s, ja, jb, same, nb);
+        default: return split_launch_rs<1, S>(s, ja, jb, same, nb);
     }
 }
 
-}  // namespace oz
+inline int tile_n(int slices) { return slices == 7 ? Cfg<7>::TN : Cfg<5>::TN; }
 
-// Workspace needed by ozaki_gemm for one M x N x K product (bytes; a batch of
-// products needs batch times this).
-size_t ozaki_workspace_bytes(int M, int N, int K) {
-    const size_t Mp = (size_t)oz::round_up(M, oz::PAD_M), Np = (size_t)oz::round_up(N, oz::PAD_N);
-    const size_t Kp = (size_t)std::max(oz::PAD_K, oz::round_up(K, oz::PAD_K));
-    return oz::S * (Mp + Np) * Kp * 2 + (Mp + Np) * sizeof(int) + 4 * 256;
+size_t workspace_bytes(int M, int N, int K, int S) {
+    const size_t Mp = (size_t)round_up(M, TM), Np = (size_t)round_up(N, tile_n(S));
+    const size_t Kp = (size_t)std::max(PAD_K, round_up(K, PAD_K));
+    return (size_t)S * (Mp + Np) * Kp * 2 + (Mp + Np) * sizeof(int) + 4 * 256;
 }
 
-// Largest M the tensor-core path accepts (row tiles per matrix).
-int ozaki_max_rows() { return oz::MAX_MT * oz::TM; }
-
-// C = beta Cin + alpha op(A) op(B) through the digit-split tensor-core path.
-// ws: device workspace of batch * ozaki_workspace_bytes(M, N, K); err: device int.
-int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
-    using namespace oz;
+template <int S>
+int gemm_s(cudaStream_t s, const Gemm64& g, void* ws, int* err, long long epi_wait) {
+    constexpr int TN = Cfg<S>::TN;
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return BTA_OK;
     if (g.M > MAX_MT * TM) return BTA_ERR_ARG;
     const int nb = g.batch;
-    const int Mp = round_up(g.M, PAD_M), Np = round_up(g.N, PAD_N);
+    const int Mp = round_up(g.M, TM), Np = round_up(g.N, TN);
     const int Kp = std::max(PAD_K, round_up(g.K, PAD_K));
     uint8_t* w = static_cast<uint8_t*>(ws);
     __nv_bfloat16* digA = reinterpret_cast<__nv_bfloat16*>(w);
@@ -868,8 +990,11 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     const bool same = g.A == g.B && g.sA == g.sB && g.M == g.N && srA == srB && skA == skB && g.shA == shBt;
     SplitJob ja{g.A, srA, skA, g.sA, g.M, g.K, g.shA, Mp, Kp, expA, digA};
     SplitJob jb{g.B, srB, skB, g.sB, g.N, g.K, shBt, Np, Kp, expB, digB};
-    BTA_TRY(split_launch(s, ja, jb, same, nb));
+    BTA_TRY(split_launch<S>(s, ja, jb, same, nb));
     // digit rows per slice of the B operand as the GEMM kernel reads them
+    // (TM is a multiple of TN for S = 7; for S = 5 the last column tile may
+    // read rows past Mp, which belong to the next slice and only feed output
+    // columns n >= N, never written)
     const int NpB = same ? Mp : Np;
     const __nv_bfloat16* digBr = same ? digA : digB;
     const int* expBr = same ? expA : expB;
@@ -894,6 +1019,8 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     const int nchunks = (a.kblocks + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
     long long ksplit = 1;
     if (base < sms) ksplit = std::min<long long>(nchunks, (sms + base - 1) / base);
+    // the 64-bit fixed-point sums of S = 7 hold at most INT_MAX_CHUNKS chunks
+    if (Cfg<S>::INT_ACC) ksplit = std::max<long long>(ksplit, (nchunks + INT_MAX_CHUNKS - 1) / INT_MAX_CHUNKS);
     if (base * ksplit > 0x7FFFFFFFLL) return BTA_ERR_ARG;
     a.ksplit = (int)ksplit;
     a.units = (int)(base * ksplit);
@@ -918,11 +1045,31 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
     a.shA = g.shA;
     a.shB = g.shB;
     a.err = err;
-    BTA_TRY(ensure_dyn_smem((const void*)ozaki_gemm_kernel, (int)SMEM_BYTES));
+    a.epi_wait = epi_wait > 0 ? epi_wait : WAIT_LIMIT_CYCLES;
+    BTA_TRY(ensure_dyn_smem((const void*)ozaki_gemm_kernel<S>, (int)Geo<S>::SMEM_BYTES));
     const int grid = (int)std::min<long long>(a.units, sms);
-    ozaki_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(mA, mB, a);
+    ozaki_gemm_kernel<S><<<grid, THREADS, Geo<S>::SMEM_BYTES, s>>>(mA, mB, a);
     BTA_LAUNCH_CHECK();
     return BTA_OK;
+}
+
+}  // namespace oz
+
+// Workspace needed by ozaki_gemm for one M x N x K product with `slices`
+// digit slices (bytes; a batch of products needs batch times this).
+size_t ozaki_workspace_bytes(int M, int N, int K, int slices) { return oz::workspace_bytes(M, N, K, slices); }
+
+// Largest M the tensor-core path accepts (row tiles per matrix).
+int ozaki_max_rows() { return oz::MAX_MT * oz::TM; }
+
+// C = beta Cin + alpha op(A) op(B) through the digit-split tensor-core path
+// with 5 or 7 digit slices.  ws: device workspace of batch *
+// ozaki_workspace_bytes(M, N, K, slices); err: device int; epi_wait: wait
+// limit (cycles) of the epilogue's accumulator hand-off, <= 0 for the default.
+int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err, int slices, long long epi_wait) {
+    if (slices == 7) return oz::gemm_s<7>(s, g, ws, err, epi_wait);
+    if (slices == 5) return oz::gemm_s<5>(s, g, ws, err, epi_wait);
+    return BTA_ERR_ARG;
 }
 
 // GEMM executor of the mixed path: products whose output is at least
@@ -932,11 +1079,18 @@ int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err) {
 // double-float GEMM on the FP32 pipe, arrow and tip products stay FP64.
 bool gemm_mixed_takes(const GemmExec* ex, const Gemm64& g) {
     return ex && ex->fn == gemm_mixed_fn && g.M >= ex->min_dim && g.N >= ex->min_dim && g.K >= 1 &&
-           g.M <= ozaki_max_rows() && (size_t)g.batch * ozaki_workspace_bytes(g.M, g.N, g.K) <= ex->ws_bytes;
+           g.M <= ozaki_max_rows() &&
+           (size_t)g.batch * ozaki_workspace_bytes(g.M, g.N, g.K, ex->slices) <= ex->ws_bytes;
 }
 
 int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
-    if (gemm_mixed_takes(ex, g)) return ozaki_gemm(s, g, ex->ws, ex->err);
+    if (gemm_mixed_takes(ex, g)) {
+        // test hook: BTA_OZ_EPI_WAIT (cycles) shortens the epilogue's wait for
+        // the accumulators, so that a test can make it run out
+        long long epi_wait = ex->epi_wait;
+        if (const char* e = std::getenv("BTA_OZ_EPI_WAIT")) epi_wait = std::atoll(e);
+        return ozaki_gemm(s, g, ex->ws, ex->err, ex->slices, epi_wait);
+    }
     // below the tensor-core threshold: square-ish products of the diagonal
     // recursion in double-float on the FP32 pipe, thin or tiny ones in FP64
     if (g.M >= 32 && g.N >= 32 && g.K >= 32 && g.batch <= 65535) return gemm_df32(s, g);

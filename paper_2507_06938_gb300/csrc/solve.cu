@@ -25,6 +25,12 @@ __global__ void ratio_sqrt_kernel(const double* num, const double* den, double* 
     *out = sqrt(*num) / sqrt(*den);
 }
 
+// out[j] = sqrt(d[3j + 1] / d[3j + 2]) for j < count (one thread each)
+__global__ void ratio_sqrt_batch_kernel(const double* d, int count, double* out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < count) out[j] = sqrt(d[3 * j + 1]) / sqrt(d[3 * j + 2]);
+}
+
 }  // namespace
 
 int axpby64(cudaStream_t s, long long len, double alpha, const double* x, double beta, const double* y,
@@ -138,5 +144,28 @@ extern "C" int bta_solve(bta_ctx_t ctx, int which, const double* rhs_dev, double
         ratio_sqrt_kernel<<<1, 1, 0, s>>>(d + 1, d + 2, resid_dev);
         BTA_LAUNCH_CHECK();
     }
+    return BTA_OK;
+}
+
+// ||b - Q_c mu||_2 / ||b||_2 of every slot's conditional mean from the last
+// f_obj group, with the assembled FP64 blocks of Q_c.
+extern "C" int bta_fobj_residual(bta_ctx_t ctx, double* out_dev) {
+    if (!ctx || !out_dev) return BTA_ERR_ARG;
+    const int B = ctx->batch;
+    for (int j = 0; j < B; ++j)
+        if (!ctx->factored[B + j]) return BTA_ERR_STATE;
+    cudaStream_t s = ctx->stream;
+    const long long N = ctx->N;
+    double* rhs = vec_row(ctx, VEC_RHS, B);
+    double* mu = vec_row(ctx, VEC_MU, B);
+    double* res = vec_row(ctx, VEC_RES, B);
+    BTA_TRY(matvec_impl(ctx, B, B, mu, res, s));
+    BTA_TRY(axpby64(s, B * N, 1.0, rhs, -1.0, res, res));
+    double* d = ctx->dots + 3 * B;
+    double* part = ctx->red + (long long)B * ctx->red_chunks;
+    BTA_TRY(dot_batch64(s, res, res, N, B, part, ctx->red_chunks, d + 1, 3));
+    BTA_TRY(dot_batch64(s, rhs, rhs, N, B, part, ctx->red_chunks, d + 2, 3));
+    ratio_sqrt_batch_kernel<<<(B + 127) / 128, 128, 0, s>>>(d, B, out_dev);
+    BTA_LAUNCH_CHECK();
     return BTA_OK;
 }

@@ -46,7 +46,7 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
         int leaf, df_leaf, min_dim;
     };
     std::vector<Cand> cands;
-    if (ctx->precision == BTA_MIXED) {
+    if (ctx->precision != BTA_FP64) {
         for (int dl : {32, 64, 128})
             for (int md : {128, 256}) cands.push_back({ctx->leaf, dl, md});
     } else {

@@ -8,33 +8,64 @@ import bench
 import synth
 
 
-def test_traffic_record_follows_the_captured_source(tmp_path, monkeypatch):
+def test_traffic_record_follows_the_captured_source_and_shape(tmp_path, monkeypatch):
     root = tmp_path
     (root / "profiles").mkdir()
     src_rel = "kernel.cu"
     (root / src_rel).write_text("prologue\n// begin\nkernel body\n// end\nhost code\n")
-    rec = {"source": src_rel, "region": ["// begin", "// end"], "bytes_per_launch": 123}
+    rec = {"kernel": "k", "M": 64, "N": 64, "K": 64, "batch": 2, "slices": 7, "source": src_rel,
+           "region": ["// begin", "// end"], "bytes_per_launch": 123}
     monkeypatch.setattr(bench, "ROOT", str(root))
     rec["source_sha1"] = bench.kernel_source_sha1(src_rel, rec["region"])
-    (root / "profiles" / "traffic.json").write_text(json.dumps({"k": rec}))
-    assert bench.traffic_record("k") == 123
+    (root / "profiles" / "traffic.json").write_text(json.dumps({"records": [rec]}))
+    shape = {"M": 64, "N": 64, "K": 64, "batch": 2, "slices": 7}
+    assert bench.traffic_record("k", shape) == 123
+    # another launch shape (batch, size or digit slices) has no capture
+    assert bench.traffic_record("k", dict(shape, batch=18)) is None
+    assert bench.traffic_record("k", dict(shape, M=6000)) is None
+    assert bench.traffic_record("k", dict(shape, slices=5)) is None
     # host code outside the region may change
     (root / src_rel).write_text("prologue\n// begin\nkernel body\n// end\nother host code\n")
-    assert bench.traffic_record("k") == 123
+    assert bench.traffic_record("k", shape) == 123
     # the kernel may not
     (root / src_rel).write_text("prologue\n// begin\nkernel body v2\n// end\nhost code\n")
-    assert bench.traffic_record("k") is None
+    assert bench.traffic_record("k", shape) is None
     # nor may its markers disappear
     (root / src_rel).write_text("prologue\nkernel body\n")
-    assert bench.traffic_record("k") is None
-    assert bench.traffic_record("missing") is None
+    assert bench.traffic_record("k", shape) is None
+    assert bench.traffic_record("missing", shape) is None
 
 
 def test_workload_text_and_l2_note_describe_the_problem():
     p = synth.problem_from_config("c2")
     text = bench.workload(p, 9)
-    for part in ("ns=1024", "nt=64", "nb=4", "m=65536", "N=65540", "9 theta points"):
+    for part in ("ns=1024", "nt=64", "nb=4", "m=65536", "N=65540", "9 theta point"):
         assert part in text, part
     assert bench.l2_note(p, 9).startswith("inputs larger than L2")
     small = synth.problem_from_config("t_uni")
     assert bench.l2_note(small, 1).startswith("inputs smaller than L2")
+
+
+def test_workload_of_the_default_configuration():
+    p = synth.problem_from_config(bench.CONFIG_NAME)
+    text = bench.workload(p, 1)
+    for part in ("3-variate coregional", "Delaunay", "ns=2000", "b=6000", "nt=48", "N=288006", "1 theta point"):
+        assert part in text, part
+    # about 96 GB per matrix with factor, inverse blocks and selected inverse
+    assert 90e9 < bench.matrix_bytes(p) < 100e9
+
+
+def test_errors_against_reference():
+    import numpy as np
+    ref = dict(ld_p=-2e5, ld_c=3e5, f=10.0, resid=1e-13, g=np.array([1.0, -2.0, 1e-6]),
+               sigma={(0, "D", 0): np.array([[2.0, 1.0], [1.0, 2.0]])})
+    mix = dict(ld_p=-2e5 * (1 + 1e-9), ld_c=3e5, f=10.0 + 5e-4, resid=2e-12, g=np.array([1.0, -2.0 + 2e-6, 0.0]),
+               sigma={(0, "D", 0): np.array([[2.0, 1.0 + 1e-8], [1.0, 2.0]])})
+    e = bench.errors_against(mix, ref)
+    assert abs(e["logdet_p_rel"] - 1e-9) < 1e-15
+    assert e["logdet_c_rel"] == 0.0
+    assert abs(e["f_rel_to_logdets"] - 5e-4 / 5e5) < 1e-15
+    assert e["solve_residual"] == 2e-12
+    assert abs(e["sigma_block_rel_max"] - 0.5e-8) < 1e-15
+    # gradient error relative to max(|g_k|, 1e-3 |g|_inf): the third entry's scale is 2e-3
+    assert abs(e["grad_rel_max"] - 1e-6 / 2e-3) < 1e-12

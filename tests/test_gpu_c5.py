@@ -1,0 +1,268 @@
+"""Parity of the large coregional model on an irregular mesh: nv = 3 fields
+on a Delaunay mesh of 2000 seeded points in the unit square (b = 6000),
+nt = 48, a = 6, N = 288,006, m = 144,000 (Eqs. 5, 11; Section IV-B), and its
+reduced copy on 200 points (b = 600, N = 28,806).
+
+The mesh of uniform random points has thin triangles: the SPDE precision's
+condition number is about 3e10 (8e3 on the regular grid of the trivariate
+benchmark), so the 35-bit split products of BTA_MIXED cannot hold the 1e-8
+log-determinant target here; the mixed path of these tests is BTA_MIXED_HI
+(49-bit digits).
+
+Reduced copy, against the oracle (every value computed by oracle/):
+  * log|Q_p| and log|Q_c| against the dense tier (LAPACK Cholesky of the
+    28,806 x 28,806 matrices);
+  * every selected-inverse block of Q_p and Q_c against the block tier (which
+    the CPU tests pin to the dense inverse);
+  * the conditional mean through its residual with the oracle's sparse Q_c;
+  * f against the block tier;
+  * the adjoint gradient against the oracle's block-tier adjoint gradient
+    (pinned to the dense tier and to central differences) and against central
+    differences of the GPU's own f (h = 1e-3, truncation O(h^2): 1e-5).
+Full size, where the dense tier cannot run:
+  * log|Q_p| against the mixing closed form and sampled blocks of Sigma_p
+    against the closed-form covariance (as for the trivariate grid model);
+  * the conditional mean through its residual, and the library's own
+    residual report (bta_fobj_residual) against it;
+  * the diagonal blocks of Sigma_c Q_c = I at three time steps;
+  * f at a sampled theta against the oracle's block tier;
+  * the mixed gradient against the FP64 gradient.
+Tolerances: FP64 log-det 1e-10, Sigma 1e-9, residual 1e-10, f 1e-9 relative;
+BTA_MIXED_HI log-det 1e-9, Sigma 1e-8, residual 1e-10, f 1e-9 of
+|log|Q_p|| + |log|Q_c||, gradient 1e-6 (FP64 1e-7)."""
+
+import time
+
+import numpy as np
+import pytest
+
+from oracle import bta as obta
+from oracle import dense as odense
+from oracle import fobj as ofobj
+from oracle import model as omodel
+
+from gpu_util import build_lib, dev, need_gpu, problem, rel_max
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+H = 1e-3
+FP64, MIXED_HI = 0, 2
+
+
+def _theta(p, seed):
+    return p.theta0 + 0.02 * np.random.default_rng(seed).standard_normal(p.theta0.shape)
+
+
+def _run(p, precision, theta, with_fd=False, sample_blocks=None):
+    """f, gradient, mu, both log-dets, the reported residual and Sigma blocks
+    (all, or the sampled ones) of one evaluation; optionally the central
+    differences of f around theta."""
+    import torch
+    from paper_2507_06938_gb300 import bta
+    model = bta.BtaModel(p)
+    ctx = bta.BtaContext(p.nt, p.b, p.a, precision, None, 1)
+    th = dev(theta[None, :])
+    f = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.zeros((1, theta.shape[0]), dtype=torch.float64, device="cuda")
+    mu = torch.zeros((1, p.N), dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    ctx.fobj_eval(model, th, f, mu)
+    ctx.fobj_grad(model, th, f, g)
+    ctx.sync()
+    dt = time.perf_counter() - t0
+    ld = torch.zeros(2, dtype=torch.float64, device="cuda")
+    ctx.logdet(bta.BTA_QP, ld[0:1])
+    ctx.logdet(bta.BTA_QC, ld[1:2])
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.fobj_residual(res)
+    ctx.sync()
+    out = dict(f=f.item(), g=g[0].cpu().numpy(), mu=mu[0].cpu().numpy(), ld_p=ld[0].item(), ld_c=ld[1].item(),
+               resid=res.item(), seconds=dt)
+    S = bta.BTA_STORE_SIGMA
+    kinds = {"D": bta.BTA_BLK_D, "B": bta.BTA_BLK_B, "R": bta.BTA_BLK_R, "T": bta.BTA_BLK_T}
+    sig = {}
+    for which in (bta.BTA_QP, bta.BTA_QC):
+        if sample_blocks is None:
+            sig[which] = dict(
+                D=np.stack([ctx.block(which, S, kinds["D"], i).cpu().numpy() for i in range(p.nt)]),
+                B=np.stack([ctx.block(which, S, kinds["B"], i).cpu().numpy() for i in range(p.nt - 1)]),
+                R=np.stack([ctx.block(which, S, kinds["R"], i).cpu().numpy() for i in range(p.nt)]),
+                T=ctx.block(which, S, kinds["T"]).cpu().numpy())
+        else:
+            sig[which] = {(k, i): ctx.block(which, S, kinds[k], i).cpu().numpy() for k, i in sample_blocks}
+    out["sigma"] = sig
+    if with_fd:
+        pts = []
+        for k in range(theta.shape[0]):
+            e = np.zeros_like(theta)
+            e[k] = H
+            pts += [theta + e, theta - e]
+        fs = torch.zeros(len(pts), dtype=torch.float64, device="cuda")
+        ctx.fobj_eval(model, dev(np.stack(pts)), fs)
+        ctx.sync()
+        fv = fs.cpu().numpy()
+        out["g_fd"] = (fv[0::2] - fv[1::2]) / (2 * H)
+    ctx.close()
+    model.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------------------------- reduced copy (ns = 200)
+
+@pytest.fixture(scope="module")
+def reduced():
+    need_gpu()
+    build_lib()
+    p = problem("c5r")
+    theta = _theta(p, 51)
+    fd = omodel.fem_data(p)
+    terms = ofobj.f_obj_terms(p, theta, tier="bta", fd=fd)
+    built = terms["built"]
+    ld_dense = {"p": odense.logdet(built.Qp), "c": odense.logdet(built.Qc)}
+    sig = {}
+    for key, Q in (("p", built.Qp), ("c", built.Qc)):
+        sig[key] = obta.selinv(obta.factor(obta.blocks_from_sparse(Q, p.nt, p.b, p.a)))
+    g = ofobj.grad_adjoint(p, theta, fd=fd, tier="bta")
+    return dict(p=p, theta=theta, terms=terms, ld=ld_dense, sig=sig, g=g, built=built)
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED_HI])
+def test_reduced_copy_against_oracle(reduced, precision):
+    from paper_2507_06938_gb300 import bta
+    p, theta, terms, built = reduced["p"], reduced["theta"], reduced["terms"], reduced["built"]
+    r = _run(p, precision, theta, with_fd=True)
+    hi = precision == FP64
+    print(f"\nc5r precision {precision}: {r['seconds']:.2f} s")
+    for key, val in (("p", r["ld_p"]), ("c", r["ld_c"])):
+        ref = reduced["ld"][key]
+        err = abs(val - ref) / max(abs(ref), 1.0)
+        print(f"  logdet {key}: {err:.2e}")
+        assert err <= (1e-10 if hi else 1e-9), (key, err)
+    for key, which in (("p", bta.BTA_QP), ("c", bta.BTA_QC)):
+        So = reduced["sig"][key]
+        for k in ("D", "B", "R", "T"):
+            e = max(rel_max(r["sigma"][which][k][i], So[k][i]) for i in range(So[k].shape[0])) if k != "T" \
+                else rel_max(r["sigma"][which][k], So[k])
+            print(f"  Sigma_{key} {k}: {e:.2e}")
+            assert e <= (1e-9 if hi else 1e-8), (key, k, e)
+    res = np.linalg.norm(built.Qc @ r["mu"] - built.rhs) / np.linalg.norm(built.rhs)
+    assert res <= 1e-10, res
+    assert r["resid"] <= 1e-10 and abs(r["resid"] - res) <= 1e-12 + 1e-3 * res, (r["resid"], res)
+    ftol = 1e-9 * (abs(terms["f"]) if hi else abs(terms["logdet_p"]) + abs(terms["logdet_c"]))
+    assert abs(r["f"] - terms["f"]) <= ftol, (r["f"], terms["f"])
+    gref = reduced["g"]
+    scale = np.maximum(np.abs(gref), 1e-3 * np.max(np.abs(gref)))
+    err_g = np.max(np.abs(r["g"] - gref) / scale)
+    err_fd = np.max(np.abs(r["g"] - r["g_fd"]) / scale)
+    print(f"  gradient vs oracle {err_g:.2e}, vs own central differences {err_fd:.2e}")
+    assert err_g <= (1e-7 if hi else 1e-6)
+    assert err_fd <= 1e-5
+
+
+# ----------------------------------------------------------------------------- full size (ns = 2000)
+
+@pytest.fixture(scope="module")
+def full():
+    need_gpu()
+    build_lib()
+    p = problem("c5")
+    theta = _theta(p, 52)
+    fd = omodel.fem_data(p)
+    prm = omodel.theta_to_params(theta, p.nv)
+    built = omodel.build(p, prm, fd)
+    ld = 0.0
+    Cs = []
+    for u in range(p.nv):
+        Qs = omodel.spde_precision(fd.C, fd.G, prm.kappa[u], prm.tau[u]).toarray()
+        sgn, ld_s = np.linalg.slogdet(Qs)
+        assert sgn > 0
+        ld_t = -(p.nt - 1) * np.log(1.0 - prm.rho[u] ** 2)
+        ld += (p.ns * ld_t + p.nt * ld_s + p.nr * np.log(p.beta_prior_prec)
+               - (p.ns * p.nt + p.nr) * np.log(prm.sigma[u] ** 2))
+        Cs.append(np.linalg.inv(Qs))
+    return dict(p=p, theta=theta, fd=fd, built=built, ld_p=ld, Cs=Cs, Lam=omodel.mixing_matrix(prm),
+                rho=prm.rho, results={})
+
+
+def _full_run(full, precision):
+    if precision not in full["results"]:
+        p = full["p"]
+        n = p.nt
+        blocks = [("D", 0), ("D", n // 2), ("D", n - 1), ("B", 0), ("B", n // 2 - 1), ("B", n // 2),
+                  ("B", n - 2), ("R", 0), ("R", n // 2), ("R", n - 1), ("T", 0)]
+        full["results"][precision] = _run(p, precision, full["theta"], sample_blocks=blocks)
+    return full["results"][precision]
+
+
+@pytest.mark.parametrize("precision", [MIXED_HI, FP64])
+def test_full_size_closed_forms_and_identities(full, precision):
+    from paper_2507_06938_gb300 import bta
+    p, built = full["p"], full["built"]
+    n, b, a, ns, nv = p.nt, p.b, p.a, p.ns, p.nv
+    r = _full_run(full, precision)
+    print(f"\nc5 precision {precision}: f, gradient and both selected inversions in {r['seconds']:.1f} s")
+    hi = precision == FP64
+    err = abs(r["ld_p"] - full["ld_p"]) / abs(full["ld_p"])
+    print(f"  log|Q_p| vs closed form {err:.2e}")
+    assert err <= (1e-10 if hi else 1e-9)
+    Lam, rho, Cs = full["Lam"], full["rho"], full["Cs"]
+
+    def sig_block(dt):
+        out = np.zeros((b, b))
+        for v in range(nv):
+            for w in range(nv):
+                out[v * ns:(v + 1) * ns, w * ns:(w + 1) * ns] = sum(
+                    Lam[v, u] * Lam[w, u] * rho[u] ** dt * Cs[u] for u in range(nv))
+        return out
+
+    sp_tol = 1e-9 if hi else 1e-8
+    D_ref, B_ref = sig_block(0), sig_block(1)
+    Sp = r["sigma"][bta.BTA_QP]
+    for (k, i), blk in Sp.items():
+        if k in ("D", "B"):
+            e = rel_max(blk, D_ref if k == "D" else B_ref)
+            assert e <= sp_tol, (k, i, e)
+    res = np.linalg.norm(built.Qc @ r["mu"] - built.rhs) / np.linalg.norm(built.rhs)
+    print(f"  mu residual {res:.2e} (reported {r['resid']:.2e})")
+    assert res <= 1e-10
+    assert abs(r["resid"] - res) <= 1e-12 + 1e-3 * res
+    # diagonal blocks of Sigma_c Q_c = I at three time steps
+    Qc = built.Qc.tocsr()
+    Sc = r["sigma"][bta.BTA_QC]
+    tip = slice(n * b, n * b + a)
+
+    def Qblk(r0, r1, c0, c1):
+        return Qc[r0:r1, c0:c1].toarray()
+
+    for i in (0, n // 2, n - 1):
+        rows = slice(i * b, (i + 1) * b)
+        acc = Sc[("D", i)] @ Qblk(rows.start, rows.stop, rows.start, rows.stop)
+        if i > 0:
+            acc += Sc[("B", i - 1)] @ Qblk((i - 1) * b, i * b, rows.start, rows.stop)
+        if i < n - 1:
+            acc += Sc[("B", i)].T @ Qblk((i + 1) * b, (i + 2) * b, rows.start, rows.stop)
+        acc += Sc[("R", i)].T @ Qblk(tip.start, tip.stop, rows.start, rows.stop)
+        scale = np.max(np.abs(Sc[("D", i)])) * abs(Qc).max() * 40
+        e = np.max(np.abs(acc - np.eye(b)))
+        print(f"  (Sigma_c Q_c)_{i},{i} - I: {e:.2e} (scale {scale:.2e})")
+        assert e <= (1e-9 if hi else 1e-8) * max(scale, 1.0), (i, e, scale)
+
+
+def test_full_size_f_and_gradient(full):
+    """f at the sampled theta against the oracle's block tier (FP64 and 49-bit
+    mixed), and the mixed gradient against the FP64 gradient."""
+    p, theta = full["p"], full["theta"]
+    terms = ofobj.f_obj_terms(p, theta, tier="bta", fd=full["fd"])
+    scale_ld = abs(terms["logdet_p"]) + abs(terms["logdet_c"])
+    r64 = _full_run(full, FP64)
+    rhi = _full_run(full, MIXED_HI)
+    print(f"\nc5 f: oracle {terms['f']:.10f} FP64 {r64['f']:.10f} mixed-hi {rhi['f']:.10f}")
+    assert abs(r64["f"] - terms["f"]) <= 1e-9 * abs(terms["f"])
+    assert abs(rhi["f"] - terms["f"]) <= 1e-9 * scale_ld
+    assert abs(r64["ld_c"] - terms["logdet_c"]) <= 1e-10 * abs(terms["logdet_c"])
+    g64 = r64["g"]
+    scale = np.maximum(np.abs(g64), 1e-3 * np.max(np.abs(g64)))
+    err = np.max(np.abs(rhi["g"] - g64) / scale)
+    print(f"  mixed-hi gradient vs FP64: {err:.2e}")
+    assert err <= 1e-6
