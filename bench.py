@@ -485,10 +485,14 @@ def errors_against(mixed_last, ref_last):
     g_ref = ref_last["g"]
     scale = np.maximum(np.abs(g_ref), 1e-3 * np.max(np.abs(g_ref)))
     sig = []
+    by_block = {}
     for key, blk in ref_last["sigma"].items():
         m = float(np.max(np.abs(blk)))
         if m > 0:
-            sig.append(float(np.max(np.abs(mixed_last["sigma"][key] - blk))) / m)
+            e = float(np.max(np.abs(mixed_last["sigma"][key] - blk))) / m
+            sig.append(e)
+            kind, k, i = key
+            by_block[f"{'Q_p' if kind == 0 else 'Q_c'} {k}{i}"] = e
     return {
         "logdet_p_rel": abs(mixed_last["ld_p"] - ref_last["ld_p"]) / max(abs(ref_last["ld_p"]), 1.0),
         "logdet_c_rel": abs(mixed_last["ld_c"] - ref_last["ld_c"]) / max(abs(ref_last["ld_c"]), 1.0),
@@ -498,6 +502,7 @@ def errors_against(mixed_last, ref_last):
         "solve_residual_fp64": ref_last["resid"],
         "sigma_block_rel_max": max(sig) if sig else None,
         "sigma_blocks_compared": len(sig),
+        "sigma_block_rel": by_block,
         "grad_rel_max": float(np.max(np.abs(mixed_last["g"] - g_ref) / scale)),
         "reference": "FP64 path of this library at the same theta (the last timed mixed step's)",
         "targets": {"logdet_rel": 1e-8, "solve_residual": 1e-10},
@@ -555,8 +560,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(B * dim * 8),
                 "d2h_bytes_per_step": int(B * (8 + dim * 8 + p.N * 8))},
         "batch": B,
-        "autotuned": (None if r["tuned"] is None else
-                      dict(zip(("fp64_leaf", "df32_leaf", "tensor_min_dim"), r["tuned"]))),
+        "autotuned": (None if r["tuned"] is None else dict(zip(bta.BtaContext.AUTOTUNE_KEYS, r["tuned"]))),
         "gpu_launches": int(r["launches"]),
         "clocks": r["clocks"],
         "fp64_peak_measured": {"dfma_tflops": fp64_peak["dfma"], "dmma_tflops": fp64_peak["dmma"],

@@ -311,6 +311,34 @@ int bta_fobj_eval_multi(int count, const bta_ctx_t* ctxs, const bta_model_t* mod
                         const double* const* thetas_dev, const int* n_theta, double* const* f_out_dev,
                         double* const* mu_out_dev, double* const* grad_out_dev, void* join);
 
+/* Likelihoods of bta_fobj_laplace. */
+#define BTA_LIK_GAUSSIAN 0   /* y_k ~ N(eta_k, 1/tau_eps of the variable)        */
+#define BTA_LIK_POISSON 1    /* y_k ~ Poisson(exp(eta_k)), counts                 */
+
+/*
+ * bta_fobj_laplace -- f_obj (Eq. 8) for a non-Gaussian likelihood by the
+ * Laplace approximation at the mode x* of the latent field (Section II-A.3:
+ * p_G from a second-order Taylor expansion of the log-likelihood ell,
+ * Q_c(x) = Q_p + A^T D(x) A with D the negative Hessian of ell in the linear
+ * predictor eta = A x, Eq. 4).  x* is found by newton_iters (1..1000) Newton
+ * steps from x = 0, each an assembly of Q_c(x_k) with per-observation
+ * weights, a block Cholesky and a solve of Q_c(x_k) x_{k+1} = A^T (g + D eta)
+ * with g = d ell / d eta (refined with an FP64 residual in mixed precision);
+ * then Q_c(x*) is assembled and factored once more and
+ *   f = log p(theta) + ell(y | x*) + 1/2 log|Q_p| - 1/2 x*^T Q_p x*
+ *       - 1/2 log|Q_c(x*)|.
+ * likelihood: BTA_LIK_POISSON (log link; y of the model are counts) or
+ * BTA_LIK_GAUSSIAN (the f of fobj_eval, reached in one step).  thetas_dev:
+ * device, n_theta x dim(theta) (the noise-precision entries enter only the
+ * hyperprior for Poisson data).  f_out_dev: n_theta values; x_out_dev (NULL
+ * or n_theta x N): the modes; step_out_dev (NULL or n_theta): max |x_K -
+ * x_{K-1}| of the last Newton step, a convergence measure.  Groups of the
+ * context's batch run through the same launches.  Afterwards the Q_p and
+ * Q_c(x*) storage of slot j hold the last group's matrices and factors.
+ */
+int bta_fobj_laplace(bta_ctx_t ctx, bta_model_t model, const double* thetas_dev, int n_theta, int likelihood,
+                     int newton_iters, double* f_out_dev, double* x_out_dev, double* step_out_dev);
+
 /* bta_fobj_residual -- accuracy of the conditional means of the last
  * fobj_eval / bta_fobj_grad group: out_dev (device, batch values) receives
  * ||b - Q_c mu||_2 / ||b||_2 for every parameter slot (slot j holds theta
@@ -352,19 +380,25 @@ long long bta_launch_count(void);
 int bta_profile(bta_ctx_t ctx, int enable);
 int bta_profile_read(bta_ctx_t ctx, double* ms_total, long long* launches, double* flops_total);
 
-/* bta_autotune -- choose the launch shapes of the diagonal-block
- * factorisation (the latency-bound chain of the block Cholesky, Section
- * III-A) for this context's block order, precision and batch by timing
- * candidates on the context's own storage: the FP64 leaf order (16, 32, 64),
- * or in mixed precision the double-float leaf order (32, 64, 128) and the
- * smallest product dimension sent to the tensor cores (128, 256).  Each
- * candidate runs once untimed and `reps` (>= 1) times timed.  The chosen
- * values are written to chosen[0..2] (host: leaf, double-float leaf, tensor
- * threshold) and used by every later call on the context.  The first
- * diagonal block of every matrix is overwritten with a synthetic SPD block:
- * call it before assembling, or assemble again afterwards.  Synchronises the
- * context's stream.  Errors: BTA_ERR_ARG (null pointers, reps < 1), CUDA
- * errors. */
+/* bta_autotune -- choose the launch shapes of the block factorisation and
+ * selected inversion for this context's block order, precision and batch by
+ * timing candidates on the context's own storage (Section III-A's
+ * operations; the sequential diagonal chain and the b x b x b products):
+ *   the FP64 leaf order (16, 32, 64), or in mixed precision the
+ *   double-float leaf order (32, 64, 128) and the smallest product dimension
+ *   sent to the tensor cores (128, 256), timed on the diagonal-block chain;
+ *   then, timed on a batched b x b x b lower update, in mixed precision the
+ *   split-product tile (35-bit digits: 0 = 128 x 96 tiles with 2 TMA stages,
+ *   1 = 128 x 64 with 3; 49-bit digits: 0 = 128 x 64 with 2) and the waves of
+ *   the persistent grid below which it splits K (1, 2), in FP64 the CTAs per
+ *   SM of the DFMA GEMM's K split (1, 2, 4).
+ * Each candidate runs once untimed and `reps` (>= 1) times timed.  The
+ * chosen values are written to chosen[0..5] (host: leaf, double-float leaf,
+ * tensor threshold, tile, waves, FP64 CTAs per SM) and used by every later
+ * call on the context.  The first diagonal block of every matrix is
+ * overwritten with a synthetic SPD block: call it before assembling, or
+ * assemble again afterwards.  Synchronises the context's stream.  Errors:
+ * BTA_ERR_ARG (null pointers, reps < 1), CUDA errors. */
 int bta_autotune(bta_ctx_t ctx, int reps, int* chosen);
 
 /*

@@ -18,7 +18,11 @@ Modules
             and selected inversion (Section III-A), for sizes where a dense
             N x N matrix does not fit in seconds.  Pinned against tier D.
   fobj   -- the objective f_obj(theta) of Eq. 8 term by term, the central
-            finite-difference gradient of Eq. 10, and the adjoint gradient.
+            finite-difference gradient of Eq. 10, and the adjoint gradient
+            (dense or block tier).
+  laplace -- f_obj for a non-Gaussian (Poisson) likelihood: Newton
+            iterations for the mode x* of the latent field and the Laplace
+            approximation at x* (Section II-A.3, Eqs. 4, 7, 8).
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` (closed forms, invariants, brute force and

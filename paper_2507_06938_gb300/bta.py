@@ -24,6 +24,7 @@ BTA_OK, BTA_ERR_ARG, BTA_ERR_OOM, BTA_ERR_NOT_PD = 0, 1, 2, 3
 BTA_ERR_TIMEOUT, BTA_ERR_NONFINITE, BTA_ERR_CUDA, BTA_ERR_STATE = 4, 5, 6, 7
 BTA_QP, BTA_QC = 0, 1
 BTA_FP64, BTA_MIXED, BTA_MIXED_HI = 0, 1, 2
+BTA_LIK_GAUSSIAN, BTA_LIK_POISSON = 0, 1
 BTA_BLK_D, BTA_BLK_B, BTA_BLK_R, BTA_BLK_T = 0, 1, 2, 3
 BTA_STORE_Q, BTA_STORE_L, BTA_STORE_SIGMA, BTA_STORE_LINV = 0, 1, 2, 3
 
@@ -91,6 +92,7 @@ def lib():
         "bta_fobj_eval_multi": (ip, [ip, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(ip),
                                      C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]),
         "bta_fobj_residual": (ip, [vp, vp]),
+        "bta_fobj_laplace": (ip, [vp, vp, vp, ip, ip, ip, vp, vp, vp]),
         "bta_fobj_grad_host": (ip, [vp, vp, vp, ip, vp, vp, vp]),
         "bta_fp64_peak": (ip, [ip, C.POINTER(dp)]),
         "bta_flops_factor": (dp, [ip, ip, ip]),
@@ -113,7 +115,7 @@ def exported_symbols():
             "bta_launch_count", "bta_profile", "bta_profile_read", "bta_chol_inv_noalloc",
             "bta_create_batched", "bta_batch_size", "bta_factor_batch", "bta_selinv_batch",
             "bta_last_error_matrix", "bta_fobj_grad", "bta_autotune", "bta_fobj_eval_multi",
-            "bta_fobj_residual", "bta_fp64_peak", "bta_fobj_grad_host"]
+            "bta_fobj_residual", "bta_fp64_peak", "bta_fobj_grad_host", "bta_fobj_laplace"]
 
 
 def _check(code: int, where: str):
@@ -261,13 +263,17 @@ class BtaContext:
     def selinv_diag(self, which: int, out):
         _check(lib().bta_selinv_diag(self.handle, which, _ptr(out)), "bta_selinv_diag")
 
+    AUTOTUNE_KEYS = ("fp64_leaf", "df32_leaf", "tensor_min_dim", "split_tile", "split_waves", "fp64_ctas_per_sm")
+
     def autotune(self, reps: int = 2):
-        """bta_autotune: time the diagonal-block launch-shape candidates on this
-        context's storage and keep the fastest; returns (leaf, df_leaf, tensor
-        threshold).  Overwrites the first diagonal block of every matrix."""
-        out = (C.c_int * 3)()
+        """bta_autotune: time the launch-shape candidates of the diagonal chain
+        and of the b x b x b products on this context's storage and keep the
+        fastest; returns (leaf, df_leaf, tensor threshold, split-product tile,
+        split waves, FP64 CTAs per SM).  Overwrites the first diagonal block
+        of every matrix."""
+        out = (C.c_int * 6)()
         _check(lib().bta_autotune(self.handle, int(reps), out), "bta_autotune")
-        return int(out[0]), int(out[1]), int(out[2])
+        return tuple(int(v) for v in out)
 
     def profile(self, enable: bool):
         _check(lib().bta_profile(self.handle, 1 if enable else 0), "bta_profile")
@@ -299,6 +305,15 @@ class BtaContext:
         _check(lib().bta_fobj_grad_host(self.handle, model.handle, hp(thetas, "thetas"), n_theta,
                                         hp(f_out, "f_out"), hp(grad_out, "grad_out"), hp(var_out, "var_out")),
                "bta_fobj_grad_host")
+
+    def fobj_laplace(self, model: BtaModel, thetas, likelihood: int, newton_iters: int, f_out, x_out=None,
+                     step_out=None):
+        """bta_fobj_laplace: f_obj by the Laplace approximation at the Newton
+        mode of the latent field (non-Gaussian likelihoods)."""
+        n_theta = int(thetas.shape[0]) if thetas.dim() == 2 else 1
+        _check(lib().bta_fobj_laplace(self.handle, model.handle, _ptr(thetas), n_theta, int(likelihood),
+                                      int(newton_iters), _ptr(f_out), _ptr(x_out), _ptr(step_out)),
+               "bta_fobj_laplace")
 
     def fobj_residual(self, out):
         """||b - Q_c mu|| / ||b|| of every slot's conditional mean (last group)."""
@@ -467,6 +482,11 @@ def bta_chol_inv_noalloc(A, X, info, stream=None):
 
 def bta_fobj_grad_host(ctx: BtaContext, model: BtaModel, thetas, f_out, grad_out, var_out=None):
     ctx.fobj_grad_host(model, thetas, f_out, grad_out, var_out)
+
+
+def bta_fobj_laplace(ctx: BtaContext, model: BtaModel, thetas, likelihood, newton_iters, f_out, x_out=None,
+                     step_out=None):
+    ctx.fobj_laplace(model, thetas, likelihood, newton_iters, f_out, x_out, step_out)
 
 
 def bta_fobj_residual(ctx: BtaContext, out):

@@ -145,6 +145,7 @@ extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch,
         c->exec.df_leaf = 64;
         if (const char* e = std::getenv("BTA_DF_LEAF")) c->exec.df_leaf = std::atoi(e);
         c->exec.slices = precision == BTA_MIXED_HI ? 7 : 5;
+        if (const char* e = std::getenv("BTA_OZ_TILE")) c->exec.tile = std::atoi(e) == 1 && c->exec.slices == 5 ? 1 : 0;
         const size_t wsb = (size_t)nm * ozaki_workspace_bytes(b, b, b, c->exec.slices);
         if (cudaMalloc(&c->exec.ws, wsb) != cudaSuccess) {
             c->exec.ws = nullptr;
@@ -215,7 +216,7 @@ extern "C" int bta_destroy(bta_ctx_t c) {
     store_free(c->S);
     if (c->fobj_graph) cudaGraphExecDestroy(c->fobj_graph);
     double* bufs[] = {c->Linv, c->work, c->vec, c->red, c->ld, c->dots, c->params, c->theta_buf, c->f_buf,
-                      c->adj, c->hs_theta, c->hs_f, c->hs_grad, c->hs_var};
+                      c->adj, c->hs_theta, c->hs_f, c->hs_grad, c->hs_var, c->lap};
     for (double* p : bufs)
         if (p) cudaFree(p);
     if (c->exec.ws) cudaFree(c->exec.ws);

@@ -36,6 +36,7 @@ struct AsmArgs {
     const double* gram;
     const double* arrow;
     const double* tipgram;
+    long long gs, as, ts;    // per-slot strides of gram / arrow / tipgram (0: the model's, shared)
     const double* params;    // parameter slots, pstride apart (0: one vector for all)
     long long pstride;
     double beta_prec;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(ASM_THREADS) assemble_db_kernel(AsmArgs p) {
     __syncthreads();
     const int r0 = p.rowptr[sp], r1 = p.rowptr[sp + 1];
     const int len = r1 - r0;
-    const double* gram = p.gram + ((size_t)t * nv + vp) * p.nnz;
+    const double* gram = p.gram + (mat % p.batch) * p.gs + ((size_t)t * nv + vp) * p.nnz;
     for (int e = threadIdx.x; e < len * nv; e += ASM_THREADS) {
         const int v = e / len;
         const int q = r0 + (e - v * len);
@@ -111,6 +112,8 @@ __global__ void assemble_rt_kernel(AsmArgs p) {
     const double* lam = params + 5 * nv;
     double* R = p.R + mat * p.sR;
     double* T = p.T + mat * p.sT;
+    const double* arrow = p.arrow + (mat % p.batch) * p.as;
+    const double* tipgram = p.tipgram + (mat % p.batch) * p.ts;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const long long nab = (long long)p.n * p.a * p.b;
@@ -122,7 +125,7 @@ __global__ void assemble_rt_kernel(AsmArgs p) {
             const int vp = colj / p.ns, s = colj % p.ns;
             double val = 0.0;
             if (with_obs && v == vp)
-                val = params[5 * v + 4] * p.arrow[(((size_t)t * nv + v) * nr + r) * p.ns + s];
+                val = params[5 * v + 4] * arrow[(((size_t)t * nv + v) * nr + r) * p.ns + s];
             R[idx] = val;
         } else {
             const int e = (int)(idx - nab);
@@ -138,7 +141,7 @@ __global__ void assemble_rt_kernel(AsmArgs p) {
                 val *= p.beta_prec;
             }
             if (with_obs && v == vp)
-                val += params[5 * v + 4] * p.tipgram[((size_t)v * nr + r) * nr + rp];
+                val += params[5 * v + 4] * tipgram[((size_t)v * nr + r) * nr + rp];
             T[e] = val;
         }
     }
@@ -173,7 +176,7 @@ int theta_to_params_impl(bta_model_t m, const double* theta, int count, double* 
 }
 
 static int assemble_run(bta_ctx_t ctx, bta_model_t m, const double* params, long long pstride, int m0, int count,
-                        cudaStream_t s) {
+                        cudaStream_t s, const ObsWeights* w = nullptr) {
     if (count <= 0) return BTA_OK;
     AsmArgs p;
     p.n = ctx->n; p.b = ctx->b; p.a = ctx->a;
@@ -182,6 +185,12 @@ static int assemble_run(bta_ctx_t ctx, bta_model_t m, const double* params, long
     p.rowptr = m->rowptr; p.col = m->col;
     p.cval = m->cval; p.gval = m->gval; p.kval = m->kval; p.gram = m->gram;
     p.arrow = m->arrow; p.tipgram = m->tipgram;
+    p.gs = p.as = p.ts = 0;
+    if (w) {
+        // observation terms weighted per observation and slot (non-Gaussian likelihoods)
+        p.gram = w->gram; p.arrow = w->arrow; p.tipgram = w->tip;
+        p.gs = w->gram_stride; p.as = w->arrow_stride; p.ts = w->tip_stride;
+    }
     p.params = params;
     p.pstride = pstride;
     p.beta_prec = m->beta_prec;
@@ -205,6 +214,11 @@ static int assemble_run(bta_ctx_t ctx, bta_model_t m, const double* params, long
 
 int assemble_impl(bta_ctx_t ctx, bta_model_t m, const double* params, int m0, int count, cudaStream_t s) {
     return assemble_run(ctx, m, params, BTA_PSTRIDE, m0, count, s);
+}
+
+int assemble_weighted_impl(bta_ctx_t ctx, bta_model_t m, const double* params, int m0, int count, cudaStream_t s,
+                           const ObsWeights& w) {
+    return assemble_run(ctx, m, params, BTA_PSTRIDE, m0, count, s, &w);
 }
 
 extern "C" int bta_assemble(bta_ctx_t ctx, bta_model_t m, const double* params_dev, int which) {

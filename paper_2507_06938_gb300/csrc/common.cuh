@@ -60,6 +60,15 @@ struct bta_model_s {
     double* theta0;          // dim_theta
     double* var_stats;       // 2 nv: ||y_v||^2, m_v
     double beta_prec;
+    // per observation k (non-Gaussian likelihoods): tv = t nv + v, the three
+    // triangle nodes and barycentric weights, the positions of the nine
+    // products w_q w_r in the Gram pattern of (t, v), covariates and y
+    int* obs_tv;             // m
+    int* obs_s;              // 3 m
+    double* obs_w;           // 3 m
+    int* obs_gpos;           // 9 m
+    double* obs_X;           // m nr
+    double* obs_y;           // m
 };
 
 // ---------------------------------------------------------------- dense GEMM descriptor
@@ -88,6 +97,9 @@ struct GemmExec {
     int df_leaf = 0;   // > 0: diagonal leaves of this order in double-float (leaf_df32.cu)
     int slices = 5;    // digit slices of the split products: 5 (35 bits) or 7 (49 bits)
     long long epi_wait = 0;   // wait limit of the tensor kernel's epilogue hand-off (0: default)
+    int tile = 0;      // tile configuration of the split product (autotuned)
+    int occupancy = 1; // waves of the persistent split-product grid before a K split (autotuned)
+    int fp64_ctas = 2; // CTAs per SM the FP64 GEMM aims for through its K split (autotuned)
 };
 
 // Side stream, events and executor for the products of the recursive
@@ -161,6 +173,10 @@ struct bta_ctx_s {
     double* hs_grad = nullptr;     // batch x dim_theta
     double* hs_var = nullptr;      // batch x N
     int hs_dim = 0;
+    // workspace of the Laplace evaluation (allocated on first use)
+    double* lap = nullptr;         // per slot: obs weights, obs rhs terms, log-likelihood terms, x_new, params
+    long long lap_slot = 0;        // doubles per slot
+    const void* lap_model = nullptr;
     // optional event timing of the b x b x b Schur-update GEMM launches
     int prof = 0;
     std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
@@ -180,7 +196,7 @@ int prof_begin(bta_ctx_t ctx, cudaStream_t s, double flops, cudaEvent_t* stop_ou
 int prof_record(cudaEvent_t e, cudaStream_t s);
 
 // ---------------------------------------------------------------- FP64 dense kernels (dense64.cu)
-int gemm64(cudaStream_t s, const Gemm64& g);
+int gemm64(cudaStream_t s, const Gemm64& g, int ctas_per_sm = 2);
 int gemm_exec(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
 
 // Recursive Cholesky + inverse of `batch` lower n x n matrices (strides sA, sX;
@@ -225,7 +241,12 @@ int dot_batch64(cudaStream_t s, const double* x, const double* y, long long len,
 size_t ozaki_workspace_bytes(int M, int N, int K, int slices);
 // same contract as gemm64 (any batch); ws holds batch x ozaki_workspace_bytes;
 // slices = 5 (35-bit digits) or 7 (49-bit digits)
-int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err, int slices, long long epi_wait = 0);
+// tile: 0 (128 x 96, 2 stages) or 1 (128 x 64, 3 stages) for 5 slices; 7 slices
+// use 128 x 64, 2 stages.  occupancy: waves of the persistent grid below
+// which the K dimension is split.
+int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err, int slices, long long epi_wait = 0,
+               int tile = 0, int occupancy = 1);
+int ozaki_tiles_for(int slices, int* out, int cap);
 int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
 // true when gemm_exec sends g to the split-precision path, whose operands are
 // read completely (digit split) before C is written: C may then alias A or B
@@ -241,6 +262,14 @@ int selinv_impl(bta_ctx_t ctx, int m0, int count, cudaStream_t s);
 // assemble matrices m0.. (kind = m / batch, parameters of slot m % batch at
 // params + slot * BTA_PSTRIDE)
 int assemble_impl(bta_ctx_t ctx, bta_model_t m, const double* params, int m0, int count, cudaStream_t s);
+// The observation terms A^T D A of Q_c with a weight per observation and slot
+// (layouts of bta_model_s::gram / arrow / tipgram, one copy per slot).
+struct ObsWeights {
+    const double* gram;  const double* arrow;  const double* tip;
+    long long gram_stride, arrow_stride, tip_stride;
+};
+int assemble_weighted_impl(bta_ctx_t ctx, bta_model_t m, const double* params, int m0, int count, cudaStream_t s,
+                           const ObsWeights& w);
 // theta (count x dim_theta) -> parameter slots (count x BTA_PSTRIDE)
 int theta_to_params_impl(bta_model_t m, const double* theta, int count, double* params, cudaStream_t s);
 int ensure_sigma(bta_ctx_t ctx);

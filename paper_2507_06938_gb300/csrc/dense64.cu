@@ -473,7 +473,7 @@ static int gemm64_thin(cudaStream_t s, const Gemm64& g) {
     return BTA_OK;
 }
 
-int gemm64(cudaStream_t s, const Gemm64& g) {
+int gemm64(cudaStream_t s, const Gemm64& g, int ctas_per_sm) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return BTA_OK;
     if (g.M <= 16 && g.N >= TH_TN) return gemm64_thin(s, g);
     if (g.K <= 8 && g.M > 32 && g.N > 32) {
@@ -487,10 +487,10 @@ int gemm64(cudaStream_t s, const Gemm64& g) {
         return BTA_OK;
     }
     // The FP64 pipe of one SM is slow (2 DFMA per clock), so every product is
-    // spread over about two CTAs per SM: pick the largest micro-tile that
-    // still reaches that with a K split of whole 16-wide slices, else the
-    // smallest tile with the largest split.
-    const long long want = 2LL * 152;
+    // spread over about `ctas_per_sm` (default two, autotuned) CTAs per SM:
+    // pick the largest micro-tile that still reaches that with a K split of
+    // whole 16-wide slices, else the smallest tile with the largest split.
+    const long long want = (long long)std::max(1, ctas_per_sm) * 152;
     int MI = 1, NJ = 1, ksplit = 1;
     const int kslices = std::max(1, (g.K + BK - 1) / BK);
     for (int sz = 4; sz >= 1; sz /= 2) {
@@ -527,7 +527,8 @@ int gemm64(cudaStream_t s, const Gemm64& g) {
 }
 
 int gemm_exec(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
-    if (!ex || !ex->fn) return gemm64(s, g);
+    if (!ex) return gemm64(s, g);
+    if (!ex->fn) return gemm64(s, g, ex->fp64_ctas);
     return ex->fn(ex, s, g);
 }
 

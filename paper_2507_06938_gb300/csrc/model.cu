@@ -128,6 +128,8 @@ extern "C" int bta_model_create(const bta_model_desc* d, bta_model_t* out) {
     std::vector<double> tip((size_t)nv * nr * nr, 0.0);
     std::vector<double> aty((size_t)N, 0.0);
     std::vector<double> stats(2 * nv, 0.0);
+    std::vector<int> o_tv(m), o_s(3 * (size_t)m), o_gpos(9 * (size_t)m);
+    std::vector<double> o_w(3 * (size_t)m), o_X((size_t)m * nr), o_y(m);
     for (int k = 0; k < m; ++k) {
         const int v = d->obs_var[k], t = d->obs_time[k], tr = d->obs_tri[k];
         if (v < 0 || v >= nv || t < 0 || t >= nt || tr < 0 || tr >= d->n_tri) return BTA_ERR_ARG;
@@ -153,7 +155,15 @@ extern "C" int bta_model_create(const bta_model_desc* d, bta_model_t* out) {
                 int pos = find_pos(pat.rowptr, pat.col, s[q], s[r]);
                 if (pos < 0) return BTA_ERR_ARG;   // cannot happen: triangle edges are in G
                 gram[gbase + pos] += w[q] * w[r];
+                o_gpos[9 * (size_t)k + 3 * q + r] = (int)(gbase + pos);
             }
+        o_tv[k] = t * nv + v;
+        o_y[k] = yk;
+        for (int q = 0; q < 3; ++q) {
+            o_s[3 * (size_t)k + q] = s[q];
+            o_w[3 * (size_t)k + q] = w[q];
+        }
+        for (int r = 0; r < nr; ++r) o_X[(size_t)k * nr + r] = d->X[(size_t)k * nr + r];
         for (int r = 0; r < nr; ++r) {
             const double xr = d->X[(size_t)k * nr + r];
             for (int q = 0; q < 3; ++q)
@@ -187,6 +197,12 @@ extern "C" int bta_model_create(const bta_model_desc* d, bta_model_t* out) {
     if (rc == BTA_OK) rc = upload(&M->aty, aty);
     if (rc == BTA_OK) rc = upload(&M->theta0, th0);
     if (rc == BTA_OK) rc = upload(&M->var_stats, stats);
+    if (rc == BTA_OK) rc = upload(&M->obs_tv, o_tv);
+    if (rc == BTA_OK) rc = upload(&M->obs_s, o_s);
+    if (rc == BTA_OK) rc = upload(&M->obs_w, o_w);
+    if (rc == BTA_OK) rc = upload(&M->obs_gpos, o_gpos);
+    if (rc == BTA_OK) rc = upload(&M->obs_X, o_X);
+    if (rc == BTA_OK) rc = upload(&M->obs_y, o_y);
     if (rc != BTA_OK) {
         bta_model_destroy(M);
         return rc;
@@ -198,7 +214,8 @@ extern "C" int bta_model_create(const bta_model_desc* d, bta_model_t* out) {
 extern "C" int bta_model_destroy(bta_model_t M) {
     if (!M) return BTA_OK;
     void* ptrs[] = {M->rowptr, M->col, M->cval, M->gval, M->kval, M->gram, M->arrow,
-                    M->tipgram, M->aty, M->theta0, M->var_stats};
+                    M->tipgram, M->aty, M->theta0, M->var_stats, M->obs_tv, M->obs_s,
+                    M->obs_w, M->obs_gpos, M->obs_X, M->obs_y};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete M;

@@ -70,7 +70,6 @@ namespace oz {
 constexpr int TM = 128, TK = 32;          // output tile rows; K block (64-byte rows)
 constexpr int ROW_BYTES = TK * 2;         // one digit row of a K block; the swizzle span
 static_assert(ROW_BYTES == 32 || ROW_BYTES == 64 || ROW_BYTES == 128, "K block of 16, 32 or 64");
-constexpr int STAGES = 2;
 constexpr int KB_PER_CHUNK = 512 / TK;    // exactness bound of the levels drained every chunk
 constexpr int EPI_WARPS = 16;             // 4 per TMEM lane quarter
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
@@ -89,12 +88,11 @@ constexpr int INT_MAX_CHUNKS = 16;        // S = 7: chunks per work unit (64-bit
 // is first written by them at the start of a chunk.
 struct Piece { int p, q0, n, kind; };
 
-template <int S> struct Cfg;
+template <int S, int TN> struct Cfg;
 
-// 35-bit digits: 5 levels x 96 columns = 480 of the 512 TMEM columns.
-// Group A = levels 0, 1, 3, 4 (every second chunk), group B = level 2.
-template <> struct Cfg<5> {
-    static constexpr int TN = 96;
+// 35-bit digits, 128 x 96 tiles: 5 levels x 96 columns = 480 of the 512 TMEM
+// columns.  Group A = levels 0, 1, 3, 4 (every second chunk), group B = level 2.
+template <> struct Cfg<5, 96> {
     static constexpr unsigned GROUP_A = 0x1Bu, GROUP_B = 0x04u;
     static constexpr int PIECES = 9;
     static constexpr int CBUF_BUFS = 2;    // 8-column staging buffers of the bulk reduce-add, per warp
@@ -106,11 +104,24 @@ template <> struct Cfg<5> {
     }
 };
 
-// 49-bit digits: 7 levels x 64 columns = 448 TMEM columns.  Group A = levels
-// 0, 1 (every second chunk), group B = levels 2..6 (every chunk); 28 pairs as
-// 11 MMAs of N <= 256.
-template <> struct Cfg<7> {
-    static constexpr int TN = 64;
+// 35-bit digits, 128 x 64 tiles (room for a third TMA stage): 320 TMEM
+// columns, the same level groups, 15 pairs as 7 MMAs of N <= 256.
+template <> struct Cfg<5, 64> {
+    static constexpr unsigned GROUP_A = 0x1Bu, GROUP_B = 0x04u;
+    static constexpr int PIECES = 7;
+    static constexpr int CBUF_BUFS = 1;
+    static constexpr bool INT_ACC = false;
+    __host__ __device__ static constexpr Piece piece(int i) {
+        constexpr Piece t[PIECES] = {{0, 0, 2, 1}, {0, 2, 1, 2}, {0, 3, 2, 1}, {1, 0, 4, 0},
+                                     {2, 0, 3, 0}, {3, 0, 2, 0}, {4, 0, 1, 0}};
+        return t[i];
+    }
+};
+
+// 49-bit digits, 128 x 64 tiles: 7 levels x 64 columns = 448 TMEM columns.
+// Group A = levels 0, 1 (every second chunk), group B = levels 2..6 (every
+// chunk); 28 pairs as 11 MMAs of N <= 256.
+template <> struct Cfg<7, 64> {
     static constexpr unsigned GROUP_A = 0x03u, GROUP_B = 0x7Cu;
     static constexpr int PIECES = 11;
     static constexpr int CBUF_BUFS = 1;
@@ -123,13 +134,14 @@ template <> struct Cfg<7> {
     }
 };
 
-template <int S> struct Geo {
-    static constexpr int TN = Cfg<S>::TN;
+template <int S, int TN_, int STG> struct Geo {
+    static constexpr int TN = TN_;
+    static constexpr int STAGES = STG;
     static constexpr int EPI_COLS = TN / (EPI_WARPS / 4);   // columns per epilogue thread
     static constexpr uint32_t B_SLICE_BYTES = TN * TK * 2;
     static constexpr uint32_t STAGE_BYTES = S * (A_SLICE_BYTES + B_SLICE_BYTES);
     // per epilogue warp, 32-row x 8-column FP64 buffers for the bulk reduce-add of C
-    static constexpr uint32_t CBUF_BYTES = Cfg<S>::CBUF_BUFS * 8 * 32 * 8;
+    static constexpr uint32_t CBUF_BYTES = Cfg<S, TN>::CBUF_BUFS * 8 * 32 * 8;
     static constexpr size_t SMEM_BYTES =
         1024 /*alignment slack*/ + STAGES * STAGE_BYTES + EPI_WARPS * CBUF_BYTES + 256;
     static_assert(SMEM_BYTES <= 232448, "shared memory of one CTA");
@@ -137,6 +149,13 @@ template <int S> struct Geo {
     static_assert(EPI_COLS % 8 == 0, "epilogue columns in groups of 8");
     static_assert(TM % TN == 0 || TN == 96, "row padding of aliased operands");
 };
+
+// The launch configurations of the split product: (slices, tile width,
+// TMA stages).  tile 0 is the default of each slice count; the autotuner may
+// pick another one of the same slice count.
+struct TileCfg { int S, TN, STG; };
+constexpr TileCfg kTiles[] = {{5, 96, 2}, {5, 64, 3}, {7, 64, 2}};
+constexpr int NUM_TILES = 3;
 
 struct Args {
     int M, N;            // output extent
@@ -393,13 +412,12 @@ __device__ __forceinline__ void drain_level_int(uint32_t taddr, int lv, long lon
     }
 }
 
-template <int S>
+template <int S, int TN, int STAGES>
 __global__ void __launch_bounds__(THREADS, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const __grid_constant__ Args a) {
-    using CF = Cfg<S>;
-    using G = Geo<S>;
-    constexpr int TN = CF::TN;
+    using CF = Cfg<S, TN>;
+    using G = Geo<S, TN, STAGES>;
     constexpr int EPI_COLS = G::EPI_COLS;
     constexpr uint32_t STAGE_BYTES = G::STAGE_BYTES;
     constexpr uint32_t B_SLICE_BYTES = G::B_SLICE_BYTES;
@@ -959,17 +977,18 @@ int split_launch(cudaStream_t s, const SplitJob& ja, const SplitJob& jb, bool sa
     }
 }
 
-inline int tile_n(int slices) { return slices == 7 ? Cfg<7>::TN : Cfg<5>::TN; }
-
 size_t workspace_bytes(int M, int N, int K, int S) {
-    const size_t Mp = (size_t)round_up(M, TM), Np = (size_t)round_up(N, tile_n(S));
+    // rows of op(B) padded to the widest tile of this slice count
+    int tn = 0;
+    for (const TileCfg& t : kTiles)
+        if (t.S == S) tn = std::max(tn, t.TN);
+    const size_t Mp = (size_t)round_up(M, TM), Np = (size_t)round_up(N, tn);
     const size_t Kp = (size_t)std::max(PAD_K, round_up(K, PAD_K));
     return (size_t)S * (Mp + Np) * Kp * 2 + (Mp + Np) * sizeof(int) + 4 * 256;
 }
 
-template <int S>
-int gemm_s(cudaStream_t s, const Gemm64& g, void* ws, int* err, long long epi_wait) {
-    constexpr int TN = Cfg<S>::TN;
+template <int S, int TN, int STG>
+int gemm_s(cudaStream_t s, const Gemm64& g, void* ws, int* err, long long epi_wait, int occupancy) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return BTA_OK;
     if (g.M > MAX_MT * TM) return BTA_ERR_ARG;
     const int nb = g.batch;
@@ -1017,10 +1036,13 @@ int gemm_s(cudaStream_t s, const Gemm64& g, void* ws, int* err, long long epi_wa
     const long long base = (long long)nb * a.tiles;
     const int sms = num_sms();
     const int nchunks = (a.kblocks + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
+    // a K split (atomic adds) only when the tiles cannot give `occupancy` waves
+    // of the persistent grid
     long long ksplit = 1;
-    if (base < sms) ksplit = std::min<long long>(nchunks, (sms + base - 1) / base);
+    const long long want = (long long)sms * std::max(1, occupancy);
+    if (base < want) ksplit = std::min<long long>(nchunks, (want + base - 1) / base);
     // the 64-bit fixed-point sums of S = 7 hold at most INT_MAX_CHUNKS chunks
-    if (Cfg<S>::INT_ACC) ksplit = std::max<long long>(ksplit, (nchunks + INT_MAX_CHUNKS - 1) / INT_MAX_CHUNKS);
+    if (Cfg<S, TN>::INT_ACC) ksplit = std::max<long long>(ksplit, (nchunks + INT_MAX_CHUNKS - 1) / INT_MAX_CHUNKS);
     if (base * ksplit > 0x7FFFFFFFLL) return BTA_ERR_ARG;
     a.ksplit = (int)ksplit;
     a.units = (int)(base * ksplit);
@@ -1046,9 +1068,10 @@ int gemm_s(cudaStream_t s, const Gemm64& g, void* ws, int* err, long long epi_wa
     a.shB = g.shB;
     a.err = err;
     a.epi_wait = epi_wait > 0 ? epi_wait : WAIT_LIMIT_CYCLES;
-    BTA_TRY(ensure_dyn_smem((const void*)ozaki_gemm_kernel<S>, (int)Geo<S>::SMEM_BYTES));
+    using G = Geo<S, TN, STG>;
+    BTA_TRY(ensure_dyn_smem((const void*)ozaki_gemm_kernel<S, TN, STG>, (int)G::SMEM_BYTES));
     const int grid = (int)std::min<long long>(a.units, sms);
-    ozaki_gemm_kernel<S><<<grid, THREADS, Geo<S>::SMEM_BYTES, s>>>(mA, mB, a);
+    ozaki_gemm_kernel<S, TN, STG><<<grid, THREADS, G::SMEM_BYTES, s>>>(mA, mB, a);
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }
@@ -1066,10 +1089,24 @@ int ozaki_max_rows() { return oz::MAX_MT * oz::TM; }
 // with 5 or 7 digit slices.  ws: device workspace of batch *
 // ozaki_workspace_bytes(M, N, K, slices); err: device int; epi_wait: wait
 // limit (cycles) of the epilogue's accumulator hand-off, <= 0 for the default.
-int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err, int slices, long long epi_wait) {
-    if (slices == 7) return oz::gemm_s<7>(s, g, ws, err, epi_wait);
-    if (slices == 5) return oz::gemm_s<5>(s, g, ws, err, epi_wait);
+int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err, int slices, long long epi_wait, int tile,
+               int occupancy) {
+    using namespace oz;
+    if (slices == 7) return gemm_s<7, 64, 2>(s, g, ws, err, epi_wait, occupancy);
+    if (slices == 5)
+        return tile == 1 ? gemm_s<5, 64, 3>(s, g, ws, err, epi_wait, occupancy)
+                         : gemm_s<5, 96, 2>(s, g, ws, err, epi_wait, occupancy);
     return BTA_ERR_ARG;
+}
+
+// Tile configurations the autotuner may choose for a slice count: writes up
+// to `cap` tile indices (index into the configuration table) and returns the
+// count; ozaki_tile_desc names one.
+int ozaki_tiles_for(int slices, int* out, int cap) {
+    int n = 0;
+    for (int i = 0; i < oz::NUM_TILES && n < cap; ++i)
+        if (oz::kTiles[i].S == slices) out[n++] = (slices == 5 ? i : 0);
+    return n;
 }
 
 // GEMM executor of the mixed path: products whose output is at least
@@ -1089,7 +1126,7 @@ int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
         // the accumulators, so that a test can make it run out
         long long epi_wait = ex->epi_wait;
         if (const char* e = std::getenv("BTA_OZ_EPI_WAIT")) epi_wait = std::atoll(e);
-        return ozaki_gemm(s, g, ex->ws, ex->err, ex->slices, epi_wait);
+        return ozaki_gemm(s, g, ex->ws, ex->err, ex->slices, epi_wait, ex->tile, ex->occupancy);
     }
     // below the tensor-core threshold: square-ish products of the diagonal
     // recursion in double-float on the FP32 pipe, thin or tiny ones in FP64

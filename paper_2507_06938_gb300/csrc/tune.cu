@@ -1,13 +1,21 @@
-// Autotuning of the launch shapes of the diagonal-block factorisation, the
-// latency-bound chain of the BTA Cholesky (one batched Cholesky + inverse of
-// a b x b block per time step).  For the context's shape, precision and
-// batch, every candidate setting is timed on the context's own storage and
-// the fastest one is kept:
-//   FP64:   the leaf order of the recursive Cholesky + inverse (16, 32, 64)
-//   mixed:  the double-float leaf order (32, 64, 128) x the smallest product
-//           dimension sent to the tensor cores (128, 256)
+// Autotuning of the launch shapes of the BTA factorisation and selected
+// inversion for a context's block order, precision and batch.  Every
+// candidate is timed on the context's own storage and the fastest is kept:
+//   1. the diagonal-block chain, the latency-bound critical path of the block
+//      Cholesky (one batched Cholesky + inverse of a b x b block per step):
+//        FP64:  the leaf order of the recursive Cholesky + inverse (16, 32, 64)
+//        mixed: the double-float leaf order (32, 64, 128) x the smallest
+//               product dimension sent to the tensor cores (128, 256)
+//   2. the b x b x b products (Schur updates, selected inversion), timed on
+//      the lower-output update D -= L L^T of every matrix:
+//        FP64:  the CTAs per SM the DFMA GEMM aims for through its K split
+//               (1, 2, 4), which sets its micro-tile and split
+//        mixed: the tile configuration of the split product (for 35-bit
+//               digits 128 x 96 with 2 TMA stages or 128 x 64 with 3; for
+//               49-bit digits 128 x 64 with 2) x the waves of the persistent
+//               grid below which it splits K (1, 2)
 // The timed matrices are synthetic SPD blocks written into the first
-// diagonal block of every matrix of the context (its contents are lost).
+// diagonal blocks of every matrix of the context (their contents are lost).
 
 #include <algorithm>
 #include <vector>
@@ -86,8 +94,6 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
             pick = c;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     ctx->leaf = pick.leaf;
     ctx->exec.df_leaf = pick.df_leaf;
     ctx->exec.min_dim = pick.min_dim;
@@ -95,10 +101,70 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
         ctx->fork->ex2.df_leaf = pick.df_leaf;
         ctx->fork->ex2.min_dim = pick.min_dim;
     }
+
+    // ---- 2. the b x b x b products: D_0 -= X X^T (lower) on every matrix, with
+    // X the synthetic block of Q and D_0 of L as the output
+    struct PCand {
+        int tile, occ, ctas;
+    };
+    std::vector<PCand> pc;
+    if (ctx->precision != BTA_FP64) {
+        int tiles[4];
+        const int nt = ozaki_tiles_for(ctx->exec.slices, tiles, 4);
+        for (int t = 0; t < nt; ++t)
+            for (int occ : {1, 2}) pc.push_back({tiles[t], occ, ctx->exec.fp64_ctas});
+    } else {
+        for (int c : {1, 2, 4}) pc.push_back({ctx->exec.tile, ctx->exec.occupancy, c});
+    }
+    Gemm64 g{};
+    g.M = b; g.N = b; g.K = b;
+    g.A = ctx->Q.D; g.lda = b;
+    g.B = ctx->Q.D; g.ldb = b; g.tb = 1;
+    g.Cin = ctx->L.D; g.ldci = b; g.beta = 1.0;
+    g.C = ctx->L.D; g.ldc = b; g.alpha = -1.0; g.lowerC = 1;
+    g.batch = nm; g.sA = ctx->Q.sD; g.sB = ctx->Q.sD; g.sCi = ctx->L.sD; g.sC = ctx->L.sD;
+    auto prun = [&](const PCand& c) -> int {
+        ctx->exec.tile = c.tile;
+        ctx->exec.occupancy = c.occ;
+        ctx->exec.fp64_ctas = c.ctas;
+        return gemm_exec(&ctx->exec, s, g);
+    };
+    float pbest = -1.f;
+    PCand ppick = pc[0];
+    for (const PCand& c : pc) {
+        if (rc != BTA_OK) break;
+        if ((rc = prun(c)) != BTA_OK) break;
+        if (cudaEventRecord(e0, s) != cudaSuccess) { rc = BTA_ERR_CUDA; break; }
+        for (int r = 0; r < reps && rc == BTA_OK; ++r) rc = prun(c);
+        if (rc != BTA_OK) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = BTA_ERR_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (pbest < 0.f || ms < pbest) {
+            pbest = ms;
+            ppick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->exec.tile = ppick.tile;
+    ctx->exec.occupancy = ppick.occ;
+    ctx->exec.fp64_ctas = ppick.ctas;
+    if (ctx->fork) {
+        ctx->fork->ex2.tile = ppick.tile;
+        ctx->fork->ex2.occupancy = ppick.occ;
+        ctx->fork->ex2.fp64_ctas = ppick.ctas;
+    }
     if (rc != BTA_OK) return rc;
     BTA_TRY(bta_sync(ctx));
     chosen[0] = pick.leaf;
     chosen[1] = pick.df_leaf;
     chosen[2] = pick.min_dim;
+    chosen[3] = ppick.tile;
+    chosen[4] = ppick.occ;
+    chosen[5] = ppick.ctas;
     return BTA_OK;
 }

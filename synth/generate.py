@@ -134,7 +134,7 @@ def _true_field(v: int, xy: np.ndarray, t: np.ndarray, nt: int) -> np.ndarray:
 def make_problem(name: str, *, nv: int, mesh, nt: int, nr: int, seed: int,
                  m_total: int | None = None, per_step: int | None = None,
                  shared_sites: bool = False, theta0=None,
-                 lam_range: float = 0.5) -> Problem:
+                 lam_range: float = 0.5, likelihood: str = "gaussian") -> Problem:
     """Build a seeded problem.
 
     mesh: ("grid", gx[, gy]) or ("delaunay", npts).
@@ -143,6 +143,9 @@ def make_problem(name: str, *, nv: int, mesh, nt: int, nr: int, seed: int,
     time of each observation is uniform over the nt steps.
     Coregional style (shared_sites=True): each time step has ``per_step``
     uniform sites, observed once per response variable with shared covariates.
+    likelihood "gaussian": y = signal + noise of precision exp(theta0 noise
+    entry); "poisson": counts y ~ Poisson(exp(eta)) with the log-rate
+    eta = 0.5 signal + 0.2 sum of the covariates (data only).
     """
     rng = np.random.default_rng(seed)
     kind = mesh[0]
@@ -199,8 +202,14 @@ def make_problem(name: str, *, nv: int, mesh, nt: int, nr: int, seed: int,
     y = np.zeros(obs_var.shape[0])
     for v in range(nv):
         sel = obs_var == v
-        y[sel] = (_true_field(v, obs_xy[sel], obs_time[sel], nt) + X[sel].sum(axis=1)
-                  + rng.standard_normal(int(sel.sum())) / math.sqrt(noise_prec[v]))
+        signal = _true_field(v, obs_xy[sel], obs_time[sel], nt)
+        if likelihood == "gaussian":
+            y[sel] = (signal + X[sel].sum(axis=1)
+                      + rng.standard_normal(int(sel.sum())) / math.sqrt(noise_prec[v]))
+        elif likelihood == "poisson":
+            y[sel] = rng.poisson(np.exp(0.5 * signal + 0.2 * X[sel].sum(axis=1)))
+        else:
+            raise ValueError(likelihood)
 
     return Problem(name=name, nv=nv, ns=ns, nt=nt, nr=nr,
                    nodes=np.ascontiguousarray(nodes, dtype=np.float64),
@@ -229,6 +238,9 @@ CONFIGS = {
     # trivariate coregional, b=3072, nt=48, a=6, N=147,462; 300 sites per step
     "c3": dict(nv=3, mesh=("grid", 32), nt=48, nr=2, seed=3, per_step=300,
                shared_sites=True),
+    # c3 with 2 time steps: one Schur update of b=3072 blocks per factorisation,
+    # small enough on the device for multi-pass kernel captures
+    "c3p": dict(nv=3, mesh=("grid", 32), nt=2, nr=2, seed=3, per_step=300, shared_sites=True),
     # trivariate coregional on a 2000-node Delaunay mesh, b=6000, N=288,006
     "c5": dict(nv=3, mesh=("delaunay", 2000), nt=48, nr=2, seed=5, per_step=1000,
                shared_sites=True),
@@ -246,6 +258,15 @@ CONFIGS = {
                          shared_sites=True),
     "t_uni_nt1": dict(nv=1, mesh=("grid", 7), nt=1, nr=1, seed=16, m_total=30),
     "t_uni_mid": dict(nv=1, mesh=("grid", 17), nt=12, nr=2, seed=17, per_step=200),
+    # count data (Poisson likelihood, log link) for the Laplace approximation
+    "t_pois": dict(nv=1, mesh=("grid", 6), nt=5, nr=2, seed=21, m_total=90, likelihood="poisson"),
+    "t_pois_coreg3": dict(nv=3, mesh=("grid", 5), nt=4, nr=2, seed=22, per_step=12, shared_sites=True,
+                          likelihood="poisson"),
+    "t_pois_mid": dict(nv=1, mesh=("grid", 17), nt=12, nr=2, seed=23, per_step=200, likelihood="poisson"),
+    "t_pois_coreg3_mid": dict(nv=3, mesh=("grid", 12), nt=10, nr=2, seed=24, per_step=60, shared_sites=True,
+                              likelihood="poisson"),
+    # univariate count model at the working size (b = 1024, nt = 64)
+    "c2pois": dict(nv=1, mesh=("grid", 32), nt=64, nr=4, seed=25, per_step=1024, likelihood="poisson"),
     "t_coreg3_mid": dict(nv=3, mesh=("grid", 12), nt=10, nr=2, seed=18, per_step=60,
                          shared_sites=True),
 }

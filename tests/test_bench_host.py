@@ -67,5 +67,6 @@ def test_errors_against_reference():
     assert abs(e["f_rel_to_logdets"] - 5e-4 / 5e5) < 1e-15
     assert e["solve_residual"] == 2e-12
     assert abs(e["sigma_block_rel_max"] - 0.5e-8) < 1e-15
+    assert list(e["sigma_block_rel"]) == ["Q_p D0"]
     # gradient error relative to max(|g_k|, 1e-3 |g|_inf): the third entry's scale is 2e-3
     assert abs(e["grad_rel_max"] - 1e-6 / 2e-3) < 1e-12

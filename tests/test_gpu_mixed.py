@@ -113,7 +113,7 @@ def test_double_float_leaf(b):
     assert e.value.info <= b // 2
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_autotune_keeps_results_exact(precision):
     """The autotuner only changes launch shapes: after it runs, f_obj and the
     conditional mean still match the oracle at the bounds of the precision."""
@@ -122,11 +122,12 @@ def test_autotune_keeps_results_exact(precision):
     from oracle import fobj as ofobj
     p = problem("t_uni_mid")
     run = GpuRun(p, precision=precision, batch=2)
-    leaf, df_leaf, tmin = run.ctx.autotune(reps=1)
+    leaf, df_leaf, tmin, tile, waves, ctas = run.ctx.autotune(reps=1)
     if precision == 0:
-        assert leaf in (16, 32, 64)
+        assert leaf in (16, 32, 64) and ctas in (1, 2, 4)
     else:
         assert df_leaf in (32, 64, 128) and tmin in (128, 256)
+        assert tile in ((0, 1) if precision == 1 else (0,)) and waves in (1, 2)
     th = np.stack([p.theta0, p.theta0 + 1e-3])
     f = torch.zeros(2, dtype=torch.float64, device="cuda")
     mu = torch.zeros((2, p.N), dtype=torch.float64, device="cuda")
@@ -134,6 +135,35 @@ def test_autotune_keeps_results_exact(precision):
     run.ctx.sync()
     for j in range(2):
         terms = ofobj.f_obj_terms(p, th[j])
-        tol = 1e-9 * abs(terms["f"]) if precision == 0 else 1e-8 * (abs(terms["logdet_p"]) + abs(terms["logdet_c"]))
+        tol = 1e-9 * abs(terms["f"]) if precision != 1 else 1e-8 * (abs(terms["logdet_p"]) + abs(terms["logdet_c"]))
         assert abs(f[j].item() - terms["f"]) <= tol
         assert rel_max(mu[j].cpu().numpy(), terms["mu"]) < 1e-8
+
+
+@pytest.mark.parametrize("name", ["t_coreg3_mid", "c2s"])
+def test_mixed_tile_128x64_three_stages(name, monkeypatch):
+    """The second 35-bit tile configuration of the split product (128 x 64
+    tiles, 3 TMA stages), which the autotuner may choose, at the same bounds
+    as the default one."""
+    import torch
+    from paper_2507_06938_gb300 import bta
+    monkeypatch.setenv("BTA_OZ_MIN", "128")
+    monkeypatch.setenv("BTA_OZ_TILE", "1")
+    p = problem(name)
+    prm = omodel.theta_to_params(p.theta0, p.nv)
+    built = omodel.build(p, prm)
+    run = GpuRun(p, precision=bta.BTA_MIXED)
+    Q = built.Qc
+    Lo = obta.factor(obta.blocks_from_sparse(Q, p.nt, p.b, p.a))
+    run.assemble(prm, bta.BTA_QC)
+    run.ctx.factor(bta.BTA_QC)
+    ld = torch.zeros(1, dtype=torch.float64, device="cuda")
+    run.ctx.logdet(bta.BTA_QC, ld)
+    run.ctx.selinv(bta.BTA_QC)
+    run.ctx.sync()
+    ref = obta.logdet(Lo)
+    assert abs(ld.item() - ref) / abs(ref) <= 1e-8
+    S = blocks_of(run.ctx, bta.BTA_QC, bta.BTA_STORE_SIGMA, p.nt, p.b, p.a)
+    So = obta.selinv(Lo)
+    for k in ("D", "B", "R", "T"):
+        assert rel_max(S[k], So[k]) <= 5e-5, k
