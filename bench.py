@@ -97,6 +97,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the host-buffer (end-to-end) timing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--time-partitions", type=int, default=1,
+                    help="P > 1: factor / solve / selinv by time-domain partitioning into P partitions")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the FP64 comparison run of the mixed-precision bench")
     return ap.parse_args()
@@ -397,6 +399,8 @@ def measure(args, precision_name, warmup, steps, e2e_steps, dist, rank, world, l
     stream = torch.cuda.Stream()
     model = bta.BtaModel(p)
     ctx = bta.BtaContext(p.nt, p.b, p.a, precision, stream, B)
+    if args.time_partitions > 1:
+        ctx.set_time_partitions(args.time_partitions)
     tuned = None if args.no_autotune else ctx.autotune(reps=2)
     nsteps = warmup + steps
     if fixed_theta is not None:
@@ -551,6 +555,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": workload(p, B), "name": args.config, "precision": args.precision, "theta_points": B,
+                   "time_partitions": args.time_partitions,
                    "l2": l2_note(p, B),
                    "parallelism": f"replicas x{world} (independent theta points per GPU)"},
         "tflops": r["tflops"], "tflops_unit": "nominal (2 F_fact + 2 F_selinv) per f_obj evaluation / time",

@@ -178,6 +178,24 @@ int bta_theta_to_params(bta_ctx_t ctx, bta_model_t model, const double* theta_de
  * A non-positive pivot records BTA_ERR_NOT_PD in the status word.
  */
 int bta_factor(bta_ctx_t ctx, int which);
+/*
+ * bta_set_time_partitions -- factor, solve and selectively invert this
+ * context's matrices by time-domain partitioning (Sections IV-C, IV-D.3;
+ * the nested dissection over time of the distributed solver, run here as one
+ * batch on one GPU): P - 1 separator blocks cut the n time blocks into P
+ * partitions whose interiors are eliminated together, then the separators
+ * form a reduced BTA system of P - 1 blocks.  The sequential chain shrinks
+ * from n to about n/P + P steps at the price of extra fill products, which
+ * pays for small blocks.  P = 1 restores the sequential recurrences.
+ * Requires floor((n + 1) / P) >= 2.  Allocates two extra block arrays of
+ * n b^2 per matrix (fill rows of the factor and of the selected inverse) and
+ * scratch; invalidates existing factors and any captured f_obj graph.
+ * Results agree with the sequential path up to rounding; a non-positive
+ * pivot is still reported as BTA_ERR_NOT_PD, but the row given by
+ * bta_last_info is then only the row inside its block.  Synchronises.
+ */
+int bta_set_time_partitions(bta_ctx_t ctx, int P);
+
 /* bta_factor_batch -- bta_factor of every slot's matrix of kind BTA_QP or
  * BTA_QC in one pass (all matrices in the same launches). */
 int bta_factor_batch(bta_ctx_t ctx, int kind);

@@ -93,6 +93,7 @@ def lib():
                                      C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]),
         "bta_fobj_residual": (ip, [vp, vp]),
         "bta_fobj_laplace": (ip, [vp, vp, vp, ip, ip, ip, vp, vp, vp]),
+        "bta_set_time_partitions": (ip, [vp, ip]),
         "bta_fobj_grad_host": (ip, [vp, vp, vp, ip, vp, vp, vp]),
         "bta_fp64_peak": (ip, [ip, C.POINTER(dp)]),
         "bta_flops_factor": (dp, [ip, ip, ip]),
@@ -115,7 +116,8 @@ def exported_symbols():
             "bta_launch_count", "bta_profile", "bta_profile_read", "bta_chol_inv_noalloc",
             "bta_create_batched", "bta_batch_size", "bta_factor_batch", "bta_selinv_batch",
             "bta_last_error_matrix", "bta_fobj_grad", "bta_autotune", "bta_fobj_eval_multi",
-            "bta_fobj_residual", "bta_fp64_peak", "bta_fobj_grad_host", "bta_fobj_laplace"]
+            "bta_fobj_residual", "bta_fp64_peak", "bta_fobj_grad_host", "bta_fobj_laplace",
+            "bta_set_time_partitions"]
 
 
 def _check(code: int, where: str):
@@ -246,6 +248,11 @@ class BtaContext:
     def selinv(self, which: int):
         _check(lib().bta_selinv(self.handle, which), "bta_selinv")
 
+    def set_time_partitions(self, P: int):
+        """bta_set_time_partitions: P > 1 runs factor/solve/selinv by time-domain
+        partitioning (P partitions eliminated together, then the separators)."""
+        _check(lib().bta_set_time_partitions(self.handle, int(P)), "bta_set_time_partitions")
+
     def factor_batch(self, kind: int):
         _check(lib().bta_factor_batch(self.handle, kind), "bta_factor_batch")
 
@@ -354,6 +361,10 @@ def bta_create(n, b, a, precision=BTA_FP64, stream=None) -> BtaContext:
 
 def bta_create_batched(n, b, a, precision=BTA_FP64, batch=1, stream=None) -> BtaContext:
     return BtaContext(n, b, a, precision, stream, batch)
+
+
+def bta_set_time_partitions(ctx: BtaContext, P: int):
+    ctx.set_time_partitions(P)
 
 
 def bta_factor_batch(ctx: BtaContext, kind: int):

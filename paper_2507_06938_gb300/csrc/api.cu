@@ -211,6 +211,7 @@ extern "C" int bta_destroy(bta_ctx_t c) {
         delete c->fork;
         c->fork = nullptr;
     }
+    ptime_free(c);
     store_free(c->Q);
     store_free(c->L);
     store_free(c->S);

@@ -173,6 +173,9 @@ struct bta_ctx_s {
     double* hs_grad = nullptr;     // batch x dim_theta
     double* hs_var = nullptr;      // batch x N
     int hs_dim = 0;
+    // parallel-in-time path (bta_set_time_partitions): P > 1 time partitions
+    int tparts = 1;
+    struct PTimeStore* pts = nullptr;
     // workspace of the Laplace evaluation (allocated on first use)
     double* lap = nullptr;         // per slot: obs weights, obs rhs terms, log-likelihood terms, x_new, params
     long long lap_slot = 0;        // doubles per slot
@@ -259,6 +262,11 @@ int logdet_impl(bta_ctx_t ctx, int m0, int count, double* out, cudaStream_t s);
 int solve_impl(bta_ctx_t ctx, int m0, int count, const double* r, double* x, cudaStream_t s);
 int matvec_impl(bta_ctx_t ctx, int m0, int count, const double* x, double* y, cudaStream_t s);
 int selinv_impl(bta_ctx_t ctx, int m0, int count, cudaStream_t s);
+// the same over P > 1 time partitions (ptime.cu), used when ctx->tparts > 1
+int pfactor_impl(bta_ctx_t ctx, int m0, int count, cudaStream_t s);
+int psolve_impl(bta_ctx_t ctx, int m0, int count, const double* r, double* x, cudaStream_t s);
+int pselinv_impl(bta_ctx_t ctx, int m0, int count, cudaStream_t s);
+void ptime_free(bta_ctx_t ctx);
 // assemble matrices m0.. (kind = m / batch, parameters of slot m % batch at
 // params + slot * BTA_PSTRIDE)
 int assemble_impl(bta_ctx_t ctx, bta_model_t m, const double* params, int m0, int count, cudaStream_t s);

@@ -17,6 +17,7 @@
 #include "common.cuh"
 
 int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
+    if (ctx->tparts > 1) return pfactor_impl(ctx, m0, cnt, s);
     const int n = ctx->n, b = ctx->b, a = ctx->a;
     const long long bb = (long long)b * b, ab = (long long)a * b;
     const BtaStore& Q = ctx->Q;

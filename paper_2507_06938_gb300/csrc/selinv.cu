@@ -20,6 +20,7 @@
 #include "common.cuh"
 
 int selinv_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
+    if (ctx->tparts > 1) return pselinv_impl(ctx, m0, cnt, s);
     const int n = ctx->n, b = ctx->b, a = ctx->a;
     const long long bb = (long long)b * b, ab = (long long)a * b;
     const BtaStore& L = ctx->L;

@@ -44,6 +44,7 @@ int axpby64(cudaStream_t s, long long len, double alpha, const double* x, double
 
 // r, x: cnt vectors N apart; scratch rows VEC_Z / VEC_TMP of the same matrices.
 int solve_impl(bta_ctx_t ctx, int m0, int cnt, const double* r, double* x, cudaStream_t s) {
+    if (ctx->tparts > 1) return psolve_impl(ctx, m0, cnt, r, x, s);
     const int n = ctx->n, b = ctx->b, a = ctx->a;
     const long long N = ctx->N, nb = (long long)n * b, bb = (long long)b * b;
     const BtaStore& L = ctx->L;
