@@ -119,6 +119,74 @@ class Objective:
         self.model.close()
 
 
+class DistributedObjective:
+    """An objective whose batched evaluations are split over the ranks of a
+    torch.distributed process group: the independent function evaluations
+    of Section IV-D.1 (the 2 dim + 1 stencil points of Eq. 10, the Hessian
+    columns), each rank on its own GPU.  Rank r evaluates rows r, r + W,
+    r + 2 W, ... of every batch through its local objective; the values (and
+    gradients) are then combined on the host by one all-reduce of a
+    zero-filled array in which every row is written by exactly one rank (the
+    sum is the gather of the paper's reduction, exact).  Every rank returns
+    the full result, so BFGS runs identically everywhere.  With gloo the
+    exchange is a host collective; the data path needs none."""
+
+    def __init__(self, local, group=None):
+        import torch.distributed as dist
+        self.local = local
+        self.dist = dist
+        self.group = group
+        self.rank = dist.get_rank(group)
+        self.world = dist.get_world_size(group)
+        self.problem = local.problem
+        self.dim = local.dim
+        self.gradient = local.gradient
+        self.h = local.h
+        self.n_eval = 0
+
+    def _mine(self, count: int) -> np.ndarray:
+        return np.arange(self.rank, count, self.world)
+
+    def _combine(self, full: np.ndarray) -> np.ndarray:
+        import torch
+        t = torch.as_tensor(full, dtype=torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM, group=self.group)
+        return t.numpy()
+
+    def values(self, thetas) -> np.ndarray:
+        th = np.atleast_2d(np.asarray(thetas, dtype=np.float64))
+        idx = self._mine(th.shape[0])
+        full = np.zeros(th.shape[0])
+        if idx.size:
+            full[idx] = self.local.values(th[idx])
+            self.n_eval += idx.size
+        return self._combine(full)
+
+    def grads(self, thetas):
+        th = np.atleast_2d(np.asarray(thetas, dtype=np.float64))
+        idx = self._mine(th.shape[0])
+        full = np.zeros((th.shape[0], 1 + th.shape[1]))
+        if idx.size:
+            f, g = self.local.grads(th[idx])
+            full[idx, 0] = f
+            full[idx, 1:] = g
+            self.n_eval += idx.size
+        out = self._combine(full)
+        return out[:, 0], out[:, 1:]
+
+    def value_grad(self, theta):
+        theta = np.asarray(theta, dtype=np.float64)
+        if self.gradient == "adjoint":
+            f, g = self.grads(theta[None, :])
+            return float(f[0]), g[0]
+        pts = stencil(theta, self.h)
+        f = self.values(pts)
+        return float(f[0]), fd_from_stencil(f, self.h)
+
+    def latent_marginals(self, theta):
+        return self.local.latent_marginals(theta)
+
+
 def stencil(theta, h: float) -> np.ndarray:
     """The 2 dim + 1 points of Eq. 10: theta, then theta + h e_i, theta - h e_i."""
     theta = np.asarray(theta, dtype=np.float64)
