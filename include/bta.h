@@ -182,17 +182,25 @@ int bta_factor(bta_ctx_t ctx, int which);
  * bta_set_time_partitions -- factor, solve and selectively invert this
  * context's matrices by time-domain partitioning (Sections IV-C, IV-D.3;
  * the nested dissection over time of the distributed solver, run here as one
- * batch on one GPU): P - 1 separator blocks cut the n time blocks into P
- * partitions whose interiors are eliminated together, then the separators
- * form a reduced BTA system of P - 1 blocks.  The sequential chain shrinks
- * from n to about n/P + P steps at the price of extra fill products, which
- * pays for small blocks.  P = 1 restores the sequential recurrences.
- * Requires floor((n + 1) / P) >= 2.  Allocates two extra block arrays of
- * n b^2 per matrix (fill rows of the factor and of the selected inverse) and
- * scratch; invalidates existing factors and any captured f_obj graph.
- * Results agree with the sequential path up to rounding; a non-positive
- * pivot is still reported as BTA_ERR_NOT_PD, but the row given by
- * bta_last_info is then only the row inside its block.  Synchronises.
+ * batch on one GPU): P - 1 separator blocks sigma_p = p h - 1, with
+ * h = ceil((n + 1) / P), cut the n time blocks into P partitions whose
+ * interiors are eliminated together (every (matrix, partition) pair is one
+ * instance of the same batched launches), then the separators form a reduced
+ * BTA system of P - 1 blocks.  The sequential chain shrinks from n to about
+ * n/P + P steps at the price of extra fill products, which pays for small
+ * blocks.  P = 1 restores the sequential recurrences.
+ * Requires n - (P - 1) h >= 1 (the last partition holds an interior block)
+ * and a <= b; otherwise BTA_ERR_ARG and nothing changes.  The block arrays are
+ * re-laid out with P h slots per matrix (padding included) and the
+ * partitioned path adds two arrays of that size (fill rows of the factor and
+ * of the selected inverse) plus per-instance scratch.  Assembled Q matrices
+ * are kept; factors, selected inverses and any captured f_obj graph are
+ * dropped.  Results agree with the sequential path up to rounding; a
+ * non-positive pivot is still reported as BTA_ERR_NOT_PD with the right
+ * matrix, but the row given by bta_last_info is then the row inside the
+ * failing block's partition.  Synchronises the device.  Errors:
+ * BTA_ERR_ARG, BTA_ERR_OOM (the context is then back in the sequential
+ * layout, or has no storage left and must be destroyed), BTA_ERR_CUDA.
  */
 int bta_set_time_partitions(bta_ctx_t ctx, int P);
 

@@ -250,7 +250,9 @@ class BtaContext:
 
     def set_time_partitions(self, P: int):
         """bta_set_time_partitions: P > 1 runs factor/solve/selinv by time-domain
-        partitioning (P partitions eliminated together, then the separators)."""
+        partitioning (P partitions eliminated together, then the separators).
+        Needs n - (P - 1) ceil((n + 1) / P) >= 1 and a <= b; keeps assembled
+        matrices, drops factors."""
         _check(lib().bta_set_time_partitions(self.handle, int(P)), "bta_set_time_partitions")
 
     def factor_batch(self, kind: int):
@@ -365,6 +367,14 @@ def bta_create_batched(n, b, a, precision=BTA_FP64, batch=1, stream=None) -> Bta
 
 def bta_set_time_partitions(ctx: BtaContext, P: int):
     ctx.set_time_partitions(P)
+
+
+def time_partitions_valid(n: int, a: int, b: int, P: int) -> bool:
+    """Whether bta_set_time_partitions accepts P for blocks of this shape."""
+    if P == 1:
+        return True
+    h = -(-(n + 1) // P)
+    return P > 1 and n - (P - 1) * h >= 1 and a <= b
 
 
 def bta_factor_batch(ctx: BtaContext, kind: int):

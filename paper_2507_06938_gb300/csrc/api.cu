@@ -1,6 +1,7 @@
 // Context life cycle, storage accessors, status and error reporting of the
 // C ABI declared in include/bta.h.
 
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstdlib>
@@ -62,31 +63,48 @@ int dalloc(double** p, size_t elems) {
 }
 
 void store_free(BtaStore& M) {
-    if (M.D) cudaFree(M.D);
-    if (M.B) cudaFree(M.B);
-    if (M.R) cudaFree(M.R);
+    if (M.D) cudaFree(M.D - M.oD);
+    if (M.B) cudaFree(M.B - M.oB);
+    if (M.R) cudaFree(M.R - M.oR);
     if (M.T) cudaFree(M.T);
     M = BtaStore{};
 }
 
-int store_alloc(BtaStore& M, int nmat, int n, int b, int a) {
-    const long long bb = (long long)b * b;
-    M.sD = n * bb;
-    M.sB = (n > 1 ? n - 1 : 0) * bb;
-    M.sR = (long long)n * a * b;
+}  // namespace
+
+// `blk` block slots per matrix (blk == n: the compact layout, n - 1 slots for
+// B) and `lead` leading padding slots before matrix 0; everything zeroed.
+int store_alloc(BtaStore& M, int nmat, int n, int b, int a, int blk, int lead) {
+    const long long bb = (long long)b * b, ab = (long long)a * b;
+    const bool compact = blk == n && lead == 0;
+    M.sD = blk * bb;
+    M.sB = (compact ? (n > 1 ? n - 1 : 0) : blk) * bb;
+    M.sR = (long long)blk * ab;
     M.sT = (long long)a * a;
-    BTA_TRY(dalloc(&M.D, (size_t)nmat * M.sD));
-    BTA_TRY(dalloc(&M.B, (size_t)nmat * M.sB));
-    BTA_TRY(dalloc(&M.R, (size_t)nmat * M.sR));
-    BTA_TRY(dalloc(&M.T, (size_t)nmat * M.sT));
+    M.oD = lead * bb;
+    M.oB = lead * bb;
+    M.oR = lead * ab;
+    double* p = nullptr;
+    BTA_TRY(dalloc(&p, (size_t)(M.oD + nmat * M.sD)));
+    M.D = p + M.oD;
+    BTA_TRY(dalloc(&p, (size_t)(M.oB + nmat * M.sB)));
+    M.B = p + M.oB;
+    BTA_TRY(dalloc(&p, (size_t)(M.oR + nmat * M.sR)));
+    M.R = p + M.oR;
+    BTA_TRY(dalloc(&p, (size_t)nmat * M.sT));
+    M.T = p;
+    BTA_CUDA_TRY(cudaMemset(M.D - M.oD, 0, (size_t)(M.oD + nmat * M.sD) * sizeof(double)));
+    BTA_CUDA_TRY(cudaMemset(M.B - M.oB, 0, (size_t)std::max<long long>(1, M.oB + nmat * M.sB) * sizeof(double)));
+    BTA_CUDA_TRY(cudaMemset(M.R - M.oR, 0, (size_t)std::max<long long>(1, M.oR + nmat * M.sR) * sizeof(double)));
+    BTA_CUDA_TRY(cudaMemset(M.T, 0, (size_t)std::max<long long>(1, nmat * M.sT) * sizeof(double)));
     return BTA_OK;
 }
 
-}  // namespace
+void store_release(BtaStore& M) { store_free(M); }
 
 int ensure_sigma(bta_ctx_t ctx) {
     if (ctx->S.D) return BTA_OK;
-    int rc = store_alloc(ctx->S, ctx->nmat, ctx->n, ctx->b, ctx->a);
+    int rc = store_alloc(ctx->S, ctx->nmat, ctx->n, ctx->b, ctx->a, ctx->blk, ctx->blk != ctx->n ? 1 : 0);
     if (rc != BTA_OK) store_free(ctx->S);
     return rc;
 }
@@ -115,8 +133,10 @@ extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch,
     if (cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) return fail(BTA_ERR_CUDA);
     const long long bb = (long long)b * b;
     const int nm = c->nmat;
-    if ((rc = store_alloc(c->Q, nm, n, b, a)) != BTA_OK) return fail(rc);
-    if ((rc = store_alloc(c->L, nm, n, b, a)) != BTA_OK) return fail(rc);
+    c->blk = n;
+    c->tip_off = (long long)n * bb;
+    if ((rc = store_alloc(c->Q, nm, n, b, a, n, 0)) != BTA_OK) return fail(rc);
+    if ((rc = store_alloc(c->L, nm, n, b, a, n, 0)) != BTA_OK) return fail(rc);
     c->sLinv = n * bb + (long long)a * a;
     if ((rc = dalloc(&c->Linv, (size_t)nm * c->sLinv)) != BTA_OK) return fail(rc);
     // the strict upper triangles of the inverse blocks are never written by the factor
@@ -244,7 +264,7 @@ extern "C" int bta_block_ptr(bta_ctx_t c, int which, int store, int kind, int i,
             return BTA_OK;
         }
         if (kind == BTA_BLK_T) {
-            *ptr_out = base + (long long)c->n * bb;
+            *ptr_out = base + c->tip_off;
             if (ld_out) *ld_out = c->a;
             return BTA_OK;
         }

@@ -124,6 +124,9 @@ struct BtaStore {
     double* R = nullptr;     // n * a * b
     double* T = nullptr;     // a * a
     long long sD = 0, sB = 0, sR = 0, sT = 0;
+    // elements between the allocation and D, B, R (a leading padding block of
+    // the time-partitioned layout; 0 otherwise)
+    long long oD = 0, oB = 0, oR = 0;
 };
 
 // Scratch vectors: row r of matrix m is vec + (r * nmat + m) * N.
@@ -131,6 +134,10 @@ enum { VEC_RCOPY = 0, VEC_RES, VEC_CORR, VEC_Z, VEC_TMP, VEC_RHS, VEC_MU, VEC_RO
 
 struct bta_ctx_s {
     int n, b, a, precision;
+    // block slots per matrix in the D, B, R and L^{-1} arrays: n (n - 1 for B)
+    // normally, P h (with one leading padding slot) when time-partitioned
+    int blk = 0;
+    long long tip_off = 0;   // elements from a matrix's L^{-1} blocks to its L_tt^{-1}
     int batch;               // parameter slots; matrix storage index m = kind * batch + slot
     int nmat;                // 2 * batch
     long long N;
@@ -214,11 +221,11 @@ struct CholFork;
 int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ldx, int n,
                long long row0, long long* status, double* W, int leaf, const GemmExec* ex = nullptr,
                int batch = 1, long long sA = 0, long long sX = 0, long long sW = 0, int m_first = 0,
-               int nbatch = 1, const CholFork* fork = nullptr, int depth = 0);
+               int nbatch = 1, const CholFork* fork = nullptr, int depth = 0, int per = 1);
 // Double-float Cholesky + inverse of `batch` blocks of order n <= 128 (leaf_df32.cu).
 int chol_inv_df32_launch(cudaStream_t s, double* A, long long lda, long long sA, double* X, long long ldx,
                          long long sX, int n, long long row0, long long* status, int batch, int m_first,
-                         int nbatch);
+                         int nbatch, int per = 1);
 // C = beta Cin + alpha op(A) op(B) in double-float on the FP32 pipe (leaf_df32.cu)
 int gemm_df32(cudaStream_t s, const Gemm64& g);
 int copy_mat64(cudaStream_t s, const double* src, long long lds, double* dst, long long ldd,
@@ -281,6 +288,10 @@ int assemble_weighted_impl(bta_ctx_t ctx, bta_model_t m, const double* params, i
 // theta (count x dim_theta) -> parameter slots (count x BTA_PSTRIDE)
 int theta_to_params_impl(bta_model_t m, const double* theta, int count, double* params, cudaStream_t s);
 int ensure_sigma(bta_ctx_t ctx);
+// (re)allocation of a block store with `blk` slots per matrix and `lead`
+// leading padding slots (api.cu); store_release frees it
+int store_alloc(BtaStore& M, int nmat, int n, int b, int a, int blk, int lead);
+void store_release(BtaStore& M);
 int axpby64(cudaStream_t s, long long len, double alpha, const double* x, double beta, const double* y,
             double* out);
 inline double* vec_row(bta_ctx_t c, int row, int m) { return c->vec + ((long long)row * c->nmat + m) * c->N; }

@@ -242,7 +242,8 @@ __device__ __forceinline__ double newton_rsqrt(double d) {
 
 __global__ void __launch_bounds__(256) chol_inv_leaf_kernel(double* A, long long lda, long long sA, double* X,
                                                             long long ldx, long long sX, int n, long long row0,
-                                                            long long* status, int m_first, int nbatch) {
+                                                            long long* status, int m_first, int nbatch,
+                                                            int per) {
     extern __shared__ double sm[];
     double* S = sm;                 // working matrix, column-major, ld LDS
     double* L = sm + LDS * LEAF_MAX;
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(256) chol_inv_leaf_kernel(double* A, long long
             if (tid == 0 && !(y > 0.0) && status) {
                 if (atomicCAS((unsigned long long*)status, 0ull, (unsigned long long)BTA_ERR_NOT_PD) == 0ull) {
                     status[1] = row0 + k;
-                    const int mm = m_first + (int)blockIdx.x;   // storage index -> public index
+                    const int mm = m_first + (int)blockIdx.x / per;   // storage index -> public index
                     status[2] = 2 * (mm % nbatch) + mm / nbatch;
                 }
             }
@@ -533,11 +534,12 @@ int gemm_exec(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
 }
 
 static int leaf_launch(cudaStream_t s, double* A, long long lda, long long sA, double* X, long long ldx,
-                       long long sX, int n, long long row0, long long* status, int batch, int m_first, int nbatch) {
+                       long long sX, int n, long long row0, long long* status, int batch, int m_first, int nbatch,
+                       int per) {
     const size_t smem = (3 * LDS * LEAF_MAX + LEAF_MAX + 1) * sizeof(double);
     BTA_TRY(ensure_dyn_smem((const void*)chol_inv_leaf_kernel, (int)smem));
     const int threads = 256;
-    chol_inv_leaf_kernel<<<batch, threads, smem, s>>>(A, lda, sA, X, ldx, sX, n, row0, status, m_first, nbatch);
+    chol_inv_leaf_kernel<<<batch, threads, smem, s>>>(A, lda, sA, X, ldx, sX, n, row0, status, m_first, nbatch, per);
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }
@@ -550,16 +552,17 @@ static int leaf_launch(cudaStream_t s, double* A, long long lda, long long sA, d
 //                 X21 = -X22 (L21 X11)
 int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ldx, int n, long long row0,
                long long* status, double* W, int leaf, const GemmExec* ex, int batch, long long sA,
-               long long sX, long long sW, int m_first, int nbatch, const CholFork* fork, int depth) {
+               long long sX, long long sW, int m_first, int nbatch, const CholFork* fork, int depth, int per) {
     if (n <= 0 || batch <= 0) return BTA_OK;
     if (ex && ex->df_leaf > 0) {
         // mixed precision: double-float leaves on the FP32 pipe
         leaf = std::min(ex->df_leaf, 128);
         if (n <= leaf)
-            return chol_inv_df32_launch(s, A, lda, sA, X, ldx, sX, n, row0, status, batch, m_first, nbatch);
+            return chol_inv_df32_launch(s, A, lda, sA, X, ldx, sX, n, row0, status, batch, m_first, nbatch, per);
     } else {
         leaf = std::max(8, std::min(leaf, LEAF_MAX));
-        if (n <= leaf) return leaf_launch(s, A, lda, sA, X, ldx, sX, n, row0, status, batch, m_first, nbatch);
+        if (n <= leaf)
+            return leaf_launch(s, A, lda, sA, X, ldx, sX, n, row0, status, batch, m_first, nbatch, per);
     }
     const int half = (n + 1) / 2;
     int n1 = ((half + leaf - 1) / leaf) * leaf;
@@ -576,7 +579,7 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
     const bool forked = fork && fork->s2 && depth < CHOL_FORK_DEPTH;
     double* Wc = forked ? W + (long long)n2 * n1 : W;
     BTA_TRY(chol_inv64(s, A11, lda, X11, ldx, n1, row0, status, Wc, leaf, ex, batch, sA, sX, sW, m_first, nbatch,
-                       fork, depth + 1));
+                       fork, depth + 1, per));
     Gemm64 g{};
     // W (n2 x n1) = A21 * X11^T      (op(B) upper)
     g = Gemm64{};
@@ -616,11 +619,11 @@ int chol_inv64(cudaStream_t s, double* A, long long lda, double* X, long long ld
         BTA_TRY(gemm_exec(ex && ex->fn ? &fork->ex2 : ex, fork->s2, g));
         BTA_CUDA_TRY(cudaEventRecord(ev_join, fork->s2));
         BTA_TRY(chol_inv64(s, A22, lda, X22, ldx, n2, row0 + n1, status, Wc, leaf, ex, batch, sA, sX, sW, m_first,
-                           nbatch, fork, depth + 1));
+                           nbatch, fork, depth + 1, per));
         BTA_CUDA_TRY(cudaStreamWaitEvent(s, ev_join, 0));
     } else {
         BTA_TRY(chol_inv64(s, A22, lda, X22, ldx, n2, row0 + n1, status, Wc, leaf, ex, batch, sA, sX, sW, m_first,
-                           nbatch));
+                           nbatch, nullptr, 0, per));
         BTA_TRY(gemm_exec(ex, s, g));
     }
     // X21 = -X22 * W   (op(A) lower)

@@ -124,7 +124,7 @@ __device__ __forceinline__ df df_rsqrt(df x) {
 __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, long long lda, long long sA, double* X,
                                                                    long long ldx, long long sX, int n,
                                                                    long long row0, long long* status, int m_first,
-                                                                   int nbatch) {
+                                                                   int nbatch, int per) {
     extern __shared__ float smf[];
     // M[r][c] at (c * DF_LD + r): lower triangle = A, then L; strict upper = B / X transposed
     float* Sh = smf;
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(DF_THREADS) chol_inv_df32_kernel(double* A, lo
             if (tid == 0 && !(y.hi > 0.f) && status) {
                 if (atomicCAS((unsigned long long*)status, 0ull, (unsigned long long)BTA_ERR_NOT_PD) == 0ull) {
                     status[1] = row0 + k;
-                    const int mm = m_first + (int)blockIdx.x;
+                    const int mm = m_first + (int)blockIdx.x / per;
                     status[2] = 2 * (mm % nbatch) + mm / nbatch;
                 }
             }
@@ -352,11 +352,12 @@ size_t chol_inv_df32_smem_bytes() {
 
 int chol_inv_df32_launch(cudaStream_t s, double* A, long long lda, long long sA, double* X, long long ldx,
                          long long sX, int n, long long row0, long long* status, int batch, int m_first,
-                         int nbatch) {
+                         int nbatch, int per) {
     if (n > DF_MAX || n < 1 || batch < 1) return BTA_ERR_ARG;
     const size_t smem = chol_inv_df32_smem_bytes();
     BTA_TRY(ensure_dyn_smem((const void*)chol_inv_df32_kernel, (int)smem));
-    chol_inv_df32_kernel<<<batch, DF_THREADS, smem, s>>>(A, lda, sA, X, ldx, sX, n, row0, status, m_first, nbatch);
+    chol_inv_df32_kernel<<<batch, DF_THREADS, smem, s>>>(A, lda, sA, X, ldx, sX, n, row0, status, m_first, nbatch,
+                                                         per);
     BTA_LAUNCH_CHECK();
     return BTA_OK;
 }

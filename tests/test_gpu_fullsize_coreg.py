@@ -15,9 +15,12 @@ checks use what holds exactly at any size:
     which involve only entries of Sigma_c on the BTA pattern:
     (Sigma Q)_ii = Sigma_{i,i-1} Q_{i-1,i} + Sigma_ii Q_ii + Sigma_{i,i+1} Q_{i+1,i}
     + Sigma_{i,t} Q_{t,i}, and the tip block likewise.
+  * f against the oracle's block tier (the block recurrences on the CPU,
+    pinned to the dense tier at small sizes), computed once per module.
 Tolerances as for the working-size univariate test: FP64 log-det 1e-10,
-Sigma 1e-9, residual 1e-10; mixed precision log-det 1e-8, residual 1e-10,
-Sigma 5e-5 of the block maximum.
+Sigma 1e-9, residual 1e-10, f 1e-10 of |log|Q_p|| + |log|Q_c||; mixed
+precision log-det 1e-8, residual 1e-10, Sigma 5e-5 of the block maximum,
+f 1e-8 of the log-determinant scale.
 """
 
 import time
@@ -39,7 +42,10 @@ def setup():
     _build.build()
     p = problem("c3")
     fd = omodel.fem_data(p)
-    return dict(p=p, fd=fd, theta=p.theta0.copy())
+    from oracle import fobj as ofobj
+    terms = ofobj.f_obj_terms(p, p.theta0, tier="bta", fd=fd)
+    return dict(p=p, fd=fd, theta=p.theta0.copy(), f=terms["f"],
+                ld_scale=abs(terms["logdet_p"]) + abs(terms["logdet_c"]))
 
 
 def _closed_form(p, theta, fd):
@@ -89,6 +95,7 @@ def test_coregional_full_size(setup, precision):
     ld_tol = 1e-10 if precision == 0 else 1e-8
     s_tol = 1e-9 if precision == 0 else 5e-5
     assert abs(ld.item() - ld_ref) <= ld_tol * abs(ld_ref), (ld.item(), ld_ref)
+    assert abs(f.item() - setup["f"]) <= ld_tol * setup["ld_scale"], (f.item(), setup["f"])
     # Sigma_p: diagonal and sub-diagonal blocks at a few time steps
     S = bta.BTA_STORE_SIGMA
 
