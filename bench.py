@@ -441,6 +441,8 @@ def measure(args, precision_name, warmup, steps, e2e_steps, dist, rank, world, l
         ctx.sync()
         out["launches"] = bta.bta_launch_count() - launches0
         out["prof"] = ctx.profile_read()
+        # CUDA-event phases of the last timed step (its last group of theta points)
+        out["phases"] = ctx.profile_phases()
         ctx.profile(False)
         out["ms"] = e0.elapsed_time(e1)
         out["clocks"] = clk.summary()
@@ -567,6 +569,8 @@ def run_ours(args):
         "batch": B,
         "autotuned": (None if r["tuned"] is None else dict(zip(bta.BtaContext.AUTOTUNE_KEYS, r["tuned"]))),
         "gpu_launches": int(r["launches"]),
+        "phases_ms": dict(r["phases"], how="CUDA events at the phase boundaries of the last timed step "
+                                            "(bta_profile_phases)"),
         "clocks": r["clocks"],
         "fp64_peak_measured": {"dfma_tflops": fp64_peak["dfma"], "dmma_tflops": fp64_peak["dmma"],
                                "how": "bta_fp64_peak: FP64 FMA loop / m8n8k4 FP64 MMA loop over every SM, "
@@ -576,6 +580,7 @@ def run_ours(args):
         line["fp64"] = {"value": cmp["value"], "unit": UNIT, "ms_per_step": cmp["ms"] / FP64_COMPARE_STEPS,
                         "steps": FP64_COMPARE_STEPS, "warmup": 1, "tflops": cmp["tflops"],
                         "roofline": cmp["roofline"], "gpu_launches": int(cmp["launches"]),
+                        "phases_ms": cmp["phases"],
                         "clocks": cmp["clocks"], "mixed_over_fp64": r["value"] / cmp["value"]}
         line["errors"] = errors_against(r["last"], cmp["last"])
     if world == 1 and not args.no_cpu_baseline:

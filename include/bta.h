@@ -406,6 +406,18 @@ long long bta_launch_count(void);
 int bta_profile(bta_ctx_t ctx, int enable);
 int bta_profile_read(bta_ctx_t ctx, double* ms_total, long long* launches, double* flops_total);
 
+/* bta_profile_phases -- durations (ms, CUDA events) of the phases of the
+ * last group of theta points that bta_fobj_grad evaluated while profiling was
+ * enabled: [0] theta map and assembly of Q_p and Q_c (Section IV-B),
+ * [1] factorisations and log-determinants (Section III-A), [2] right-hand
+ * side, solve with refinement and f (Eq. 8), [3] selected inversions,
+ * [4] adjoint traces and gradient.  Writes min(count, BTA_PHASES) values to
+ * ms_out (host) and synchronises the events.  BTA_ERR_STATE if no such group
+ * ran since profiling was enabled; BTA_ERR_ARG for a null pointer or
+ * count < 1.  Measurement aid; no effect on results. */
+#define BTA_PHASES 5
+int bta_profile_phases(bta_ctx_t ctx, double* ms_out, int count);
+
 /* bta_autotune -- choose the launch shapes of the block factorisation and
  * selected inversion for this context's block order, precision and batch by
  * timing candidates on the context's own storage (Section III-A's

@@ -27,6 +27,8 @@ BTA_FP64, BTA_MIXED, BTA_MIXED_HI = 0, 1, 2
 BTA_LIK_GAUSSIAN, BTA_LIK_POISSON = 0, 1
 BTA_BLK_D, BTA_BLK_B, BTA_BLK_R, BTA_BLK_T = 0, 1, 2, 3
 BTA_STORE_Q, BTA_STORE_L, BTA_STORE_SIGMA, BTA_STORE_LINV = 0, 1, 2, 3
+BTA_PHASES = 5
+PHASE_NAMES = ("assemble", "factor_logdet", "solve_f", "selinv", "adjoint")
 
 
 class BtaError(RuntimeError):
@@ -87,6 +89,7 @@ def lib():
         "bta_launch_count": (C.c_longlong, []),
         "bta_profile": (ip, [vp, ip]),
         "bta_profile_read": (ip, [vp, C.POINTER(dp), C.POINTER(C.c_longlong), C.POINTER(dp)]),
+        "bta_profile_phases": (ip, [vp, C.POINTER(dp), ip]),
         "bta_chol_inv_noalloc": (ip, [vp, ip, ip, vp, ip, vp, vp]),
         "bta_autotune": (ip, [vp, ip, C.POINTER(C.c_int)]),
         "bta_fobj_eval_multi": (ip, [ip, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(ip),
@@ -117,7 +120,7 @@ def exported_symbols():
             "bta_create_batched", "bta_batch_size", "bta_factor_batch", "bta_selinv_batch",
             "bta_last_error_matrix", "bta_fobj_grad", "bta_autotune", "bta_fobj_eval_multi",
             "bta_fobj_residual", "bta_fp64_peak", "bta_fobj_grad_host", "bta_fobj_laplace",
-            "bta_set_time_partitions"]
+            "bta_set_time_partitions", "bta_profile_phases"]
 
 
 def _check(code: int, where: str):
@@ -291,6 +294,13 @@ class BtaContext:
         ms, n, fl = C.c_double(), C.c_longlong(), C.c_double()
         _check(lib().bta_profile_read(self.handle, C.byref(ms), C.byref(n), C.byref(fl)), "bta_profile_read")
         return ms.value, n.value, fl.value
+
+    def profile_phases(self):
+        """bta_profile_phases: ms of (assembly, factorisation + log-det, solve + f,
+        selected inversion, adjoint) of the last profiled gradient group."""
+        out = (C.c_double * BTA_PHASES)()
+        _check(lib().bta_profile_phases(self.handle, out, BTA_PHASES), "bta_profile_phases")
+        return dict(zip(PHASE_NAMES, (float(v) for v in out)))
 
     def fobj_grad(self, model: BtaModel, thetas, f_out, grad_out):
         n_theta = int(thetas.shape[0]) if thetas.dim() == 2 else 1
@@ -467,6 +477,10 @@ def bta_profile(ctx: BtaContext, enable: bool):
 
 def bta_profile_read(ctx: BtaContext):
     return ctx.profile_read()
+
+
+def bta_profile_phases(ctx: BtaContext):
+    return ctx.profile_phases()
 
 
 NOALLOC_MAX_B = 2048

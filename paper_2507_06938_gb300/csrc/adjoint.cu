@@ -348,6 +348,7 @@ extern "C" int bta_fobj_grad(bta_ctx_t ctx, bta_model_t m, const double* thetas_
             BTA_TRY(selinv_impl(ctx, 0, cnt, s));
             BTA_TRY(selinv_impl(ctx, B, cnt, s));
         }
+        BTA_TRY(prof_phase(ctx, 4, s));
         double* Tp = ctx->adj;
         double* Tc = ctx->adj + (long long)B * rec;
         double* Tm = ctx->adj + 2LL * B * rec;
@@ -367,6 +368,7 @@ extern "C" int bta_fobj_grad(bta_ctx_t ctx, bta_model_t m, const double* thetas_
         const int threads = ((m->dim_theta + 31) / 32) * 32;
         adjoint_combine_kernel<<<cnt, threads, 0, s>>>(c);
         BTA_LAUNCH_CHECK();
+        BTA_TRY(prof_phase(ctx, 5, s));
     }
     return BTA_OK;
 }

@@ -244,6 +244,8 @@ extern "C" int bta_destroy(bta_ctx_t c) {
     if (c->oz_err) cudaFree(c->oz_err);
     if (c->status) cudaFree(c->status);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->phase_ev)
+        if (e) cudaEventDestroy(e);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->aux) cudaStreamDestroy(c->aux);
@@ -343,6 +345,30 @@ extern "C" int bta_profile(bta_ctx_t c, int enable) {
     c->prof = enable;
     c->prof_used = 0;
     c->prof_flops = 0.0;
+    c->phase_seen = 0;
+    if (enable)
+        for (cudaEvent_t& e : c->phase_ev)
+            if (!e) BTA_CUDA_TRY(cudaEventCreate(&e));
+    return BTA_OK;
+}
+
+int prof_phase(bta_ctx_t ctx, int k, cudaStream_t s) {
+    if (!ctx->prof || !ctx->phase_ev[k]) return BTA_OK;
+    BTA_TRY(prof_record(ctx->phase_ev[k], s));
+    ctx->phase_seen |= 1 << k;
+    return BTA_OK;
+}
+
+extern "C" int bta_profile_phases(bta_ctx_t c, double* ms_out, int count) {
+    if (!c || !ms_out || count < 1) return BTA_ERR_ARG;
+    const int all = (1 << (BTA_PHASES + 1)) - 1;
+    if ((c->phase_seen & all) != all) return BTA_ERR_STATE;
+    BTA_CUDA_TRY(cudaEventSynchronize(c->phase_ev[BTA_PHASES]));
+    for (int k = 0; k < std::min(count, BTA_PHASES); ++k) {
+        float ms = 0.f;
+        BTA_CUDA_TRY(cudaEventElapsedTime(&ms, c->phase_ev[k], c->phase_ev[k + 1]));
+        ms_out[k] = ms;
+    }
     return BTA_OK;
 }
 

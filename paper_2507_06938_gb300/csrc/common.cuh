@@ -192,7 +192,15 @@ struct bta_ctx_s {
     std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
     size_t prof_used = 0;
     double prof_flops = 0.0;
+    // phase boundaries of the last full-group gradient evaluation (profiling on):
+    // [0] start, [1] assembled, [2] factored + log-det, [3] f (solve, refinement),
+    // [4] selected inversions, [5] adjoint traces and gradient
+    cudaEvent_t phase_ev[BTA_PHASES + 1] = {};
+    int phase_seen = 0;      // bit k: boundary k recorded since profiling was enabled
 };
+
+// boundary k of the phase timing, when profiling is on (fobj.cu, adjoint.cu)
+int prof_phase(bta_ctx_t ctx, int k, cudaStream_t s);
 
 // public matrix index (2 slot + kind) <-> storage index (kind batch + slot)
 inline int storage_index(const bta_ctx_s* c, int which) {

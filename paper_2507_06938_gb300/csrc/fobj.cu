@@ -63,19 +63,23 @@ __global__ void fobj_final_kernel(const double* theta, const double* theta0, int
 static int fobj_group(bta_ctx_t ctx, bta_model_t m, const double* theta, int cnt, double* f, cudaStream_t s) {
     const int B = ctx->batch;
     const long long N = ctx->N, nb = (long long)ctx->n * ctx->b;
+    BTA_TRY(prof_phase(ctx, 0, s));
     BTA_TRY(theta_to_params_impl(m, theta, cnt, ctx->params, s));
     if (cnt == B) {
         // all Q_p and Q_c of the batch in one pass
         BTA_TRY(assemble_impl(ctx, m, ctx->params, 0, 2 * B, s));
+        BTA_TRY(prof_phase(ctx, 1, s));
         BTA_TRY(factor_impl(ctx, 0, 2 * B, s));
         BTA_TRY(logdet_impl(ctx, 0, 2 * B, ctx->ld, s));
     } else {
+        for (int kind = 0; kind < 2; ++kind) BTA_TRY(assemble_impl(ctx, m, ctx->params, kind * B, cnt, s));
+        BTA_TRY(prof_phase(ctx, 1, s));
         for (int kind = 0; kind < 2; ++kind) {
-            BTA_TRY(assemble_impl(ctx, m, ctx->params, kind * B, cnt, s));
             BTA_TRY(factor_impl(ctx, kind * B, cnt, s));
             BTA_TRY(logdet_impl(ctx, kind * B, cnt, ctx->ld + kind * B, s));
         }
     }
+    BTA_TRY(prof_phase(ctx, 2, s));
     double* rhs = vec_row(ctx, VEC_RHS, B);
     double* mu = vec_row(ctx, VEC_MU, B);
     {
@@ -99,6 +103,7 @@ static int fobj_group(bta_ctx_t ctx, bta_model_t m, const double* theta, int cnt
     fobj_final_kernel<<<cnt, 1, 0, s>>>(theta, m->theta0, m->dim_theta, ctx->params, m->var_stats, m->nv,
                                         (double)m->m, ctx->ld, ctx->ld + B, ctx->dots + 3 * B, f);
     BTA_LAUNCH_CHECK();
+    BTA_TRY(prof_phase(ctx, 3, s));
     return BTA_OK;
 }
 

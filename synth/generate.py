@@ -244,6 +244,8 @@ CONFIGS = {
     # trivariate coregional on a 2000-node Delaunay mesh, b=6000, N=288,006
     "c5": dict(nv=3, mesh=("delaunay", 2000), nt=48, nr=2, seed=5, per_step=1000,
                shared_sites=True),
+    # c5 with 2 time steps: the b=6000 Schur-update products of c5 at about 11 GB on the device
+    "c5p": dict(nv=3, mesh=("delaunay", 2000), nt=2, nr=2, seed=5, per_step=1000, shared_sites=True),
     # reduced copy of c5 with 200 mesh nodes (b=600, N=28,806)
     "c5r": dict(nv=3, mesh=("delaunay", 200), nt=48, nr=2, seed=5, per_step=100,
                 shared_sites=True),

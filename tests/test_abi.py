@@ -48,6 +48,18 @@ def test_binding_matches_header():
     assert sorted(bta.exported_symbols()) == _declared_functions()
 
 
+def test_binding_constants_match_header():
+    """Every integer #define of the header has the same value in the binding."""
+    from paper_2507_06938_gb300 import bta
+    text = open(os.path.join(ROOT, "include", "bta.h")).read()
+    defs = dict(re.findall(r"^#define\s+(BTA_[A-Z0-9_]+)\s+(-?\d+)\b", text, flags=re.M))
+    assert "BTA_PHASES" in defs and "BTA_MIXED_HI" in defs
+    for name, value in defs.items():
+        if hasattr(bta, name):
+            assert getattr(bta, name) == int(value), name
+    assert len(bta.PHASE_NAMES) == bta.BTA_PHASES
+
+
 def test_host_only_entry_points(lib):
     assert lib.bta_strerror(0) == b"ok"
     assert b"positive definite" in lib.bta_strerror(3)
