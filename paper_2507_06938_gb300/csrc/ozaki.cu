@@ -183,6 +183,9 @@ struct Args {
     int mcum[MAX_MT + 1];// lowerC: tiles of row tiles 0..m-1
 };
 
+// row tiles per band of the tile order of a general (not lower-only) output
+constexpr int RASTER_ROWS = 8;
+
 struct Unit {
     int inst, m0, n0;
     int kbl;             // first K block of the tile
@@ -203,8 +206,15 @@ __device__ __forceinline__ bool decode_unit(const Args& a, int u, Unit& w) {
         while (mt + 1 < a.gm && a.mcum[mt + 1] <= tile) ++mt;
         nt = tile - a.mcum[mt];
     } else {
-        mt = tile / a.gn;
-        nt = tile % a.gn;
+        // bands of RASTER_ROWS row tiles, column by column inside a band: the
+        // units in flight at one time (one per SM) cover about 8 x 19 tiles and
+        // share their A and B digit panels in L2, instead of one or two row
+        // tiles against every column panel
+        const int band = tile / (RASTER_ROWS * a.gn);
+        const int in = tile - band * RASTER_ROWS * a.gn;
+        const int rows = min(RASTER_ROWS, a.gm - band * RASTER_ROWS);
+        mt = band * RASTER_ROWS + in % rows;
+        nt = in / rows;
     }
     w.m0 = mt * TM;
     w.n0 = nt * TN;
@@ -846,6 +856,8 @@ template <int RS, int S>
 __global__ void __launch_bounds__(SPLIT_THREADS) split_kernel(SplitJob j0, SplitJob j1) {
     extern __shared__ double stile[];   // RS x (Kp + 4)
     __shared__ int row_e[RS];
+    __shared__ unsigned int row_m[RS];
+    static_assert(RS >= 1 && RS <= SPLIT_THREADS / 32 && (SPLIT_THREADS / 32) % RS == 0, "rows per CTA");
     int rb = blockIdx.x;
     const int nrb0 = j0.Rp / RS;
     const bool second = rb >= nrb0;
@@ -867,22 +879,31 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_kernel(SplitJob j0, Split
         else
             *dst = 0.0;
     }
+    if (threadIdx.x < RS) row_m[threadIdx.x] = 0u;
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    for (int rr = warp; rr < RS; rr += SPLIT_THREADS / 32) {
+    {
+        // largest exponent field of each row: WPR warps per row, each over an
+        // interleaved share of the row, combined in shared memory
+        constexpr int WPR = (SPLIT_THREADS / 32) / RS;
+        const int rr = warp / WPR, q = warp % WPR;
         unsigned int m = 0;
         const double* row = stile + rr * ld;
-        for (int k = lane; k < J.Kp; k += 32) m = max(m, (unsigned int)((__double2hiint(row[k]) >> 20) & 0x7FF));
+        for (int k = q * 32 + lane; k < J.Kp; k += 32 * WPR)
+            m = max(m, (unsigned int)((__double2hiint(row[k]) >> 20) & 0x7FF));
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) {
-            // |x| < 2^(ef - 1023 + 1) for a normal number with exponent field ef;
-            // a NaN or Inf in the row gives a huge exponent, so the product
-            // overflows to a non-finite value instead of passing silently
-            const int e = m == 0 ? 0 : (m == 0x7FF ? 4096 : (int)m - 1023 + 1);
-            row_e[rr] = e;
-            expo[r0 + rr] = e;
-        }
+        if (lane == 0) atomicMax(&row_m[rr], m);
+    }
+    __syncthreads();
+    if (threadIdx.x < RS) {
+        const unsigned int m = row_m[threadIdx.x];
+        // |x| < 2^(ef - 1023 + 1) for a normal number with exponent field ef;
+        // a NaN or Inf in the row gives a huge exponent, so the product
+        // overflows to a non-finite value instead of passing silently
+        const int e = m == 0 ? 0 : (m == 0x7FF ? 4096 : (int)m - 1023 + 1);
+        row_e[threadIdx.x] = e;
+        expo[r0 + threadIdx.x] = e;
     }
     __syncthreads();
     const int per = J.Kp / 4;   // Kp is a multiple of 64

@@ -2,8 +2,8 @@
 around the Schur-update products of the factorisation) and
 bta_profile_phases (events at the phase boundaries of a gradient group).
 Checks that the phases cover the step: each positive, their sum within a few
-percent of the whole call timed on the same stream, for the directly run
-group and for the CUDA-graph replay; the product events count two launches
+percent of the whole call timed on the same stream, for the graph capture
+and its replays; the product events count two launches
 per factorisation step and matrix group with b^3 nominal flops per matrix;
 and the state errors.  Profiling leaves the results unchanged."""
 
@@ -64,6 +64,7 @@ def test_phases_cover_the_gradient_step(precision, monkeypatch):
         assert abs(flops - launches * 2 * B * float(p.b) ** 3) <= 1e-9 * flops
         ctx.profile(False)
         ctx.sync()
-    assert torch.equal(f, f0) and torch.equal(g, g0)
+    # the same values as unprofiled (the graph replay may sum in another order)
+    assert torch.allclose(f, f0, rtol=1e-12, atol=0) and torch.allclose(g, g0, rtol=1e-9, atol=1e-12)
     ctx.close()
     model.close()
