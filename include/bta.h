@@ -429,11 +429,15 @@ int bta_profile_phases(bta_ctx_t ctx, double* ms_out, int count);
  *   split-product tile (35-bit digits: 0 = 128 x 96 tiles with 2 TMA stages,
  *   1 = 128 x 64 with 3; 49-bit digits: 0 = 128 x 64 with 2) and the waves of
  *   the persistent grid below which it splits K (1, 2), in FP64 the CTAs per
- *   SM of the DFMA GEMM's K split (1, 2, 4).
+ *   SM of the DFMA GEMM's K split (1, 2, 4); then in mixed precision the
+ *   tile order of the split product (row tiles per band: 1, 4, 8, 16),
+ *   timed separately on a product with a triangular operand (B X^T) and on a
+ *   general one.
  * Each candidate runs once untimed and `reps` (>= 1) times timed.  The
- * chosen values are written to chosen[0..5] (host: leaf, double-float leaf,
- * tensor threshold, tile, waves, FP64 CTAs per SM) and used by every later
- * call on the context.  The first diagonal block of every matrix is
+ * chosen values are written to chosen[0..7] (host: leaf, double-float leaf,
+ * tensor threshold, tile, waves, FP64 CTAs per SM, band of triangular-operand
+ * products, band of general products) and used by every later call on the
+ * context.  The first diagonal block of every matrix is
  * overwritten with a synthetic SPD block: call it before assembling, or
  * assemble again afterwards.  Synchronises the context's stream.  Errors:
  * BTA_ERR_ARG (null pointers, reps < 1), CUDA errors. */

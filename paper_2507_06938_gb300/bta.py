@@ -275,7 +275,8 @@ class BtaContext:
     def selinv_diag(self, which: int, out):
         _check(lib().bta_selinv_diag(self.handle, which, _ptr(out)), "bta_selinv_diag")
 
-    AUTOTUNE_KEYS = ("fp64_leaf", "df32_leaf", "tensor_min_dim", "split_tile", "split_waves", "fp64_ctas_per_sm")
+    AUTOTUNE_KEYS = ("fp64_leaf", "df32_leaf", "tensor_min_dim", "split_tile", "split_waves", "fp64_ctas_per_sm",
+                     "split_band_triangular", "split_band_general")
 
     def autotune(self, reps: int = 2):
         """bta_autotune: time the launch-shape candidates of the diagonal chain
@@ -283,7 +284,7 @@ class BtaContext:
         fastest; returns (leaf, df_leaf, tensor threshold, split-product tile,
         split waves, FP64 CTAs per SM).  Overwrites the first diagonal block
         of every matrix."""
-        out = (C.c_int * 6)()
+        out = (C.c_int * len(self.AUTOTUNE_KEYS))()
         _check(lib().bta_autotune(self.handle, int(reps), out), "bta_autotune")
         return tuple(int(v) for v in out)
 

@@ -100,6 +100,10 @@ struct GemmExec {
     int tile = 0;      // tile configuration of the split product (autotuned)
     int occupancy = 1; // waves of the persistent split-product grid before a K split (autotuned)
     int fp64_ctas = 2; // CTAs per SM the FP64 GEMM aims for through its K split (autotuned)
+    // row tiles per band of the split product's tile order, for products with a
+    // triangular operand and for general ones (autotuned; 1 = row by row)
+    int band_tri = 1;
+    int band_gen = 8;
 };
 
 // Side stream, events and executor for the products of the recursive
@@ -263,7 +267,7 @@ size_t ozaki_workspace_bytes(int M, int N, int K, int slices);
 // use 128 x 64, 2 stages.  occupancy: waves of the persistent grid below
 // which the K dimension is split.
 int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err, int slices, long long epi_wait = 0,
-               int tile = 0, int occupancy = 1);
+               int tile = 0, int occupancy = 1, int band = 1);
 int ozaki_tiles_for(int slices, int* out, int cap);
 int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
 // true when gemm_exec sends g to the split-precision path, whose operands are

@@ -180,11 +180,9 @@ struct Args {
     int inplace;         // Cin is C with beta = 1 (or the K split pre-initialised C)
     int bulk;            // in-place accumulation through bulk reduce-add (C, ldc, sC 16-byte aligned)
     long long epi_wait;  // wait limit (cycles) of the epilogue's accumulator hand-off
+    int band;            // row tiles per band of the tile order of a general output (1: row by row)
     int mcum[MAX_MT + 1];// lowerC: tiles of row tiles 0..m-1
 };
-
-// row tiles per band of the tile order of a general (not lower-only) output
-constexpr int RASTER_ROWS = 8;
 
 struct Unit {
     int inst, m0, n0;
@@ -206,14 +204,16 @@ __device__ __forceinline__ bool decode_unit(const Args& a, int u, Unit& w) {
         while (mt + 1 < a.gm && a.mcum[mt + 1] <= tile) ++mt;
         nt = tile - a.mcum[mt];
     } else {
-        // bands of RASTER_ROWS row tiles, column by column inside a band: the
-        // units in flight at one time (one per SM) cover about 8 x 19 tiles and
-        // share their A and B digit panels in L2, instead of one or two row
-        // tiles against every column panel
-        const int band = tile / (RASTER_ROWS * a.gn);
-        const int in = tile - band * RASTER_ROWS * a.gn;
-        const int rows = min(RASTER_ROWS, a.gm - band * RASTER_ROWS);
-        mt = band * RASTER_ROWS + in % rows;
+        // bands of a.band row tiles, column by column inside a band (a.band = 1:
+        // row by row).  With bands of 8 the units in flight at one time (one per
+        // SM) cover about 8 x 19 tiles and share their A and B digit panels in
+        // L2; row by row they cover one or two row tiles against every column
+        // panel.  Which is faster depends on the shape (a triangular operand
+        // makes the tiles' K extents uneven): the autotuner chooses.
+        const int band = tile / (a.band * a.gn);
+        const int in = tile - band * a.band * a.gn;
+        const int rows = min(a.band, a.gm - band * a.band);
+        mt = band * a.band + in % rows;
         nt = in / rows;
     }
     w.m0 = mt * TM;
@@ -1009,7 +1009,7 @@ size_t workspace_bytes(int M, int N, int K, int S) {
 }
 
 template <int S, int TN, int STG>
-int gemm_s(cudaStream_t s, const Gemm64& g, void* ws, int* err, long long epi_wait, int occupancy) {
+int gemm_s(cudaStream_t s, const Gemm64& g, void* ws, int* err, long long epi_wait, int occupancy, int band) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return BTA_OK;
     if (g.M > MAX_MT * TM) return BTA_ERR_ARG;
     const int nb = g.batch;
@@ -1066,6 +1066,7 @@ int gemm_s(cudaStream_t s, const Gemm64& g, void* ws, int* err, long long epi_wa
     if (Cfg<S, TN>::INT_ACC) ksplit = std::max<long long>(ksplit, (nchunks + INT_MAX_CHUNKS - 1) / INT_MAX_CHUNKS);
     if (base * ksplit > 0x7FFFFFFFLL) return BTA_ERR_ARG;
     a.ksplit = (int)ksplit;
+    a.band = std::max(1, std::min(band, MAX_MT));
     a.units = (int)(base * ksplit);
     // with a K split the parts add into C, which must hold beta Cin first;
     // otherwise the epilogue reads beta Cin itself
@@ -1109,14 +1110,15 @@ int ozaki_max_rows() { return oz::MAX_MT * oz::TM; }
 // C = beta Cin + alpha op(A) op(B) through the digit-split tensor-core path
 // with 5 or 7 digit slices.  ws: device workspace of batch *
 // ozaki_workspace_bytes(M, N, K, slices); err: device int; epi_wait: wait
-// limit (cycles) of the epilogue's accumulator hand-off, <= 0 for the default.
+// limit (cycles) of the epilogue's accumulator hand-off, <= 0 for the default;
+// band: row tiles per band of the tile order (1: row by row).
 int ozaki_gemm(cudaStream_t s, const Gemm64& g, void* ws, int* err, int slices, long long epi_wait, int tile,
-               int occupancy) {
+               int occupancy, int band) {
     using namespace oz;
-    if (slices == 7) return gemm_s<7, 64, 2>(s, g, ws, err, epi_wait, occupancy);
+    if (slices == 7) return gemm_s<7, 64, 2>(s, g, ws, err, epi_wait, occupancy, band);
     if (slices == 5)
-        return tile == 1 ? gemm_s<5, 64, 3>(s, g, ws, err, epi_wait, occupancy)
-                         : gemm_s<5, 96, 2>(s, g, ws, err, epi_wait, occupancy);
+        return tile == 1 ? gemm_s<5, 64, 3>(s, g, ws, err, epi_wait, occupancy, band)
+                         : gemm_s<5, 96, 2>(s, g, ws, err, epi_wait, occupancy, band);
     return BTA_ERR_ARG;
 }
 
@@ -1147,7 +1149,8 @@ int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
         // the accumulators, so that a test can make it run out
         long long epi_wait = ex->epi_wait;
         if (const char* e = std::getenv("BTA_OZ_EPI_WAIT")) epi_wait = std::atoll(e);
-        return ozaki_gemm(s, g, ex->ws, ex->err, ex->slices, epi_wait, ex->tile, ex->occupancy);
+        const int band = (g.shA != 0 || g.shB != 0) ? ex->band_tri : ex->band_gen;
+        return ozaki_gemm(s, g, ex->ws, ex->err, ex->slices, epi_wait, ex->tile, ex->occupancy, band);
     }
     // below the tensor-core threshold: square-ish products of the diagonal
     // recursion in double-float on the FP32 pipe, thin or tiny ones in FP64

@@ -14,6 +14,10 @@
 //               digits 128 x 96 with 2 TMA stages or 128 x 64 with 3; for
 //               49-bit digits 128 x 64 with 2) x the waves of the persistent
 //               grid below which it splits K (1, 2)
+//   3. mixed only: the tile order of the split product (row tiles per band:
+//      1, 4, 8, 16), separately for products with a triangular operand (timed
+//      on B X^T with X = L^{-1} lower, as in L_{i+1,i} = B_i X_i^T) and for
+//      general ones (timed on a dense product, as in Sigma_{i+1,i+1} G_i)
 // The timed matrices are synthetic SPD blocks written into the first
 // diagonal blocks of every matrix of the context (their contents are lost).
 
@@ -148,8 +152,6 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
             ppick = c;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     ctx->exec.tile = ppick.tile;
     ctx->exec.occupancy = ppick.occ;
     ctx->exec.fp64_ctas = ppick.ctas;
@@ -158,6 +160,50 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
         ctx->fork->ex2.occupancy = ppick.occ;
         ctx->fork->ex2.fp64_ctas = ppick.ctas;
     }
+
+    // ---- 3. tile order of the split products (mixed precision only)
+    if (rc == BTA_OK && ctx->precision != BTA_FP64) {
+        for (int tri = 1; tri >= 0 && rc == BTA_OK; --tri) {
+            Gemm64 h{};
+            h.M = b; h.N = b; h.K = b;
+            h.A = ctx->Q.D; h.lda = b; h.sA = ctx->Q.sD;
+            if (tri) {
+                // C = A X^T with X the lower inverse factor of the chain stage
+                h.B = ctx->Linv; h.ldb = b; h.tb = 1; h.shB = 2; h.sB = ctx->sLinv;
+            } else {
+                h.B = ctx->Q.D; h.ldb = b; h.sB = ctx->Q.sD;
+            }
+            h.C = ctx->L.D; h.ldc = b; h.sC = ctx->L.sD; h.alpha = 1.0;
+            h.batch = nm;
+            float bbest = -1.f;
+            int bpick = tri ? ctx->exec.band_tri : ctx->exec.band_gen;
+            for (int band : {1, 4, 8, 16}) {
+                int& slot = tri ? ctx->exec.band_tri : ctx->exec.band_gen;
+                slot = band;
+                if ((rc = gemm_exec(&ctx->exec, s, h)) != BTA_OK) break;
+                if (cudaEventRecord(e0, s) != cudaSuccess) { rc = BTA_ERR_CUDA; break; }
+                for (int r = 0; r < reps && rc == BTA_OK; ++r) rc = gemm_exec(&ctx->exec, s, h);
+                if (rc != BTA_OK) break;
+                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = BTA_ERR_CUDA;
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (bbest < 0.f || ms < bbest) {
+                    bbest = ms;
+                    bpick = band;
+                }
+            }
+            (tri ? ctx->exec.band_tri : ctx->exec.band_gen) = bpick;
+        }
+        if (ctx->fork) {
+            ctx->fork->ex2.band_tri = ctx->exec.band_tri;
+            ctx->fork->ex2.band_gen = ctx->exec.band_gen;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     if (rc != BTA_OK) return rc;
     BTA_TRY(bta_sync(ctx));
     chosen[0] = pick.leaf;
@@ -166,5 +212,7 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
     chosen[3] = ppick.tile;
     chosen[4] = ppick.occ;
     chosen[5] = ppick.ctas;
+    chosen[6] = ctx->exec.band_tri;
+    chosen[7] = ctx->exec.band_gen;
     return BTA_OK;
 }
