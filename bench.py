@@ -44,6 +44,7 @@ L2_BYTES = 129e6
 CONFIG_NAME = "c5"
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_hi": 2}
 SLICES = {"mixed": 5, "mixed_hi": 7}
+DEFAULT_BAND_TRI = 1          # tile order of the triangular-operand split products without autotuning
 FP64_COMPARE_STEPS = 2        # timed FP64 steps (after one warm-up) of the mixed-precision line
 CPU_SAMPLE_BLOCKS = 2         # time blocks of the oracle sample
 
@@ -333,10 +334,12 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- GPU measurement
 
-def _roofline(precision_name, prof, p, B, fp64_peak):
+def _roofline(precision_name, prof, p, B, fp64_peak, tuned=None):
     """Roofline record of the dominant operation from the profiling events of
     the last timed step: the two b x b x b Schur-update products of every
-    factorisation step (batched over the step's matrices)."""
+    factorisation step (batched over the step's matrices).  The DRAM traffic
+    comes from a capture of the same launch shape and, for the split product,
+    the same tile order of its triangular-operand product (B X^T)."""
     prof_ms, prof_n, prof_flops = prof
     achieved = (prof_flops / (prof_ms / 1e3) / 1e12) if prof_ms > 0 else None
     shape = {"M": p.b, "N": p.b, "K": p.b, "batch": 2 * B}
@@ -353,6 +356,8 @@ def _roofline(precision_name, prof, p, B, fp64_peak):
         }
     S = SLICES[precision_name]
     pairs = S * (S + 1) // 2
+    keys = bta.BtaContext.AUTOTUNE_KEYS
+    band_tri = DEFAULT_BAND_TRI if tuned is None else int(tuned[keys.index("split_band_triangular")])
     tensor = pairs * achieved if achieved else None
     return {
         "bound": "tensor", "kernel": f"ozaki split product ({S}-slice digit split + tcgen05 bf16 kernel, {pairs} "
@@ -360,7 +365,7 @@ def _roofline(precision_name, prof, p, B, fp64_peak):
         "achieved": tensor, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": (tensor / BF16_PEAK_TFLOPS) if tensor else None,
         "achieved_fp64_equivalent": achieved,
-        "traffic": traffic_record("ozaki_bxbxb", dict(shape, slices=S)),
+        "traffic": traffic_record("ozaki_bxbxb", dict(shape, slices=S, band_tri=band_tri)),
         "launches_timed": prof_n, "flops_per_launch": (prof_flops / prof_n) if prof_n else None,
         "peak_source": BF16_PEAK_SOURCE,
     }
@@ -535,7 +540,7 @@ def run_ours(args):
 
     fp64_peak = {"dfma": bta.bta_fp64_peak(False), "dmma": bta.bta_fp64_peak(True)}
     r = measure(args, args.precision, args.warmup, args.steps, args.e2e_steps, dist, rank, world, local)
-    r["roofline"] = _roofline(args.precision, r["prof"], r["problem"], r["B"], fp64_peak)
+    r["roofline"] = _roofline(args.precision, r["prof"], r["problem"], r["B"], fp64_peak, r["tuned"])
     cmp = None
     if args.precision != "fp64" and not args.no_compare:
         # the FP64 path at the theta of the last timed mixed step (one warm-up,
