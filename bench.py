@@ -356,6 +356,7 @@ def _roofline(precision_name, prof, p, B, fp64_peak, tuned=None):
         }
     S = SLICES[precision_name]
     pairs = S * (S + 1) // 2
+    from paper_2507_06938_gb300 import bta
     keys = bta.BtaContext.AUTOTUNE_KEYS
     band_tri = DEFAULT_BAND_TRI if tuned is None else int(tuned[keys.index("split_band_triangular")])
     tensor = pairs * achieved if achieved else None

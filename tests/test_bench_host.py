@@ -70,3 +70,24 @@ def test_errors_against_reference():
     assert list(e["sigma_block_rel"]) == ["Q_p D0"]
     # gradient error relative to max(|g_k|, 1e-3 |g|_inf): the third entry's scale is 2e-3
     assert abs(e["grad_rel_max"] - 1e-6 / 2e-3) < 1e-12
+
+
+def test_roofline_records_of_both_precisions():
+    """The roofline record from the profiling events: achieved rate, the
+    measured peak it divides by, and the traffic lookup keyed on the launch
+    shape and, for the split product, the tuned tile order."""
+    import bench
+    import synth
+    from paper_2507_06938_gb300 import bta
+    p = synth.problem_from_config("c5p")
+    prof = (10.0, 2, 2 * 4.32e11)            # ms, launches, nominal flops
+    peak = {"dfma": 1.25, "dmma": 1.1}
+    r = bench._roofline("fp64", prof, p, 1, peak)
+    assert r["bound"] == "alu" and abs(r["achieved"] - 86.4) < 1e-9 and r["peak"] == 1.25
+    tuned = (32, 64, 256, 0, 1, 2, 1, 8)
+    assert len(tuned) == len(bta.BtaContext.AUTOTUNE_KEYS)
+    r = bench._roofline("mixed_hi", prof, p, 1, peak, tuned)
+    assert r["bound"] == "tensor" and abs(r["achieved_fp64_equivalent"] - 86.4) < 1e-9
+    assert abs(r["achieved"] - 28 * 86.4) < 1e-6 and r["frac"] == r["achieved"] / bench.BF16_PEAK_TFLOPS
+    r2 = bench._roofline("mixed_hi", prof, p, 1, peak, None)
+    assert r2["achieved"] == r["achieved"]
