@@ -192,6 +192,13 @@ struct Unit {
 };
 
 // Decode work unit u; returns false when the unit has no K blocks.
+// The i-th unit of CTA `cta` in a grid of g CTAs: the units go out in waves
+// of g, every second wave in reverse CTA order, so that a CTA that drew a
+// cheap unit (a short K extent under a triangular operand) draws a dear one
+// next and the CTAs' totals stay even.  Every role of a CTA walks the same
+// sequence.
+__device__ __forceinline__ int unit_of(int i, int cta, int g) { return i * g + ((i & 1) ? g - 1 - cta : cta); }
+
 template <int TN>
 __device__ __forceinline__ bool decode_unit(const Args& a, int u, Unit& w) {
     const int kpart = u % a.ksplit;
@@ -477,9 +484,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) {
             // ------------------------------------------------------------ TMA producer
             int it = 0;
-            for (int u = blockIdx.x; u < a.units && !*abort_flag; u += gridDim.x) {
+            for (int wv = 0; wv * (int)gridDim.x < a.units && !*abort_flag; ++wv) {
+                const int u = unit_of(wv, blockIdx.x, gridDim.x);
                 Unit w;
-                if (!decode_unit<TN>(a, u, w)) continue;
+                if (u >= a.units || !decode_unit<TN>(a, u, w)) continue;
                 const int kb0 = w.kbl + w.c0 * KB_PER_CHUNK;
                 const int kb1 = min(w.kbh, w.kbl + w.c1 * KB_PER_CHUNK);
                 const int kb_last = w.kbl + (w.c1 - 1) * KB_PER_CHUNK;
@@ -521,9 +529,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             // ------------------------------------------------------------ MMA issuer
             int it = 0, nA = 0, nB = 0;
             bool ok = true;
-            for (int u = blockIdx.x; ok && u < a.units && !*abort_flag; u += gridDim.x) {
+            for (int wv = 0; ok && wv * (int)gridDim.x < a.units && !*abort_flag; ++wv) {
+                const int u = unit_of(wv, blockIdx.x, gridDim.x);
                 Unit w;
-                if (!decode_unit<TN>(a, u, w)) continue;
+                if (u >= a.units || !decode_unit<TN>(a, u, w)) continue;
                 for (int c = w.c0; ok && c < w.c1; ++c) {
                     const int kb0 = w.kbl + c * KB_PER_CHUNK, kb1 = min(w.kbh, kb0 + KB_PER_CHUNK);
                     const bool resetA = ((c - w.c0) & 1) == 0;
@@ -599,7 +608,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         long long acc[CF::INT_ACC ? EPI_COLS : 1];
         int nA = 0, nB = 0;
         bool ok = true;
-        for (int u = blockIdx.x; ok && u < a.units; u += gridDim.x) {
+        for (int wv = 0; ok && wv * (int)gridDim.x < a.units; ++wv) {
+            const int u = unit_of(wv, blockIdx.x, gridDim.x);
+            if (u >= a.units) continue;
             Unit w;
             // a unit without K blocks still writes beta Cin when there is no K split
             if (!decode_unit<TN>(a, u, w) && (a.ksplit > 1 || a.inplace)) continue;
