@@ -44,7 +44,7 @@ L2_BYTES = 129e6
 CONFIG_NAME = "c5"
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_hi": 2}
 SLICES = {"mixed": 5, "mixed_hi": 7}
-DEFAULT_BAND_TRI = 1          # tile order of the triangular-operand split products without autotuning
+DEFAULT_BAND = 1              # tile order of the split products' Schur updates without autotuning
 FP64_COMPARE_STEPS = 2        # timed FP64 steps (after one warm-up) of the mixed-precision line
 CPU_SAMPLE_BLOCKS = 2         # time blocks of the oracle sample
 
@@ -339,7 +339,8 @@ def _roofline(precision_name, prof, p, B, fp64_peak, tuned=None):
     the last timed step: the two b x b x b Schur-update products of every
     factorisation step (batched over the step's matrices).  The DRAM traffic
     comes from a capture of the same launch shape and, for the split product,
-    the same tile order of its triangular-operand product (B X^T)."""
+    the same tile orders of its triangular-operand product (B X^T) and its
+    lower-triangle update (L L^T)."""
     prof_ms, prof_n, prof_flops = prof
     achieved = (prof_flops / (prof_ms / 1e3) / 1e12) if prof_ms > 0 else None
     shape = {"M": p.b, "N": p.b, "K": p.b, "batch": 2 * B}
@@ -358,7 +359,8 @@ def _roofline(precision_name, prof, p, B, fp64_peak, tuned=None):
     pairs = S * (S + 1) // 2
     from paper_2507_06938_gb300 import bta
     keys = bta.BtaContext.AUTOTUNE_KEYS
-    band_tri = DEFAULT_BAND_TRI if tuned is None else int(tuned[keys.index("split_band_triangular")])
+    band_tri = DEFAULT_BAND if tuned is None else int(tuned[keys.index("split_band_triangular")])
+    band_low = DEFAULT_BAND if tuned is None else int(tuned[keys.index("split_band_lower")])
     tensor = pairs * achieved if achieved else None
     return {
         "bound": "tensor", "kernel": f"ozaki split product ({S}-slice digit split + tcgen05 bf16 kernel, {pairs} "
@@ -366,7 +368,7 @@ def _roofline(precision_name, prof, p, B, fp64_peak, tuned=None):
         "achieved": tensor, "peak": BF16_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": (tensor / BF16_PEAK_TFLOPS) if tensor else None,
         "achieved_fp64_equivalent": achieved,
-        "traffic": traffic_record("ozaki_bxbxb", dict(shape, slices=S, band_tri=band_tri)),
+        "traffic": traffic_record("ozaki_bxbxb", dict(shape, slices=S, band_tri=band_tri, band_low=band_low)),
         "launches_timed": prof_n, "flops_per_launch": (prof_flops / prof_n) if prof_n else None,
         "peak_source": BF16_PEAK_SOURCE,
     }

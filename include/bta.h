@@ -431,13 +431,13 @@ int bta_profile_phases(bta_ctx_t ctx, double* ms_out, int count);
  *   the persistent grid below which it splits K (1, 2), in FP64 the CTAs per
  *   SM of the DFMA GEMM's K split (1, 2, 4); then in mixed precision the
  *   tile order of the split product (row tiles per band: 1, 4, 8, 16),
- *   timed separately on a product with a triangular operand (B X^T) and on a
- *   general one.
+ *   timed separately on a product with a triangular operand (B X^T), on a
+ *   general one and on a lower-triangle update.
  * Each candidate runs once untimed and `reps` (>= 1) times timed.  The
- * chosen values are written to chosen[0..7] (host: leaf, double-float leaf,
+ * chosen values are written to chosen[0..8] (host: leaf, double-float leaf,
  * tensor threshold, tile, waves, FP64 CTAs per SM, band of triangular-operand
- * products, band of general products) and used by every later call on the
- * context.  The first diagonal block of every matrix is
+ * products, band of general products, band of lower-triangle updates) and
+ * used by every later call on the context.  The first diagonal block of every matrix is
  * overwritten with a synthetic SPD block: call it before assembling, or
  * assemble again afterwards.  Synchronises the context's stream.  Errors:
  * BTA_ERR_ARG (null pointers, reps < 1), CUDA errors. */

@@ -276,7 +276,7 @@ class BtaContext:
         _check(lib().bta_selinv_diag(self.handle, which, _ptr(out)), "bta_selinv_diag")
 
     AUTOTUNE_KEYS = ("fp64_leaf", "df32_leaf", "tensor_min_dim", "split_tile", "split_waves", "fp64_ctas_per_sm",
-                     "split_band_triangular", "split_band_general")
+                     "split_band_triangular", "split_band_general", "split_band_lower")
 
     def autotune(self, reps: int = 2):
         """bta_autotune: time the launch-shape candidates of the diagonal chain

@@ -101,9 +101,11 @@ struct GemmExec {
     int occupancy = 1; // waves of the persistent split-product grid before a K split (autotuned)
     int fp64_ctas = 2; // CTAs per SM the FP64 GEMM aims for through its K split (autotuned)
     // row tiles per band of the split product's tile order, for products with a
-    // triangular operand and for general ones (autotuned; 1 = row by row)
+    // triangular operand, for general ones and for lower-triangle outputs
+    // (autotuned; 1 = row by row)
     int band_tri = 1;
     int band_gen = 8;
+    int band_low = 1;
 };
 
 // Side stream, events and executor for the products of the recursive

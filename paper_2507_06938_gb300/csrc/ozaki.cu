@@ -207,9 +207,34 @@ __device__ __forceinline__ bool decode_unit(const Args& a, int u, Unit& w) {
     w.inst = u / a.tiles;
     int mt, nt;
     if (a.lowerC) {
-        mt = 0;
-        while (mt + 1 < a.gm && a.mcum[mt + 1] <= tile) ++mt;
-        nt = tile - a.mcum[mt];
+        // lower-triangle tiles: row tile mt holds column tiles nt with
+        // nt TN <= (mt + 1) TM - 1, so column nt starts at row tile
+        // floor(nt TN / TM) and the rows of a band that hold it are a suffix of
+        // the band.  The band (a.band row tiles) is found from the row-major
+        // counts, then walked column by column: first the columns every row of
+        // the band holds, then the partial ones near the diagonal.
+        int m = 0;
+        while (m + 1 < a.gm && a.mcum[m + 1] <= tile) ++m;
+        const int r0 = (m / a.band) * a.band, r1 = min(a.gm, r0 + a.band), rows = r1 - r0;
+        int idx = tile - a.mcum[r0];
+        const int nfull = a.mcum[r0 + 1] - a.mcum[r0];
+        if (idx < nfull * rows) {
+            mt = r0 + idx % rows;
+            nt = idx / rows;
+        } else {
+            idx -= nfull * rows;
+            nt = nfull;
+            mt = r1 - 1;
+            for (; nt < a.gn; ++nt) {
+                const int f = max(r0, (nt * TN) / TM);
+                const int here = f < r1 ? r1 - f : 0;
+                if (idx < here) {
+                    mt = f + idx;
+                    break;
+                }
+                idx -= here;
+            }
+        }
     } else {
         // bands of a.band row tiles, column by column inside a band (a.band = 1:
         // row by row).  With bands of 8 the units in flight at one time (one per
@@ -1160,7 +1185,7 @@ int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g) {
         // the accumulators, so that a test can make it run out
         long long epi_wait = ex->epi_wait;
         if (const char* e = std::getenv("BTA_OZ_EPI_WAIT")) epi_wait = std::atoll(e);
-        const int band = (g.shA != 0 || g.shB != 0) ? ex->band_tri : ex->band_gen;
+        const int band = g.lowerC ? ex->band_low : ((g.shA != 0 || g.shB != 0) ? ex->band_tri : ex->band_gen);
         return ozaki_gemm(s, g, ex->ws, ex->err, ex->slices, epi_wait, ex->tile, ex->occupancy, band);
     }
     // below the tensor-core threshold: square-ish products of the diagonal

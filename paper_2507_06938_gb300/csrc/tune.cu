@@ -16,8 +16,9 @@
 //               grid below which it splits K (1, 2)
 //   3. mixed only: the tile order of the split product (row tiles per band:
 //      1, 4, 8, 16), separately for products with a triangular operand (timed
-//      on B X^T with X = L^{-1} lower, as in L_{i+1,i} = B_i X_i^T) and for
-//      general ones (timed on a dense product, as in Sigma_{i+1,i+1} G_i)
+//      on B X^T with X = L^{-1} lower, as in L_{i+1,i} = B_i X_i^T), for
+//      general ones (timed on a dense product, as in Sigma_{i+1,i+1} G_i) and
+//      for lower-triangle outputs (timed on the update of stage 2)
 // The timed matrices are synthetic SPD blocks written into the first
 // diagonal blocks of every matrix of the context (their contents are lost).
 
@@ -163,7 +164,8 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
 
     // ---- 3. tile order of the split products (mixed precision only)
     if (rc == BTA_OK && ctx->precision != BTA_FP64) {
-        for (int tri = 1; tri >= 0 && rc == BTA_OK; --tri) {
+        for (int kind = 0; kind < 3 && rc == BTA_OK; ++kind) {
+            const bool tri = kind == 0;
             Gemm64 h{};
             h.M = b; h.N = b; h.K = b;
             h.A = ctx->Q.D; h.lda = b; h.sA = ctx->Q.sD;
@@ -175,10 +177,11 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
             }
             h.C = ctx->L.D; h.ldc = b; h.sC = ctx->L.sD; h.alpha = 1.0;
             h.batch = nm;
+            if (kind == 2) h = g;   // the lower-output update of stage 2
+            int& slot = kind == 0 ? ctx->exec.band_tri : (kind == 1 ? ctx->exec.band_gen : ctx->exec.band_low);
             float bbest = -1.f;
-            int bpick = tri ? ctx->exec.band_tri : ctx->exec.band_gen;
+            int bpick = slot;
             for (int band : {1, 4, 8, 16}) {
-                int& slot = tri ? ctx->exec.band_tri : ctx->exec.band_gen;
                 slot = band;
                 if ((rc = gemm_exec(&ctx->exec, s, h)) != BTA_OK) break;
                 if (cudaEventRecord(e0, s) != cudaSuccess) { rc = BTA_ERR_CUDA; break; }
@@ -195,11 +198,12 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
                     bpick = band;
                 }
             }
-            (tri ? ctx->exec.band_tri : ctx->exec.band_gen) = bpick;
+            slot = bpick;
         }
         if (ctx->fork) {
             ctx->fork->ex2.band_tri = ctx->exec.band_tri;
             ctx->fork->ex2.band_gen = ctx->exec.band_gen;
+            ctx->fork->ex2.band_low = ctx->exec.band_low;
         }
     }
     cudaEventDestroy(e0);
@@ -214,5 +218,6 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
     chosen[5] = ppick.ctas;
     chosen[6] = ctx->exec.band_tri;
     chosen[7] = ctx->exec.band_gen;
+    chosen[8] = ctx->exec.band_low;
     return BTA_OK;
 }

@@ -84,7 +84,7 @@ def test_roofline_records_of_both_precisions():
     peak = {"dfma": 1.25, "dmma": 1.1}
     r = bench._roofline("fp64", prof, p, 1, peak)
     assert r["bound"] == "alu" and abs(r["achieved"] - 86.4) < 1e-9 and r["peak"] == 1.25
-    tuned = (32, 64, 256, 0, 1, 2, 1, 8)
+    tuned = (32, 64, 256, 0, 1, 2, 1, 8, 1)
     assert len(tuned) == len(bta.BtaContext.AUTOTUNE_KEYS)
     r = bench._roofline("mixed_hi", prof, p, 1, peak, tuned)
     assert r["bound"] == "tensor" and abs(r["achieved_fp64_equivalent"] - 86.4) < 1e-9

@@ -122,13 +122,13 @@ def test_autotune_keeps_results_exact(precision):
     from oracle import fobj as ofobj
     p = problem("t_uni_mid")
     run = GpuRun(p, precision=precision, batch=2)
-    leaf, df_leaf, tmin, tile, waves, ctas, band_tri, band_gen = run.ctx.autotune(reps=1)
+    leaf, df_leaf, tmin, tile, waves, ctas, band_tri, band_gen, band_low = run.ctx.autotune(reps=1)
     if precision == 0:
         assert leaf in (16, 32, 64) and ctas in (1, 2, 4)
     else:
         assert df_leaf in (32, 64, 128) and tmin in (128, 256)
         assert tile in ((0, 1) if precision == 1 else (0,)) and waves in (1, 2)
-        assert band_tri in (1, 4, 8, 16) and band_gen in (1, 4, 8, 16)
+        assert band_tri in (1, 4, 8, 16) and band_gen in (1, 4, 8, 16) and band_low in (1, 4, 8, 16)
     th = np.stack([p.theta0, p.theta0 + 1e-3])
     f = torch.zeros(2, dtype=torch.float64, device="cuda")
     mu = torch.zeros((2, p.N), dtype=torch.float64, device="cuda")
