@@ -166,7 +166,17 @@ extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch,
         if (const char* e = std::getenv("BTA_DF_LEAF")) c->exec.df_leaf = std::atoi(e);
         c->exec.slices = precision == BTA_MIXED_HI ? 7 : 5;
         if (const char* e = std::getenv("BTA_OZ_TILE")) c->exec.tile = std::atoi(e) == 1 && c->exec.slices == 5 ? 1 : 0;
-        if (const char* e = std::getenv("BTA_OZ_BAND")) c->exec.band_tri = c->exec.band_gen = c->exec.band_low = std::max(1, std::atoi(e));
+        if (const char* e = std::getenv("BTA_OZ_BAND")) {
+            // test and profiling hook: one band for all products, or "tri,gen,low"
+            int v[3] = {0, 0, 0};
+            const int k = std::sscanf(e, "%d,%d,%d", &v[0], &v[1], &v[2]);
+            if (k == 1) v[1] = v[2] = v[0];
+            if (k == 1 || k == 3) {
+                c->exec.band_tri = std::max(1, v[0]);
+                c->exec.band_gen = std::max(1, v[1]);
+                c->exec.band_low = std::max(1, v[2]);
+            }
+        }
         const size_t wsb = (size_t)nm * ozaki_workspace_bytes(b, b, b, c->exec.slices);
         if (cudaMalloc(&c->exec.ws, wsb) != cudaSuccess) {
             c->exec.ws = nullptr;
