@@ -330,33 +330,51 @@ __global__ void symmetrize_kernel(double* A, long long lda, int n, long long sA)
 }
 
 // ---------------------------------------------------------------- GEMV (blockIdx.y = matrix)
-// y[m] = alpha sum_n op(A)[m][n] x[n] + beta yin[m]
-// Non-transposed: a CTA owns 32 rows; 8 warps split the columns; lanes read
-// consecutive rows (coalesced).  Transposed: a warp owns one output, lanes
-// stride down the stored column (coalesced), shuffle reduction.
-__global__ void __launch_bounds__(256) gemv_n_kernel(int M, int N, const double* A, long long lda, int sh,
-                                                     const double* x, double alpha, const double* yin,
-                                                     double beta, double* y, long long sA, long long sx,
-                                                     long long sy) {
-    __shared__ double part[8][33];
+// y[m] = alpha sum_n op(A)[m][n] x[n] + beta yin[m].  These are HBM-bound
+// (each element of A is read once), so what matters is enough loads in flight:
+//   non-transposed: a CTA of 32 warps owns 32 rows; lanes read consecutive rows
+//     (256-byte segments), warps split the columns, and each thread keeps four
+//     columns in flight with independent accumulators;
+//   transposed: a warp owns one output and its lanes stride down the stored
+//     column (coalesced), four loads in flight, shuffle reduction;
+//   short rows (non-transposed, M <= 16, the arrow rows R of a BTA matrix
+//     against a vector of length n b): one CTA of 1024 threads per matrix,
+//     each thread taking whole columns of M contiguous values;
+//   short columns (transposed, N <= 16, R^T x_t): one thread per output.
+constexpr int GV_WARPS = 32;
+constexpr int GV_SHORT = 16;
+
+__global__ void __launch_bounds__(32 * GV_WARPS) gemv_n_kernel(int M, int N, const double* A, long long lda,
+                                                              int sh, const double* x, double alpha,
+                                                              const double* yin, double beta, double* y,
+                                                              long long sA, long long sx, long long sy) {
+    __shared__ double part[GV_WARPS][33];
     A += blockIdx.y * sA;
     x += blockIdx.y * sx;
     y += blockIdx.y * sy;
     if (yin) yin += blockIdx.y * sy;
     const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
     const int m = blockIdx.x * 32 + lane;
-    double acc = 0.0;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     if (m < M) {
         int nb = 0, ne = N;
         if (sh == 1) ne = min(N, m + 1);
         if (sh == 2) nb = m;
-        for (int n = nb + w; n < ne; n += 8) acc = fma(A[m + (long long)n * lda], x[n], acc);
+        const double* Am = A + m;
+        int n = nb + w;
+        for (; n + 3 * GV_WARPS < ne; n += 4 * GV_WARPS) {
+            a0 = fma(Am[(long long)n * lda], x[n], a0);
+            a1 = fma(Am[(long long)(n + GV_WARPS) * lda], x[n + GV_WARPS], a1);
+            a2 = fma(Am[(long long)(n + 2 * GV_WARPS) * lda], x[n + 2 * GV_WARPS], a2);
+            a3 = fma(Am[(long long)(n + 3 * GV_WARPS) * lda], x[n + 3 * GV_WARPS], a3);
+        }
+        for (; n < ne; n += GV_WARPS) a0 = fma(Am[(long long)n * lda], x[n], a0);
     }
-    part[w][lane] = acc;
+    part[w][lane] = (a0 + a1) + (a2 + a3);
     __syncthreads();
     if (w == 0 && m < M) {
         double s = 0.0;
-        for (int q = 0; q < 8; ++q) s += part[q][lane];
+        for (int q = 0; q < GV_WARPS; ++q) s += part[q][lane];
         double v = alpha * s;
         if (beta != 0.0) v += beta * yin[m];
         y[m] = v;
@@ -379,14 +397,80 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(int M, int N, const double*
     if (sh == 1) ne = min(N, m + 1);
     if (sh == 2) nb = m;
     const double* col = A + (long long)m * lda;
-    double acc = 0.0;
-    for (int n = nb + lane; n < ne; n += 32) acc = fma(col[n], x[n], acc);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int n = nb + lane;
+    for (; n + 96 < ne; n += 128) {
+        a0 = fma(col[n], x[n], a0);
+        a1 = fma(col[n + 32], x[n + 32], a1);
+        a2 = fma(col[n + 64], x[n + 64], a2);
+        a3 = fma(col[n + 96], x[n + 96], a3);
+    }
+    for (; n < ne; n += 32) a0 = fma(col[n], x[n], a0);
+    double acc = (a0 + a1) + (a2 + a3);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) {
         double v = alpha * acc;
         if (beta != 0.0) v += beta * yin[m];
         y[m] = v;
     }
+}
+
+// M <= GV_SHORT rows, general op(A) shape only
+__global__ void __launch_bounds__(1024) gemv_short_n_kernel(int M, int N, const double* A, long long lda,
+                                                            const double* x, double alpha, const double* yin,
+                                                            double beta, double* y, long long sA, long long sx,
+                                                            long long sy) {
+    __shared__ double red[GV_SHORT][33];
+    A += blockIdx.y * sA;
+    x += blockIdx.y * sx;
+    y += blockIdx.y * sy;
+    if (yin) yin += blockIdx.y * sy;
+    const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+    double acc[GV_SHORT];
+#pragma unroll
+    for (int i = 0; i < GV_SHORT; ++i) acc[i] = 0.0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const double xn = x[n];
+        const double* c = A + (long long)n * lda;
+#pragma unroll
+        for (int i = 0; i < GV_SHORT; ++i)
+            if (i < M) acc[i] = fma(c[i], xn, acc[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < GV_SHORT; ++i) {
+        if (i >= M) break;
+        double v = acc[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[i][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < M) {
+        const int i = threadIdx.x;
+        double s = 0.0;
+        for (int q = 0; q < (int)(blockDim.x / 32); ++q) s += red[i][q];
+        double v = alpha * s;
+        if (beta != 0.0) v += beta * yin[i];
+        y[i] = v;
+    }
+}
+
+// N <= GV_SHORT columns of op(A) = A^T, general shape only
+__global__ void __launch_bounds__(256) gemv_short_t_kernel(int M, int N, const double* A, long long lda,
+                                                           const double* x, double alpha, const double* yin,
+                                                           double beta, double* y, long long sA, long long sx,
+                                                           long long sy) {
+    A += blockIdx.y * sA;
+    x += blockIdx.y * sx;
+    y += blockIdx.y * sy;
+    if (yin) yin += blockIdx.y * sy;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const double* r = A + (long long)m * lda;
+    double s = 0.0;
+    for (int n = 0; n < N; ++n) s = fma(r[n], x[n], s);
+    double v = alpha * s;
+    if (beta != 0.0) v += beta * yin[m];
+    y[m] = v;
 }
 
 // ---------------------------------------------------------------- reductions (blockIdx.y = matrix)
@@ -674,9 +758,15 @@ int gemv64(cudaStream_t s, int M, int N, const double* A, long long lda, int ta,
            double alpha, const double* yin, double beta, double* y, int batch, long long sA, long long sx,
            long long sy) {
     if (M <= 0 || batch <= 0) return BTA_OK;
-    if (!ta) {
+    if (batch > 65535) return BTA_ERR_ARG;
+    if (!ta && sh == 0 && M <= GV_SHORT && N >= 4096) {
+        gemv_short_n_kernel<<<dim3(1, batch), 1024, 0, s>>>(M, N, A, lda, x, alpha, yin, beta, y, sA, sx, sy);
+    } else if (ta && sh == 0 && N <= GV_SHORT && M >= 4096) {
+        dim3 grid((M + 255) / 256, batch);
+        gemv_short_t_kernel<<<grid, 256, 0, s>>>(M, N, A, lda, x, alpha, yin, beta, y, sA, sx, sy);
+    } else if (!ta) {
         dim3 grid((M + 31) / 32, batch);
-        gemv_n_kernel<<<grid, 256, 0, s>>>(M, N, A, lda, sh, x, alpha, yin, beta, y, sA, sx, sy);
+        gemv_n_kernel<<<grid, 32 * GV_WARPS, 0, s>>>(M, N, A, lda, sh, x, alpha, yin, beta, y, sA, sx, sy);
     } else {
         dim3 grid((M + 7) / 8, batch);
         gemv_t_kernel<<<grid, 256, 0, s>>>(M, N, A, lda, sh, x, alpha, yin, beta, y, sA, sx, sy);
