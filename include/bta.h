@@ -144,6 +144,12 @@ int bta_create(int n, int b, int a, int precision, void* stream, bta_ctx_t* out)
  * Eq. 10 and the two matrices of each are independent, Sections IV-D.1 and
  * IV-D.2).  bta_create is bta_create_batched with batch = 1. */
 int bta_create_batched(int n, int b, int a, int precision, int batch, void* stream, bta_ctx_t* out);
+/* bta_create_ex -- bta_create_batched with creation flags: 0, or
+ * BTA_CREATE_LOW_MEMORY to allocate the low-memory layout of
+ * bta_set_low_memory from the start (the default layout of the same batch
+ * may not fit at all).  BTA_ERR_ARG for unknown flags. */
+#define BTA_CREATE_LOW_MEMORY 1
+int bta_create_ex(int n, int b, int a, int precision, int batch, int flags, void* stream, bta_ctx_t* out);
 int bta_batch_size(bta_ctx_t ctx, int* batch);
 int bta_destroy(bta_ctx_t ctx);
 
@@ -203,6 +209,32 @@ int bta_factor(bta_ctx_t ctx, int which);
  * layout, or has no storage left and must be destroyed), BTA_ERR_CUDA.
  */
 int bta_set_time_partitions(bta_ctx_t ctx, int P);
+
+/*
+ * bta_set_low_memory -- keep this context's matrices in a layout that needs
+ * about 0.6 of the default device memory at large n, so that more theta
+ * points fit in one batch of the largest models (Section III-A's factor,
+ * selected inversion and solve, unchanged in arithmetic):
+ *   - the inverse diagonal factor blocks L_ii^{-1} replace L_ii in the
+ *     factor's diagonal blocks (the log-determinant is summed while the blocks
+ *     are factored), L_tt^{-1} taking a spare block slot;
+ *   - the selected inverse overwrites the factor.
+ * Per matrix that is Q (n diagonal, n - 1 off-diagonal blocks), the factor
+ * (n + 1 and n + 1) and one b x b buffer, against Q, the factor, Sigma and n
+ * inverse blocks.  Consequences: after bta_selinv, bta_selinv_batch or
+ * bta_fobj_grad the matrix counts as not factored (bta_solve, bta_logdet and
+ * bta_selinv return BTA_ERR_STATE until the next factorisation), and the
+ * factor's diagonal blocks read through bta_block_ptr hold L_ii^{-1}
+ * (BTA_STORE_L, BTA_STORE_LINV and, after the selected inversion,
+ * BTA_STORE_SIGMA name the same memory).  enable = 0 restores the default
+ * layout (bta_create_ex with BTA_CREATE_LOW_MEMORY starts in the low-memory
+ * one).  Assembled Q matrices are kept; factors, selected inverses and a
+ * captured f_obj graph are dropped.  BTA_ERR_STATE with time partitions
+ * (P > 1); BTA_ERR_OOM if the new layout cannot be allocated (the context
+ * then keeps the default one, or has no factor storage and must be
+ * destroyed).  Synchronises the device.
+ */
+int bta_set_low_memory(bta_ctx_t ctx, int enable);
 
 /* bta_factor_batch -- bta_factor of every slot's matrix of kind BTA_QP or
  * BTA_QC in one pass (all matrices in the same launches). */
@@ -424,7 +456,7 @@ int bta_profile_phases(bta_ctx_t ctx, double* ms_out, int count);
  * operations; the sequential diagonal chain and the b x b x b products):
  *   the FP64 leaf order (16, 32, 64), or in mixed precision the
  *   double-float leaf order (32, 64, 128) and the smallest product dimension
- *   sent to the tensor cores (128, 256), timed on the diagonal-block chain;
+ *   sent to the tensor cores (128, 256, 384, 512), timed on the diagonal-block chain;
  *   then, timed on a batched b x b x b lower update, in mixed precision the
  *   split-product tile (35-bit digits: 0 = 128 x 96 tiles with 2 TMA stages,
  *   1 = 128 x 64 with 3; 49-bit digits: 0 = 128 x 64 with 2) and the waves of

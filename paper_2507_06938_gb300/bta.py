@@ -28,6 +28,7 @@ BTA_LIK_GAUSSIAN, BTA_LIK_POISSON = 0, 1
 BTA_BLK_D, BTA_BLK_B, BTA_BLK_R, BTA_BLK_T = 0, 1, 2, 3
 BTA_STORE_Q, BTA_STORE_L, BTA_STORE_SIGMA, BTA_STORE_LINV = 0, 1, 2, 3
 BTA_PHASES = 5
+BTA_CREATE_LOW_MEMORY = 1
 PHASE_NAMES = ("assemble", "factor_logdet", "solve_f", "selinv", "adjoint")
 
 
@@ -67,6 +68,7 @@ def lib():
         "bta_model_dims": (ip, [vp, C.POINTER(ip), C.POINTER(ip), C.POINTER(ip), C.POINTER(ip)]),
         "bta_create": (ip, [ip, ip, ip, ip, vp, C.POINTER(vp)]),
         "bta_create_batched": (ip, [ip, ip, ip, ip, ip, vp, C.POINTER(vp)]),
+        "bta_create_ex": (ip, [ip, ip, ip, ip, ip, ip, vp, C.POINTER(vp)]),
         "bta_batch_size": (ip, [vp, C.POINTER(ip)]),
         "bta_factor_batch": (ip, [vp, ip]),
         "bta_selinv_batch": (ip, [vp, ip]),
@@ -97,6 +99,7 @@ def lib():
         "bta_fobj_residual": (ip, [vp, vp]),
         "bta_fobj_laplace": (ip, [vp, vp, vp, ip, ip, ip, vp, vp, vp]),
         "bta_set_time_partitions": (ip, [vp, ip]),
+        "bta_set_low_memory": (ip, [vp, ip]),
         "bta_fobj_grad_host": (ip, [vp, vp, vp, ip, vp, vp, vp]),
         "bta_fp64_peak": (ip, [ip, C.POINTER(dp)]),
         "bta_flops_factor": (dp, [ip, ip, ip]),
@@ -120,7 +123,7 @@ def exported_symbols():
             "bta_create_batched", "bta_batch_size", "bta_factor_batch", "bta_selinv_batch",
             "bta_last_error_matrix", "bta_fobj_grad", "bta_autotune", "bta_fobj_eval_multi",
             "bta_fobj_residual", "bta_fp64_peak", "bta_fobj_grad_host", "bta_fobj_laplace",
-            "bta_set_time_partitions", "bta_profile_phases"]
+            "bta_set_time_partitions", "bta_profile_phases", "bta_set_low_memory", "bta_create_ex"]
 
 
 def _check(code: int, where: str):
@@ -211,14 +214,16 @@ class BtaContext:
     """bta_ctx_t: device storage of Q_p and Q_c, their factors and selected
     inverses, bound to a CUDA stream."""
 
-    def __init__(self, n: int, b: int, a: int, precision: int = BTA_FP64, stream=None, batch: int = 1):
+    def __init__(self, n: int, b: int, a: int, precision: int = BTA_FP64, stream=None, batch: int = 1,
+                 low_memory: bool = False):
         L = lib()
         import torch
         # the torch stream the context runs on (the current one when none is given)
         self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
-        _check(L.bta_create_batched(n, b, a, precision, batch, C.c_void_p(_stream_handle(stream)), C.byref(h)),
-               "bta_create_batched")
+        flags = BTA_CREATE_LOW_MEMORY if low_memory else 0
+        _check(L.bta_create_ex(n, b, a, precision, batch, flags, C.c_void_p(_stream_handle(stream)), C.byref(h)),
+               "bta_create_ex")
         self.handle = h
         self.n, self.b, self.a, self.batch = n, b, a, batch
         self.N = n * b + a
@@ -257,6 +262,12 @@ class BtaContext:
         Needs n - (P - 1) ceil((n + 1) / P) >= 1 and a <= b; keeps assembled
         matrices, drops factors."""
         _check(lib().bta_set_time_partitions(self.handle, int(P)), "bta_set_time_partitions")
+
+    def set_low_memory(self, enable: bool):
+        """bta_set_low_memory: inverse diagonal blocks in the factor's diagonal
+        slots and the selected inverse over the factor (about 0.6 of the
+        default memory at large n); a selected inversion consumes the factor."""
+        _check(lib().bta_set_low_memory(self.handle, 1 if enable else 0), "bta_set_low_memory")
 
     def factor_batch(self, kind: int):
         _check(lib().bta_factor_batch(self.handle, kind), "bta_factor_batch")

@@ -103,14 +103,48 @@ int store_alloc(BtaStore& M, int nmat, int n, int b, int a, int blk, int lead) {
 void store_release(BtaStore& M) { store_free(M); }
 
 int ensure_sigma(bta_ctx_t ctx) {
+    if (ctx->lowmem) {
+        ctx->S = ctx->L;   // the selected inverse overwrites the factor
+        return BTA_OK;
+    }
     if (ctx->S.D) return BTA_OK;
     int rc = store_alloc(ctx->S, ctx->nmat, ctx->n, ctx->b, ctx->a, ctx->blk, ctx->blk != ctx->n ? 1 : 0);
     if (rc != BTA_OK) store_free(ctx->S);
     return rc;
 }
 
-extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch, void* stream, bta_ctx_t* out) {
-    if (!out || n < 1 || b < 1 || a < 0 || batch < 1 ||
+// The default factor storage: L blocks, and the inverse diagonal blocks apart.
+static int alloc_default_factor(bta_ctx_t c) {
+    const int n = c->n, b = c->b, a = c->a, nm = c->nmat;
+    const long long bb = (long long)b * b;
+    BTA_TRY(store_alloc(c->L, nm, n, b, a, n, 0));
+    c->sLinv = n * bb + (long long)a * a;
+    c->tip_off = n * bb;
+    BTA_TRY(dalloc(&c->Linv, (size_t)nm * c->sLinv));
+    // the strict upper triangles of the inverse blocks are never written by the factor
+    BTA_CUDA_TRY(cudaMemset(c->Linv, 0, (size_t)nm * c->sLinv * sizeof(double)));
+    return BTA_OK;
+}
+
+// The low-memory factor storage: a spare diagonal slot per matrix for
+// L_tt^{-1}, the inverse blocks in the diagonal slots, one X buffer per matrix.
+static int alloc_low_factor(bta_ctx_t c) {
+    const int n = c->n, b = c->b, a = c->a, nm = c->nmat;
+    const long long bb = (long long)b * b;
+    BTA_TRY(store_alloc(c->L, nm, n, b, a, n + 1, 0));
+    BTA_TRY(dalloc(&c->xtmp, (size_t)nm * bb));
+    BTA_TRY(dalloc(&c->ldacc, (size_t)nm));
+    BTA_CUDA_TRY(cudaMemset(c->xtmp, 0, (size_t)nm * bb * sizeof(double)));
+    c->Linv = c->L.D;
+    c->sLinv = c->L.sD;
+    c->tip_off = n * bb;
+    c->lowmem = 1;
+    return BTA_OK;
+}
+
+extern "C" int bta_create_ex(int n, int b, int a, int precision, int batch, int flags, void* stream,
+                             bta_ctx_t* out) {
+    if (!out || n < 1 || b < 1 || a < 0 || batch < 1 || (flags & ~BTA_CREATE_LOW_MEMORY) != 0 ||
         (precision != BTA_FP64 && precision != BTA_MIXED && precision != BTA_MIXED_HI))
         return BTA_ERR_ARG;
     const bool mixed = precision != BTA_FP64;
@@ -126,6 +160,7 @@ extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch,
     c->aux = nullptr; c->ev_fork = nullptr; c->ev_join = nullptr;
     c->exec = GemmExec{};
     c->factored.assign(c->nmat, 0);
+    c->mu_valid.assign(c->batch, 0);
     int rc = BTA_OK;
     auto fail = [&](int r) { bta_destroy(c); return r; };
     if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess) return fail(BTA_ERR_CUDA);
@@ -136,11 +171,8 @@ extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch,
     c->blk = n;
     c->tip_off = (long long)n * bb;
     if ((rc = store_alloc(c->Q, nm, n, b, a, n, 0)) != BTA_OK) return fail(rc);
-    if ((rc = store_alloc(c->L, nm, n, b, a, n, 0)) != BTA_OK) return fail(rc);
-    c->sLinv = n * bb + (long long)a * a;
-    if ((rc = dalloc(&c->Linv, (size_t)nm * c->sLinv)) != BTA_OK) return fail(rc);
-    // the strict upper triangles of the inverse blocks are never written by the factor
-    if (cudaMemset(c->Linv, 0, (size_t)nm * c->sLinv * sizeof(double)) != cudaSuccess) return fail(BTA_ERR_CUDA);
+    rc = (flags & BTA_CREATE_LOW_MEMORY) ? alloc_low_factor(c) : alloc_default_factor(c);
+    if (rc != BTA_OK) return fail(rc);
     c->sWork = bb + bb / 2 + 2LL * b + 2LL * a * b + (long long)a * a + 64;
     if ((rc = dalloc(&c->work, (size_t)nm * c->sWork)) != BTA_OK) return fail(rc);
     if ((rc = dalloc(&c->vec, (size_t)VEC_ROWS * nm * c->N)) != BTA_OK) return fail(rc);
@@ -213,6 +245,10 @@ extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch,
     return BTA_OK;
 }
 
+extern "C" int bta_create_batched(int n, int b, int a, int precision, int batch, void* stream, bta_ctx_t* out) {
+    return bta_create_ex(n, b, a, precision, batch, 0, stream, out);
+}
+
 extern "C" int bta_create(int n, int b, int a, int precision, void* stream, bta_ctx_t* out) {
     return bta_create_batched(n, b, a, precision, 1, stream, out);
 }
@@ -243,6 +279,13 @@ extern "C" int bta_destroy(bta_ctx_t c) {
         c->fork = nullptr;
     }
     ptime_free(c);
+    if (c->lowmem) {
+        // S and Linv alias the factor's storage
+        c->S = BtaStore{};
+        c->Linv = nullptr;
+    }
+    for (double* p : {c->xtmp, c->ldacc})
+        if (p) cudaFree(p);
     store_free(c->Q);
     store_free(c->L);
     store_free(c->S);
@@ -457,4 +500,51 @@ extern "C" const char* bta_strerror(int code) {
         case BTA_ERR_STATE: return "call out of order";
         default: return "unknown error";
     }
+}
+
+// Switch between the default storage (factor, selected inverse and inverse
+// diagonal blocks apart) and the low-memory one (see bta.h).  Assembled Q
+// blocks are kept; factors and selected inverses are dropped.
+extern "C" int bta_set_low_memory(bta_ctx_t c, int enable) {
+    if (!c) return BTA_ERR_ARG;
+    enable = enable ? 1 : 0;
+    if (enable == c->lowmem) return BTA_OK;
+    if (c->tparts > 1) return BTA_ERR_STATE;
+    BTA_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    BTA_CUDA_TRY(cudaDeviceSynchronize());
+    if (c->fobj_graph) {
+        cudaGraphExecDestroy(c->fobj_graph);
+        c->fobj_graph = nullptr;
+        c->graph_calls = 1;
+    }
+    std::fill(c->factored.begin(), c->factored.end(), 0);
+    if (c->lowmem) {
+        c->S = BtaStore{};
+        c->Linv = nullptr;
+    } else {
+        store_free(c->S);
+        if (c->Linv) cudaFree(c->Linv);
+        c->Linv = nullptr;
+    }
+    store_free(c->L);
+    for (double** p : {&c->xtmp, &c->ldacc}) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+    c->lowmem = 0;
+    if (enable) {
+        const int rc = alloc_low_factor(c);
+        if (rc == BTA_OK) return BTA_OK;
+        // fall back to the default layout
+        c->lowmem = 0;
+        c->Linv = nullptr;
+        store_free(c->L);
+        for (double** p : {&c->xtmp, &c->ldacc}) {
+            if (*p) cudaFree(*p);
+            *p = nullptr;
+        }
+        const int rc2 = alloc_default_factor(c);
+        return rc2 == BTA_OK ? rc : rc2;
+    }
+    return alloc_default_factor(c);
 }

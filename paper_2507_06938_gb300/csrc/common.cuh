@@ -167,6 +167,7 @@ struct bta_ctx_s {
     int* oz_err = nullptr;   // device flag of the tensor-core GEMM (time-out)
     int refine = 0;          // refinement steps of the f_obj solve
     std::vector<int> factored;   // per storage index
+    std::vector<int> mu_valid;   // per slot: an f_obj evaluation has left mu (and b) there
     int leaf;                // leaf size of the recursive diagonal factorisation
     long long last_info = -1;
     int last_matrix = -1;
@@ -186,6 +187,12 @@ struct bta_ctx_s {
     double* hs_grad = nullptr;     // batch x dim_theta
     double* hs_var = nullptr;      // batch x N
     int hs_dim = 0;
+    // low-memory layout (bta_set_low_memory): the factor's D array has a spare
+    // slot per matrix, the inverse blocks X_i replace L_ii in it (Linv aliases
+    // L.D) and the selected inverse overwrites the factor (S aliases L)
+    int lowmem = 0;
+    double* xtmp = nullptr;   // nmat b^2: X of the block being factored, X_i copy of the selected inversion
+    double* ldacc = nullptr;  // nmat: 2 sum log diag(L_ii), accumulated while the blocks are factored
     // parallel-in-time path (bta_set_time_partitions): P > 1 time partitions
     int tparts = 1;
     struct PTimeStore* pts = nullptr;

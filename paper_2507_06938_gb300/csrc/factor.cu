@@ -16,6 +16,44 @@
 
 #include "common.cuh"
 
+namespace {
+
+// acc[m] (= or +=) 2 sum_k log D_m[k, k] of one diagonal factor block per
+// matrix (blockIdx.x = matrix): the log-determinant of the low-memory layout,
+// taken before X_i replaces L_ii
+__global__ void logdiag_acc_kernel(const double* D, int b, long long sD, double* acc, int first) {
+    __shared__ double red[32];
+    D += blockIdx.x * sD;
+    double v = 0.0;
+    for (int k = threadIdx.x; k < b; k += blockDim.x) v += log(D[k * (long long)(b + 1)]);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
+        acc[blockIdx.x] = (first ? 0.0 : acc[blockIdx.x]) + 2.0 * s;
+    }
+}
+
+// out[j] = acc[j] + 2 sum_k log T_j[k, k] (blockIdx.x = matrix)
+__global__ void logdet_tip_kernel(const double* acc, const double* T, int a, long long sT, double* out) {
+    __shared__ double red[32];
+    T += blockIdx.x * sT;
+    double v = 0.0;
+    for (int k = threadIdx.x; k < a; k += blockDim.x) v += log(T[k * (long long)(a + 1)]);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) s += red[w];
+        out[blockIdx.x] = acc[blockIdx.x] + 2.0 * s;
+    }
+}
+
+}  // namespace
+
 int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
     if (ctx->tparts > 1) return pfactor_impl(ctx, m0, cnt, s);
     const int n = ctx->n, b = ctx->b, a = ctx->a;
@@ -46,8 +84,21 @@ int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
     for (int i = 0; i < n; ++i) {
         double* Di = LD + i * bb;
         double* Xi = Linv + i * bb;
-        BTA_TRY(chol_inv64(s, Di, b, Xi, b, b, (long long)i * b, status, W, leaf, ex, cnt, L.sD, sX, sW, m0,
-                           ctx->batch, ctx->fork));
+        long long sXi = sX;
+        if (ctx->lowmem) {
+            // L_ii and X_i side by side in the D slot and the X buffer; the
+            // slot keeps X_i once the diagonal of L_ii is summed
+            double* Xw = ctx->xtmp + m0 * bb;
+            BTA_TRY(chol_inv64(s, Di, b, Xw, b, b, (long long)i * b, status, W, leaf, ex, cnt, L.sD, bb, sW, m0,
+                               ctx->batch, ctx->fork));
+            logdiag_acc_kernel<<<cnt, 256, 0, s>>>(Di, b, L.sD, ctx->ldacc + m0, i == 0 ? 1 : 0);
+            BTA_LAUNCH_CHECK();
+            BTA_TRY(copy_mat64(s, Xw, b, Di, b, b, b, 0, cnt, bb, L.sD));
+            sXi = L.sD;
+        } else {
+            BTA_TRY(chol_inv64(s, Di, b, Xi, b, b, (long long)i * b, status, W, leaf, ex, cnt, L.sD, sX, sW, m0,
+                               ctx->batch, ctx->fork));
+        }
         Gemm64 g{};
         if (i < n - 1) {
             // L_{i+1,i} = B_i X_i^T
@@ -56,7 +107,7 @@ int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
             g.A = QB + i * bb; g.lda = b;
             g.B = Xi; g.ldb = b; g.tb = 1; g.shB = 2;
             g.C = LB + i * bb; g.ldc = b; g.alpha = 1.0;
-            g.batch = cnt; g.sA = Q.sB; g.sB = sX; g.sC = L.sB;
+            g.batch = cnt; g.sA = Q.sB; g.sB = sXi; g.sC = L.sB;
             cudaEvent_t stop;
             BTA_TRY(prof_begin(ctx, s, (double)cnt * b * b * b, &stop));
             BTA_TRY(gemm_exec(ex, s, g));
@@ -89,7 +140,7 @@ int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
             g.A = Racc; g.lda = a;
             g.B = Xi; g.ldb = b; g.tb = 1; g.shB = 2;
             g.C = Lri; g.ldc = a; g.alpha = 1.0;
-            g.batch = cnt; g.sA = sW; g.sB = sX; g.sC = L.sR;
+            g.batch = cnt; g.sA = sW; g.sB = sXi; g.sC = L.sR;
             BTA_TRY(gemm64(as, g));
             if (i < n - 1) {
                 // Racc = R_{i+1} - L_{t,i} L_{i+1,i}^T
@@ -128,6 +179,12 @@ int factor_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
 int logdet_impl(bta_ctx_t ctx, int m0, int cnt, double* out, cudaStream_t s) {
     const int n = ctx->n, b = ctx->b, a = ctx->a;
     const BtaStore& L = ctx->L;
+    if (ctx->lowmem) {
+        // the diagonal blocks were summed while they were factored
+        logdet_tip_kernel<<<cnt, 32, 0, s>>>(ctx->ldacc + m0, L.T + m0 * L.sT, a, L.sT, out);
+        BTA_LAUNCH_CHECK();
+        return BTA_OK;
+    }
     // 2 sum log diag over the n diagonal blocks and the tip of every matrix
     double* part = ctx->red + (long long)m0 * ctx->red_chunks;
     return logdet_batch64(s, L.D + m0 * L.sD, b, b, n, (long long)b * b, L.sD, L.T + m0 * L.sT, a, L.sT, cnt, part,

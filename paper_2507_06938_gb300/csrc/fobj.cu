@@ -171,6 +171,7 @@ extern "C" int fobj_eval(bta_ctx_t ctx, bta_model_t m, const double* thetas_dev,
         } else {
             BTA_TRY(fobj_group(ctx, m, theta, cnt, f_out_dev + r0, s));
         }
+        for (int j = 0; j < cnt; ++j) ctx->mu_valid[j] = 1;
         if (mu_out_dev)
             BTA_CUDA_TRY(cudaMemcpyAsync(mu_out_dev + (long long)r0 * N, vec_row(ctx, VEC_MU, B),
                                          cnt * N * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -674,6 +674,7 @@ int pselinv_impl(bta_ctx_t c, int m0, int cnt, cudaStream_t s) {
 
 extern "C" int bta_set_time_partitions(bta_ctx_t ctx, int P) {
     if (!ctx || P < 1) return BTA_ERR_ARG;
+    if (P > 1 && ctx->lowmem) return BTA_ERR_STATE;   // the low-memory layout is sequential only
     if (P > 1) {
         // every partition holds an interior block, and L_tt^{-1} fits one block slot
         const PLay L = layout(ctx, P);

@@ -142,12 +142,24 @@ int selinv_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
             if (i > 0) BTA_TRY(arrow_F(i - 1, as));
         }
         // Sigma_ii = X_i^T X_i - Sigma_{i+1,i}^T G - Sigma_{t,i}^T F   (lower, then mirrored)
+        const double* Xs = Xi;
+        long long sXs = sX;
+        if (ctx->lowmem) {
+            // Sigma_ii takes X_i's slot: the product reads a copy.  F_{n-1}
+            // (third stream, issued before the loop) reads that slot too; the
+            // later F_i were joined at the end of step i + 1
+            if (i == n - 1) BTA_TRY(join());
+            double* Xw = ctx->xtmp + m0 * bb;
+            BTA_TRY(copy_mat64(s, Xi, b, Xw, b, b, b, 0, cnt, sX, bb));
+            Xs = Xw;
+            sXs = bb;
+        }
         g = Gemm64{};
         g.M = b; g.N = b; g.K = b;
-        g.A = Xi; g.lda = b; g.ta = 1; g.shA = 2;
-        g.B = Xi; g.ldb = b; g.shB = 1;
+        g.A = Xs; g.lda = b; g.ta = 1; g.shA = 2;
+        g.B = Xs; g.ldb = b; g.shB = 1;
         g.C = SDi; g.ldc = b; g.alpha = 1.0; g.lowerC = 1;
-        g.batch = cnt; g.sA = sX; g.sB = sX; g.sC = S.sD;
+        g.batch = cnt; g.sA = sXs; g.sB = sXs; g.sC = S.sD;
         BTA_TRY(gemm_exec(ex, s, g));
         if (i < n - 1) {
             g = Gemm64{};
@@ -173,6 +185,9 @@ int selinv_impl(bta_ctx_t ctx, int m0, int cnt, cudaStream_t s) {
         }
         BTA_TRY(symmetrize_lower64(s, SDi, b, b, cnt, S.sD));
     }
+    // the low-memory layout has overwritten the factor
+    if (ctx->lowmem)
+        for (int m = m0; m < m0 + cnt; ++m) ctx->factored[m] = 0;
     return BTA_OK;
 }
 

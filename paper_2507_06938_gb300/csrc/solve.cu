@@ -154,7 +154,7 @@ extern "C" int bta_fobj_residual(bta_ctx_t ctx, double* out_dev) {
     if (!ctx || !out_dev) return BTA_ERR_ARG;
     const int B = ctx->batch;
     for (int j = 0; j < B; ++j)
-        if (!ctx->factored[B + j]) return BTA_ERR_STATE;
+        if (!ctx->mu_valid[j]) return BTA_ERR_STATE;
     cudaStream_t s = ctx->stream;
     const long long N = ctx->N;
     double* rhs = vec_row(ctx, VEC_RHS, B);

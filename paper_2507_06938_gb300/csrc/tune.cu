@@ -5,7 +5,7 @@
 //      Cholesky (one batched Cholesky + inverse of a b x b block per step):
 //        FP64:  the leaf order of the recursive Cholesky + inverse (16, 32, 64)
 //        mixed: the double-float leaf order (32, 64, 128) x the smallest
-//               product dimension sent to the tensor cores (128, 256)
+//               product dimension sent to the tensor cores (128, 256, 384, 512)
 //   2. the b x b x b products (Schur updates, selected inversion), timed on
 //      the lower-output update D -= L L^T of every matrix:
 //        FP64:  the CTAs per SM the DFMA GEMM aims for through its K split
@@ -61,7 +61,7 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
     std::vector<Cand> cands;
     if (ctx->precision != BTA_FP64) {
         for (int dl : {32, 64, 128})
-            for (int md : {128, 256}) cands.push_back({ctx->leaf, dl, md});
+            for (int md : {128, 256, 384, 512}) cands.push_back({ctx->leaf, dl, md});
     } else {
         for (int lf : {16, 32, 64}) cands.push_back({lf, ctx->exec.df_leaf, ctx->exec.min_dim});
     }
@@ -77,8 +77,11 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
             ctx->fork->ex2.min_dim = c.min_dim;
         }
         BTA_TRY(copy_mat64(s, ctx->Q.D, b, ctx->L.D, b, b, b, 1, nm, ctx->Q.sD, ctx->L.sD));
-        return chol_inv64(s, ctx->L.D, b, ctx->Linv, b, b, 0, ctx->status, ctx->work, c.leaf, &ctx->exec, nm,
-                          ctx->L.sD, ctx->sLinv, ctx->sWork, 0, ctx->batch, ctx->fork);
+        // the low-memory layout keeps X apart from L only in its X buffer
+        double* X = ctx->lowmem ? ctx->xtmp : ctx->Linv;
+        const long long sX = ctx->lowmem ? (long long)b * b : ctx->sLinv;
+        return chol_inv64(s, ctx->L.D, b, X, b, b, 0, ctx->status, ctx->work, c.leaf, &ctx->exec, nm,
+                          ctx->L.sD, sX, ctx->sWork, 0, ctx->batch, ctx->fork);
     };
     float best = -1.f;
     Cand pick = cands[0];
@@ -171,7 +174,8 @@ extern "C" int bta_autotune(bta_ctx_t ctx, int reps, int* chosen) {
             h.A = ctx->Q.D; h.lda = b; h.sA = ctx->Q.sD;
             if (tri) {
                 // C = A X^T with X the lower inverse factor of the chain stage
-                h.B = ctx->Linv; h.ldb = b; h.tb = 1; h.shB = 2; h.sB = ctx->sLinv;
+                h.B = ctx->lowmem ? ctx->xtmp : ctx->Linv; h.ldb = b; h.tb = 1; h.shB = 2;
+                h.sB = ctx->lowmem ? (long long)b * b : ctx->sLinv;
             } else {
                 h.B = ctx->Q.D; h.ldb = b; h.sB = ctx->Q.sD;
             }

@@ -91,3 +91,17 @@ def test_roofline_records_of_both_precisions():
     assert abs(r["achieved"] - 28 * 86.4) < 1e-6 and r["frac"] == r["achieved"] / bench.BF16_PEAK_TFLOPS
     r2 = bench._roofline("mixed_hi", prof, p, 1, peak, None)
     assert r2["achieved"] == r["achieved"]
+
+
+def test_memory_layouts_of_the_batch_sizing():
+    """The low-memory layout keeps Q, the factor (one spare slot each way) and
+    one buffer per matrix; the default adds the selected inverse and the n
+    inverse blocks: about 0.6 of the bytes at n = 48."""
+    import bench
+    import synth
+    p = synth.problem_from_config("c5")
+    full, low = bench.matrix_bytes(p), bench.matrix_bytes(p, True)
+    bb = 8.0 * p.b * p.b
+    assert abs(full / bb - (3 * (2 * p.nt - 1) + p.nt + 8.5)) < 1e-9
+    assert abs(low / bb - ((2 * p.nt - 1) + 2 * (p.nt + 1) + 1 + 8.5)) < 1e-9
+    assert 0.55 < low / full < 0.62

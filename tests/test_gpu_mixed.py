@@ -126,7 +126,7 @@ def test_autotune_keeps_results_exact(precision):
     if precision == 0:
         assert leaf in (16, 32, 64) and ctas in (1, 2, 4)
     else:
-        assert df_leaf in (32, 64, 128) and tmin in (128, 256)
+        assert df_leaf in (32, 64, 128) and tmin in (128, 256, 384, 512)
         assert tile in ((0, 1) if precision == 1 else (0,)) and waves in (1, 2)
         assert band_tri in (1, 4, 8, 16) and band_gen in (1, 4, 8, 16) and band_low in (1, 4, 8, 16)
     th = np.stack([p.theta0, p.theta0 + 1e-3])
