@@ -51,7 +51,10 @@
 //               next tile's products run
 // Work units are (matrix, tile, K part); a K split (atomic adds into C) only
 // appears when the tiles alone cannot fill the GPU, or, for S = 7, when K
-// exceeds 8192.  Every wait on an mbarrier is bounded in time; on expiry the
+// exceeds 8192.  The units go out in waves of one per CTA, every second wave
+// in reverse CTA order; inside a matrix the tiles are numbered in bands of a
+// tuned number of row tiles, column by column within a band (unit_of,
+// decode_unit).  Every wait on an mbarrier is bounded in time; on expiry the
 // kernel records an error, stops issuing, drains what it issued and frees its
 // tensor memory.
 
