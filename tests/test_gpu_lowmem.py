@@ -128,3 +128,27 @@ def test_switching_keeps_assembled_matrices():
     with pytest.raises(bta.BtaError) as err:
         run.ctx.set_low_memory(True)
     assert err.value.code == bta.BTA_ERR_STATE
+
+
+def test_laplace_in_the_low_memory_layout():
+    """The Newton iterations of the non-Gaussian path factor, take log-dets and
+    solve many times without a selected inversion: the low-memory layout gives
+    the same f and mode as the default one."""
+    import torch
+    from paper_2507_06938_gb300 import bta
+    p = problem("t_pois")
+    thetas = dev(np.stack([p.theta0, p.theta0 + 0.05]))
+    out = []
+    for low in (False, True):
+        model = bta.BtaModel(p)
+        ctx = bta.BtaContext(p.nt, p.b, p.a, 0, None, 2, low_memory=low)
+        f = torch.zeros(2, dtype=torch.float64, device="cuda")
+        x = torch.zeros((2, p.N), dtype=torch.float64, device="cuda")
+        step = torch.zeros(2, dtype=torch.float64, device="cuda")
+        ctx.fobj_laplace(model, thetas, bta.BTA_LIK_POISSON, 12, f, x, step)
+        ctx.sync()
+        out.append((f.cpu().numpy(), x.cpu().numpy()))
+        ctx.close()
+        model.close()
+    assert np.max(np.abs(out[0][0] - out[1][0])) <= 1e-11 * np.max(np.abs(out[0][0]))
+    assert rel_max(out[1][1], out[0][1]) <= 1e-11
