@@ -38,7 +38,7 @@ def blocks_of(ctx, which, store, n, b, a):
     return dict(D=D, B=B, R=R, T=T)
 
 
-class GpuRun:
+class GpuCase:
     """A model + context for one problem; params given directly or by theta."""
 
     def __init__(self, problem, precision=0, stream=None, batch=1):

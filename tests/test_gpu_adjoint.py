@@ -10,7 +10,7 @@ import pytest
 
 from oracle import fobj as ofobj
 
-from gpu_util import GpuRun, build_lib, dev, need_gpu, problem
+from gpu_util import GpuCase, build_lib, dev, need_gpu, problem
 
 pytestmark = pytest.mark.gpu
 
@@ -34,7 +34,7 @@ def test_adjoint_gradient(name, precision, batch, monkeypatch):
     p = problem(name)
     rng = np.random.default_rng(4)
     thetas = p.theta0 + 0.1 * rng.standard_normal((3, p.theta0.shape[0]))
-    run = GpuRun(p, precision=precision, batch=batch)
+    run = GpuCase(p, precision=precision, batch=batch)
     f = torch.zeros(3, dtype=torch.float64, device="cuda")
     g = torch.zeros((3, p.theta0.shape[0]), dtype=torch.float64, device="cuda")
     run.ctx.fobj_grad(run.model, dev(thetas), f, g)
@@ -52,7 +52,7 @@ def test_autograd_function():
     import torch
     from paper_2507_06938_gb300.autograd import fobj
     p = problem("t_coreg2")
-    run = GpuRun(p, batch=2)
+    run = GpuCase(p, batch=2)
     th = torch.tensor(p.theta0 + 0.05, dtype=torch.float64, device="cuda", requires_grad=True)
     val = fobj(th, run.ctx, run.model)
     val.backward()

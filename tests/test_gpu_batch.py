@@ -10,7 +10,7 @@ from oracle import bta as obta
 from oracle import fobj as ofobj
 from oracle import model as omodel
 
-from gpu_util import GpuRun, blocks_of, build_lib, dev, need_gpu, problem, rel_max
+from gpu_util import GpuCase, blocks_of, build_lib, dev, need_gpu, problem, rel_max
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +37,7 @@ def test_batched_fobj_and_selinv(name, precision, batch, monkeypatch):
     monkeypatch.setenv("BTA_OZ_MIN", "64")
     p = problem(name)
     thetas = _stencil(p.theta0)[:5]          # 5 points: one full group and a partial one when batch < 5
-    run = GpuRun(p, precision=precision, batch=batch)
+    run = GpuCase(p, precision=precision, batch=batch)
     f = torch.zeros(thetas.shape[0], dtype=torch.float64, device="cuda")
     mu = torch.zeros((thetas.shape[0], p.N), dtype=torch.float64, device="cuda")
     run.ctx.fobj_eval(run.model, dev(thetas), f, mu)
@@ -64,7 +64,7 @@ def test_batched_error_names_the_matrix():
     import torch
     from paper_2507_06938_gb300 import bta
     p = problem("t_uni")
-    run = GpuRun(p, batch=3)
+    run = GpuCase(p, batch=3)
     prm = omodel.theta_to_params(p.theta0, p.nv)
     params = dev(omodel.params_vector(prm))
     for j in range(3):
@@ -88,7 +88,7 @@ def test_graph_replay_matches_direct(precision, monkeypatch):
     import torch
     monkeypatch.setenv("BTA_OZ_MIN", "64")
     p = problem("t_uni_mid")
-    run = GpuRun(p, precision=precision, batch=3)
+    run = GpuCase(p, precision=precision, batch=3)
     rng = np.random.default_rng(21)
     tol = 1e-9 if precision == 0 else 1e-7
     for call in range(4):

@@ -16,7 +16,7 @@ from oracle import bta as obta
 from oracle import fobj as ofobj
 from oracle import model as omodel
 
-from gpu_util import GpuRun, blocks_of, build_lib, dev, need_gpu, problem, rel_max
+from gpu_util import GpuCase, blocks_of, build_lib, dev, need_gpu, problem, rel_max
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +35,7 @@ def test_factor_logdet_solve_selinv(name, precision, monkeypatch):
     p = problem(name)
     prm = omodel.theta_to_params(p.theta0, p.nv)
     built = omodel.build(p, prm)
-    run = GpuRun(p, precision=precision)
+    run = GpuCase(p, precision=precision)
     run.ctx.set_low_memory(True)
     stol = 1e-9 if precision == 0 else 1e-8
     rng = np.random.default_rng(5)
@@ -82,7 +82,7 @@ def test_fobj_gradient_batch(name, precision, monkeypatch):
     monkeypatch.setenv("BTA_OZ_MIN", "64")
     from paper_2507_06938_gb300 import bta
     p = problem(name)
-    run = GpuRun(p, precision=precision, batch=2)
+    run = GpuCase(p, precision=precision, batch=2)
     if precision == 0:
         run.ctx.set_low_memory(True)
     else:
@@ -111,7 +111,7 @@ def test_switching_keeps_assembled_matrices():
     prm = omodel.theta_to_params(p.theta0, p.nv)
     built = omodel.build(p, prm)
     ref = obta.logdet(obta.factor(obta.blocks_from_sparse(built.Qc, p.nt, p.b, p.a)))
-    run = GpuRun(p, precision=0)
+    run = GpuCase(p, precision=0)
     run.assemble(prm, bta.BTA_QC)
     ld = torch.zeros(1, dtype=torch.float64, device="cuda")
     for low in (True, False, True):

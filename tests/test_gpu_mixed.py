@@ -19,7 +19,7 @@ from oracle import bta as obta
 from oracle import fobj as ofobj
 from oracle import model as omodel
 
-from gpu_util import GpuRun, blocks_of, build_lib, dev, need_gpu, problem, rel_max
+from gpu_util import GpuCase, blocks_of, build_lib, dev, need_gpu, problem, rel_max
 
 pytestmark = pytest.mark.gpu
 
@@ -39,7 +39,7 @@ def test_mixed_factor_logdet_selinv(name, min_dim, monkeypatch):
     p = problem(name)
     prm = omodel.theta_to_params(p.theta0, p.nv)
     built = omodel.build(p, prm)
-    run = GpuRun(p, precision=bta.BTA_MIXED)
+    run = GpuCase(p, precision=bta.BTA_MIXED)
     for which, Q in ((bta.BTA_QP, built.Qp), (bta.BTA_QC, built.Qc)):
         blk = obta.blocks_from_sparse(Q, p.nt, p.b, p.a)
         Lo = obta.factor(blk)
@@ -72,7 +72,7 @@ def test_mixed_fobj(name, monkeypatch):
     from paper_2507_06938_gb300 import bta
     monkeypatch.setenv("BTA_OZ_MIN", "64")
     p = problem(name)
-    run = GpuRun(p, precision=bta.BTA_MIXED)
+    run = GpuCase(p, precision=bta.BTA_MIXED)
     th = p.theta0[None, :]
     f = torch.zeros(1, dtype=torch.float64, device="cuda")
     mu = torch.zeros(p.N, dtype=torch.float64, device="cuda")
@@ -118,10 +118,10 @@ def test_autotune_keeps_results_exact(precision):
     """The autotuner only changes launch shapes: after it runs, f_obj and the
     conditional mean still match the oracle at the bounds of the precision."""
     import torch
-    from gpu_util import GpuRun, dev, problem, rel_max
+    from gpu_util import GpuCase, dev, problem, rel_max
     from oracle import fobj as ofobj
     p = problem("t_uni_mid")
-    run = GpuRun(p, precision=precision, batch=2)
+    run = GpuCase(p, precision=precision, batch=2)
     leaf, df_leaf, tmin, tile, waves, ctas, band_tri, band_gen, band_low = run.ctx.autotune(reps=1)
     if precision == 0:
         assert leaf in (16, 32, 64) and ctas in (1, 2, 4)
@@ -153,7 +153,7 @@ def test_mixed_tile_128x64_three_stages(name, monkeypatch):
     p = problem(name)
     prm = omodel.theta_to_params(p.theta0, p.nv)
     built = omodel.build(p, prm)
-    run = GpuRun(p, precision=bta.BTA_MIXED)
+    run = GpuCase(p, precision=bta.BTA_MIXED)
     Q = built.Qc
     Lo = obta.factor(obta.blocks_from_sparse(Q, p.nt, p.b, p.a))
     run.assemble(prm, bta.BTA_QC)

@@ -21,7 +21,7 @@ from oracle import bta as obta
 from oracle import fobj as ofobj
 from oracle import model as omodel
 
-from gpu_util import GpuRun, blocks_of, build_lib, dev, need_gpu, problem, rel_max
+from gpu_util import GpuCase, blocks_of, build_lib, dev, need_gpu, problem, rel_max
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +41,7 @@ def test_mixed_hi_factor_logdet_selinv(name, min_dim, monkeypatch):
     p = problem(name)
     prm = omodel.theta_to_params(p.theta0, p.nv)
     built = omodel.build(p, prm)
-    run = GpuRun(p, precision=bta.BTA_MIXED_HI)
+    run = GpuCase(p, precision=bta.BTA_MIXED_HI)
     for which, Q in ((bta.BTA_QP, built.Qp), (bta.BTA_QC, built.Qc)):
         Lo = obta.factor(obta.blocks_from_sparse(Q, p.nt, p.b, p.a))
         run.assemble(prm, which)
@@ -72,7 +72,7 @@ def test_mixed_hi_fobj_and_gradient(name, monkeypatch):
     from paper_2507_06938_gb300 import bta
     monkeypatch.setenv("BTA_OZ_MIN", "64")
     p = problem(name)
-    run = GpuRun(p, precision=bta.BTA_MIXED_HI)
+    run = GpuCase(p, precision=bta.BTA_MIXED_HI)
     th = dev(p.theta0[None, :])
     f = torch.zeros(1, dtype=torch.float64, device="cuda")
     mu = torch.zeros(p.N, dtype=torch.float64, device="cuda")
@@ -103,7 +103,7 @@ def test_tile_order_bands(band, monkeypatch):
     p = problem("t_coreg3_mid")
     prm = omodel.theta_to_params(p.theta0, p.nv)
     built = omodel.build(p, prm)
-    run = GpuRun(p, precision=bta.BTA_MIXED_HI)
+    run = GpuCase(p, precision=bta.BTA_MIXED_HI)
     Lo = obta.factor(obta.blocks_from_sparse(built.Qc, p.nt, p.b, p.a))
     run.assemble(prm, bta.BTA_QC)
     run.ctx.factor(bta.BTA_QC)

@@ -19,7 +19,7 @@ from oracle import dense as odense
 from oracle import fobj as ofobj
 from oracle import model as omodel
 
-from gpu_util import GpuRun, blocks_of, build_lib, dev, need_gpu, problem, rel_max
+from gpu_util import GpuCase, blocks_of, build_lib, dev, need_gpu, problem, rel_max
 
 pytestmark = pytest.mark.gpu
 
@@ -51,7 +51,7 @@ def test_assembly_matches_oracle(name):
     p = problem(name)
     prm = _params(p, rho_override=0.7 if name == "c1" else None)
     built, ref = _oracle_blocks(p, prm)
-    run = GpuRun(p)
+    run = GpuCase(p)
     for which in (bta.BTA_QP, bta.BTA_QC):
         run.assemble(prm, which)
         run.ctx.sync()
@@ -69,7 +69,7 @@ def test_factor_logdet_solve_selinv_match_dense(name, leaf, monkeypatch):
     p = problem(name)
     prm = _params(p)
     built, ref = _oracle_blocks(p, prm)
-    run = GpuRun(p)
+    run = GpuCase(p)
     rng = np.random.default_rng(7)
     for which, Q in ((bta.BTA_QP, built.Qp), (bta.BTA_QC, built.Qc)):
         Qd = Q.toarray()
@@ -110,7 +110,7 @@ def test_factor_logdet_solve_selinv_match_dense(name, leaf, monkeypatch):
 def test_fobj_matches_oracle(name):
     import torch
     p = problem(name)
-    run = GpuRun(p)
+    run = GpuCase(p)
     rng = np.random.default_rng(11)
     thetas = np.stack([p.theta0, p.theta0 + 0.1 * rng.standard_normal(p.theta0.shape)])
     f = torch.zeros(2, dtype=torch.float64, device="cuda")
@@ -132,7 +132,7 @@ def test_mid_size_against_tier_b(name):
     p = problem(name)
     prm = _params(p)
     built, ref = _oracle_blocks(p, prm)
-    run = GpuRun(p)
+    run = GpuCase(p)
     which = bta.BTA_QC
     Lo = obta.factor(ref[which])
     So = obta.selinv(Lo)
@@ -154,7 +154,7 @@ def test_not_positive_definite_is_reported():
     from paper_2507_06938_gb300 import bta
     p = problem("t_uni")
     prm = _params(p)
-    run = GpuRun(p)
+    run = GpuCase(p)
     run.assemble(prm, bta.BTA_QP)
     run.ctx.sync()
     D1 = run.ctx.block(bta.BTA_QP, bta.BTA_STORE_Q, bta.BTA_BLK_D, 1)
@@ -175,7 +175,7 @@ def test_argument_errors_are_returned():
     import torch
     from paper_2507_06938_gb300 import bta
     p = problem("t_uni")
-    run = GpuRun(p)
+    run = GpuCase(p)
     with pytest.raises(bta.BtaError) as e:
         run.ctx.solve(bta.BTA_QC, torch.zeros(p.N, dtype=torch.float64, device="cuda"),
                       torch.zeros(p.N, dtype=torch.float64, device="cuda"))

@@ -19,7 +19,7 @@ from oracle import bta as obta
 from oracle import fobj as ofobj
 from oracle import model as omodel
 
-from gpu_util import GpuRun, blocks_of, build_lib, dev, need_gpu, problem, rel_max
+from gpu_util import GpuCase, blocks_of, build_lib, dev, need_gpu, problem, rel_max
 
 pytestmark = pytest.mark.gpu
 
@@ -43,7 +43,7 @@ def test_partitioned_factor_solve_selinv(name, P):
     p = problem(name)
     prm = omodel.theta_to_params(p.theta0, p.nv)
     built = omodel.build(p, prm)
-    run = GpuRun(p, precision=bta.BTA_FP64)
+    run = GpuCase(p, precision=bta.BTA_FP64)
     run.ctx.set_time_partitions(P)
     rng = np.random.default_rng(P)
     for which, Q in ((bta.BTA_QP, built.Qp), (bta.BTA_QC, built.Qc)):
@@ -77,7 +77,7 @@ def test_partitioned_fobj_and_gradient(name, P, precision, monkeypatch):
     from paper_2507_06938_gb300 import bta
     monkeypatch.setenv("BTA_OZ_MIN", "64")
     p = problem(name)
-    run = GpuRun(p, precision=precision, batch=2)
+    run = GpuCase(p, precision=precision, batch=2)
     run.ctx.set_time_partitions(P)
     thetas = np.stack([p.theta0, p.theta0 + 0.03])
     f = torch.zeros(2, dtype=torch.float64, device="cuda")
@@ -96,7 +96,7 @@ def test_partitioned_fobj_and_gradient(name, P, precision, monkeypatch):
 def test_partition_count_limits():
     from paper_2507_06938_gb300 import bta
     p = problem("t_uni")          # n = 5: P = 2 (h = 3) and P = 3 (h = 2); P = 4 leaves no last interior
-    run = GpuRun(p, precision=0)
+    run = GpuCase(p, precision=0)
     for P in (0, 4, 6):
         with pytest.raises(bta.BtaError) as e:
             run.ctx.set_time_partitions(P)
@@ -117,7 +117,7 @@ def test_relayout_keeps_assembled_matrices():
     p = problem("t_coreg3_mid")
     prm = omodel.theta_to_params(p.theta0, p.nv)
     built = omodel.build(p, prm)
-    run = GpuRun(p, precision=0)
+    run = GpuCase(p, precision=0)
     run.assemble(prm, bta.BTA_QC)
     ref = obta.logdet(obta.factor(obta.blocks_from_sparse(built.Qc, p.nt, p.b, p.a)))
     ld = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -137,7 +137,7 @@ def test_partitioned_error_names_the_matrix():
     import torch
     from paper_2507_06938_gb300 import bta
     p = problem("t_uni_mid")      # n = 12, P = 3: h = 5, partition 1 holds blocks 5..8
-    run = GpuRun(p, batch=3)
+    run = GpuCase(p, batch=3)
     run.ctx.set_time_partitions(3)
     prm = omodel.theta_to_params(p.theta0, p.nv)
     params = dev(omodel.params_vector(prm))
