@@ -105,3 +105,28 @@ def test_memory_layouts_of_the_batch_sizing():
     assert abs(full / bb - (3 * (2 * p.nt - 1) + p.nt + 8.5)) < 1e-9
     assert abs(low / bb - ((2 * p.nt - 1) + 2 * (p.nt + 1) + 1 + 8.5)) < 1e-9
     assert 0.55 < low / full < 0.62
+
+
+def test_layout_choice_follows_the_free_memory(monkeypatch):
+    """--memory auto takes the low-memory layout exactly when it fits more
+    theta points per step; an explicit batch or time partitions keep the
+    default layout, and --memory low/full force it."""
+    import types
+    import bench
+    import synth
+    import torch
+    p = synth.problem_from_config("c5")
+    free = {"v": 290e9}
+    monkeypatch.setattr(torch.cuda, "mem_get_info", lambda *a: (free["v"], 298e9))
+    args = types.SimpleNamespace(memory="auto", batch=0, time_partitions=1)
+    assert bench.choose_layout(args, p) == (2, True)
+    free["v"] = 120e9                      # one point either way: keep the default layout
+    assert bench.choose_layout(args, p) == (1, False)
+    free["v"] = 290e9
+    assert bench.choose_layout(args, p, batch=1) == (1, False)
+    args.time_partitions = 4
+    assert bench.choose_layout(args, p) == (1, False)
+    args.time_partitions, args.memory = 1, "low"
+    assert bench.choose_layout(args, p, batch=1) == (1, True)
+    args.memory = "full"
+    assert bench.choose_layout(args, p) == (1, False)
