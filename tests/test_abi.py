@@ -79,6 +79,13 @@ def test_host_only_entry_points(lib):
     assert lib.bta_fobj_eval_multi(0, null, null, null, one, null, None, None, None) == 1
     assert lib.bta_fobj_eval_multi(1, null, null, null, one, null, None, None, None) == 1
     assert lib.bta_fobj_eval_multi(1, None, None, None, None, None, None, None, None) == 1
+    # the creation flags, the layout switches and the read-outs check their arguments first
+    assert lib.bta_create_ex(4, 10, 2, 0, 1, 2, None, ctypes.byref(h)) == 1
+    assert lib.bta_create_ex(4, 10, 2, 0, 0, 1, None, ctypes.byref(h)) == 1
+    assert lib.bta_set_low_memory(None, 1) == 1
+    assert lib.bta_set_time_partitions(None, 2) == 1
+    ms = (ctypes.c_double * 5)()
+    assert lib.bta_profile_phases(None, ms, 5) == 1
 
 
 C_PROGRAM = r"""
@@ -103,6 +110,8 @@ int main(void) {
     if (bta_fobj_eval_multi(0, ctxs, models, thetas, n_theta, fs, NULL, NULL, NULL) != BTA_ERR_ARG) return 14;
     if (bta_fobj_eval_multi(1, ctxs, models, thetas, n_theta, fs, NULL, NULL, NULL) != BTA_ERR_ARG) return 15;
     if (bta_chol_inv_noalloc(NULL, 4, 4, NULL, 4, NULL, NULL) != BTA_ERR_ARG) return 16;
+    if (bta_create_ex(4, 10, 2, BTA_MIXED_HI, 0, BTA_CREATE_LOW_MEMORY, NULL, &ctx) != BTA_ERR_ARG) return 17;
+    if (bta_set_low_memory(NULL, 1) != BTA_ERR_ARG) return 18;
     printf("%s|%s\n", bta_strerror(BTA_ERR_ARG), bta_strerror(BTA_ERR_STATE));
     return 0;
 }
