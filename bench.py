@@ -274,7 +274,9 @@ def choose_layout(args, p, batch=None):
     """(points per step, low-memory layout?): `--memory auto` takes the
     low-memory layout when it fits more points per step."""
     requested = batch or args.batch
-    if args.memory == "low" or (args.memory == "auto" and args.time_partitions <= 1 and not requested and
+    if args.time_partitions > 1:       # the partitioned path has its own layout
+        return default_batch(p, requested, False), False
+    if args.memory == "low" or (args.memory == "auto" and not requested and
                                 default_batch(p, 0, True) > default_batch(p, 0, False)):
         return default_batch(p, requested, True), True
     return default_batch(p, requested, False), False

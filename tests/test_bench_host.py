@@ -126,6 +126,9 @@ def test_layout_choice_follows_the_free_memory(monkeypatch):
     assert bench.choose_layout(args, p, batch=1) == (1, False)
     args.time_partitions = 4
     assert bench.choose_layout(args, p) == (1, False)
+    args.memory = "low"
+    assert bench.choose_layout(args, p) == (1, False)
+    args.memory = "auto"
     args.time_partitions, args.memory = 1, "low"
     assert bench.choose_layout(args, p, batch=1) == (1, True)
     args.memory = "full"
