@@ -152,3 +152,31 @@ def test_laplace_in_the_low_memory_layout():
         model.close()
     assert np.max(np.abs(out[0][0] - out[1][0])) <= 1e-11 * np.max(np.abs(out[0][0]))
     assert rel_max(out[1][1], out[0][1]) <= 1e-11
+
+
+def test_partial_group_and_host_buffers():
+    """Three theta points through a two-slot context (a full group, then a
+    partial one) and the host-buffer entry, in the low-memory layout: the
+    same f, gradient and marginal variances as the default layout."""
+    import torch
+    from paper_2507_06938_gb300 import bta
+    p = problem("t_coreg3")
+    dim = p.theta0.shape[0]
+    th = np.stack([p.theta0, p.theta0 + 0.02, p.theta0 - 0.02])
+    res = []
+    for low in (False, True):
+        model = bta.BtaModel(p)
+        ctx = bta.BtaContext(p.nt, p.b, p.a, 0, None, 2, low_memory=low)
+        f = torch.zeros(3, dtype=torch.float64, device="cuda")
+        g = torch.zeros((3, dim), dtype=torch.float64, device="cuda")
+        ctx.fobj_grad(model, dev(th), f, g)
+        ctx.sync()
+        fh = torch.zeros(2, dtype=torch.float64).pin_memory()
+        gh = torch.zeros((2, dim), dtype=torch.float64).pin_memory()
+        vh = torch.zeros((2, p.N), dtype=torch.float64).pin_memory()
+        ctx.fobj_grad_host(model, torch.tensor(th[:2]).pin_memory(), fh, gh, vh)
+        res.append((f.cpu().numpy(), g.cpu().numpy(), fh.numpy().copy(), gh.numpy().copy(), vh.numpy().copy()))
+        ctx.close()
+        model.close()
+    for a, b in zip(res[0], res[1]):
+        assert rel_max(b, a) <= 1e-11
