@@ -283,7 +283,7 @@ int gemm_mixed_fn(const GemmExec* ex, cudaStream_t s, const Gemm64& g);
 // read completely (digit split) before C is written: C may then alias A or B
 bool gemm_mixed_takes(const GemmExec* ex, const Gemm64& g);
 
-// ---------------------------------------------------------------- drivers on matrices m0 .. m0+count-1
+// ---------------------------------------------------------------- entry points on matrices m0 .. m0+count-1
 int factor_impl(bta_ctx_t ctx, int m0, int count, cudaStream_t s);
 int logdet_impl(bta_ctx_t ctx, int m0, int count, double* out, cudaStream_t s);
 // x_j = Q_{m0+j}^{-1} r_j, vectors N apart

@@ -1,5 +1,5 @@
 // FP64 throughput probes: the measured denominators of the FP64 path's
-// roofline (the measured peaks cover HBM and bf16 only).
+// roofline (the measured peaks the benchmark reads cover HBM and bf16 only).
 
 #include "common.cuh"
 

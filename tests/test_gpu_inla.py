@@ -1,4 +1,4 @@
-"""The INLA driver on the GPU path (c1: 10x10 grid, nt = 8, N = 802,
+"""The INLA optimiser on the GPU path (c1: 10x10 grid, nt = 8, N = 802,
 dim(theta) = 4): the mode of f_obj by BFGS (Eq. 9), the Gaussian
 hyperparameter marginals and the latent marginals at the mode.
 

@@ -1,4 +1,4 @@
-"""Host logic of the INLA driver (mode by BFGS, Hessian, marginals), run on
+"""Host logic of the INLA optimiser (mode by BFGS, Hessian, marginals), run on
 the CPU with objectives that need no GPU:
   * Rosenbrock's function, whose maximiser of -f is (1, ..., 1);
   * a quadratic, whose central-difference Hessian of the gradient is exact;
@@ -32,7 +32,7 @@ def _rosen_grad(x):
 
 
 def test_bfgs_finds_the_rosenbrock_minimum():
-    # the driver maximises f, so f = -rosen
+    # the optimiser maximises f, so f = -rosen
     res = inla.bfgs(lambda x: (-_rosen(x), -_rosen_grad(x)), np.array([-1.2, 1.0, -0.5, 0.8]),
                     gtol=1e-8, max_iter=500)
     assert res.converged
@@ -64,7 +64,7 @@ def test_stencil_differences_match_eq10():
 
 class _OracleObjective:
     """The oracle's f_obj (dense tier) and adjoint gradient: test stand-in for
-    the GPU objective of the driver."""
+    the GPU objective of the optimiser."""
 
     def __init__(self, problem):
         self.problem = problem
